@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the whole HR-EBSD hot path on GB300, in pattern pairs per second.
+
+One step = one pass of every stage over one batch of synthetic pairs:
+preprocess (references + tests), multi-resolution demons registration,
+rotation fit, remap, second-pass ROI XCF and deformation-gradient solve, all
+through the C ABI of libhrebsd.  Workload (default): the batched scan of
+100 x 100 = 10,000 test patterns at 256 x 256 FP32 against 4 grain
+references, demons with 4 levels and a convergence-driven stop (<= 100
+iterations per level), 25 ROIs of 64 x 64.  Inputs come from the seeded
+Kikuchi generator and are resident in HBM before timing (2.6 GB, larger than
+L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank processes its own 10,000 pairs (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+ALGO_BYTES_PER_PIXEL_ITER = 24   # test 4 B + moving 4 B + field 8 B read, field 8 B written
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "pattern pairs/s (demons+XCF) on 1 GB300"
+
+
+def workload(n_pairs):
+    from synth import kikuchi as K
+    spec = K.config2(n_pairs)
+    return dict(spec=spec, H=256, W=256, levels=4, caps=(100, 100, 100, 100), stop_window=5, stop_tol=1e-4,
+                S=64, roi=K.roi_grid(256, 256, 64, False))
+
+
+def workload_config(wl, B):
+    return {"workload": f"batched scan: {B} test patterns 256x256 FP32 vs 4 grain references; demons 4 levels, "
+                        f"<=100 it/level, stop w=5 tol=1e-4, alpha=1, sigma=1; 25 ROIs 64x64; FP64 fits",
+            "pairs_per_gpu": B, "H": 256, "W": 256, "refs": 4, "levels": 4, "max_iters_per_level": 100,
+            "rois": 25, "roi_size": 64, "misorientation_deg": [0, 6], "counts": 500,
+            "l2": "inputs (2.6 GB) larger than L2; no flush"}
+
+
+# ------------------------------------------------------------------ oracle on host cores
+def _oracle_pair(args):
+    p, n_pairs = args
+    import numpy as np
+    import oracle
+    from synth import kikuchi as K
+    wl = workload(n_pairs)
+    spec = wl["spec"]
+    r = K.ref_index(spec, p)
+    ref = K.render_ref(spec, r).astype(np.float64)
+    test = K.render_test(spec, p).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.pipeline(ref, test, wl["roi"], wl["S"], spec.geom, wl["levels"], list(wl["caps"]), 1.0, 1.0,
+                    wl["stop_window"], wl["stop_tol"])
+    return time.perf_counter() - t0
+
+
+def oracle_throughput(n_sample, n_pairs, cores, pool=None):
+    """Pairs/s of the oracle over `n_sample` pairs, one pair per process."""
+    import oracle
+    oracle.build()
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    try:
+        t0 = time.perf_counter()
+        per_pair = pool.map(_oracle_pair, [(p, n_pairs) for p in range(n_sample)], chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    return n_sample / wall, sum(per_pair), wall
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d and isinstance(d[k], (int, float)):
+                return float(d[k]), "measured"
+        for v in d.values():
+            if isinstance(v, dict) and "hbm_gbs" in v:
+                return float(v["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_launch(px_per_launch):
+    """DRAM bytes per demons-iteration launch from the committed ncu summary, if it still matches the kernel."""
+    path = os.path.join(ROOT, "profiles", "demons_iter_traffic.json")
+    try:
+        d = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_1907_05993_gb300", "csrc", "demons.cu"), "rb").read()
+        if d.get("demons_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return d["dram_bytes_per_pixel_iter"] * px_per_launch
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ main arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = workload(args.pairs)
+    cores = os.cpu_count() or 1
+    sample = max(cores, args.ref_sample)
+    pool = mp.get_context("spawn").Pool(cores)
+    try:
+        for _ in range(args.warmup):
+            oracle_throughput(min(sample, cores), args.pairs, cores, pool)
+        vals, cpu_s = [], 0.0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, cs, wall = oracle_throughput(sample, args.pairs, cores, pool)
+            vals.append(wall)
+            cpu_s += cs
+        total = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    value = args.steps * sample / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, args.pairs),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} pairs of the workload per step (pairs 0..{sample - 1}), "
+                                       f"one pair per process, FP64 C oracle"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # before any CUDA call: the oracle pool is spawned, never forked from a CUDA process
+        cores = os.cpu_count() or 1
+        n = max(cores, args.cpu_sample)
+        v, cpu_s, wall = oracle_throughput(n, args.pairs, cores)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} pairs of the workload (pairs 0..{n - 1}), one pair per process over {cores} host "
+                         f"cores, {cpu_s:.1f} s of CPU work"}
+    import numpy as np
+    import torch
+    import paper_1907_05993_gb300 as P
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    from synth import gpu as synth_gpu
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    wl = workload(args.pairs)
+    spec = wl["spec"]
+    B = args.pairs
+    # this rank's shard of a world * B point scan (independent pairs)
+    from synth import kikuchi as K
+    spec = K.ScanSpec(**{**spec.__dict__, "n_pairs": B * world})
+    pairs = range(rank * B, (rank + 1) * B)
+    refs, tests, ridx, _ = synth_gpu.make_scan_gpu(spec, pairs)
+    torch.cuda.synchronize()
+    cfg = PipelineConfig(wl["H"], wl["W"], wl["roi"], wl["S"], wl["levels"], wl["caps"], 1.0, 1.0,
+                         wl["stop_tol"], wl["stop_window"])
+    pipe = Pipeline(cfg, device=local_rank)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for _ in range(args.warmup):
+        pipe.run(refs, tests, ridx, out=out)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    P.hrebsd_profile_enable(pipe.ctx, True)
+    l0 = P.hrebsd_launch_count(pipe.ctx)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        pipe.run(refs, tests, ridx, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = P.hrebsd_launch_count(pipe.ctx) - l0
+    prof = P.hrebsd_profile_read(pipe.ctx)
+    P.hrebsd_profile_enable(pipe.ctx, False)
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt)
+    value = world * B * args.steps / t
+    iters = out["iters"].cpu().numpy()
+    status = out["status"].cpu().numpy()
+
+    # ---- end to end through the ABI with host buffers (pinned), copies inside the timed region
+    h_tests = tests.cpu().pin_memory()
+    h_refs = refs.cpu().pin_memory()
+    h_ridx = ridx.cpu().pin_memory()
+    d_tests, d_refs, d_ridx = torch.empty_like(tests), torch.empty_like(refs), torch.empty_like(ridx)
+    h_F = torch.empty((B, 9), dtype=torch.float64).pin_memory()
+    h_R = torch.empty((B, 9), dtype=torch.float64).pin_memory()
+    h_st = torch.empty((B,), dtype=torch.int32).pin_memory()
+    e_steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        d_tests.copy_(h_tests, non_blocking=True)
+        d_refs.copy_(h_refs, non_blocking=True)
+        d_ridx.copy_(h_ridx, non_blocking=True)
+        pipe.run(d_refs, d_tests, d_ridx, out=out)
+        h_F.copy_(out["F"], non_blocking=True)
+        h_R.copy_(out["R_finite"], non_blocking=True)
+        h_st.copy_(out["status"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = e0.elapsed_time(e1) / 1e3
+    if dist:
+        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt)
+        dist.barrier()
+    h2d = tests.numel() * 4 + refs.numel() * 4 + ridx.numel() * 4
+    d2h = B * 9 * 8 * 2 + B * 4
+
+    if rank == 0:
+        it = prof["demons_iter"]
+        px = prof["pixel_iters"]
+        peak, peak_kind = measured_peak_hbm()
+        achieved = ALGO_BYTES_PER_PIXEL_ITER * px / (it["ms"] / 1e3) / 1e9 if it["ms"] > 0 else None
+        px_per_launch = px / max(1, it["launches"])
+        traffic = traffic_per_launch(px_per_launch)
+        total_ms = sum(v["ms"] for k, v in prof.items() if k != "pixel_iters")
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded kinematic Kikuchi generator)",
+            "config": workload_config(wl, B),
+            "e2e": {"value": world * B * e_steps / te, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": "demons_iter_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s",
+                         "algorithmic_bytes": f"{ALGO_BYTES_PER_PIXEL_ITER} B per pixel-iteration x "
+                                              f"{px_per_launch:.0f} pixel-iterations per launch (average)",
+                         "avg_launch_ms": it["ms"] / max(1, it["launches"]),
+                         "share_of_step": it["ms"] / total_ms if total_ms else None},
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if k != "pixel_iters"},
+            "demons_iters_mean_per_level": [float(x) for x in iters.mean(axis=0)],
+            "pairs_capped": int(np.sum(status & 1)),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    pipe.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--pairs", type=int, default=10_000)
+    ap.add_argument("--cpu-sample", type=int, default=48)
+    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * hrebsd.h -- C ABI of the GB300 (sm_103a) HR-EBSD demons-remapping library.
+ *
+ * The method is Zhu, Kaufmann & Vecchio, "Novel Remapping Approach for
+ * HR-EBSD based on Demons Registration" (arXiv 1907.05993).  For every scan
+ * point the test Kikuchi pattern is registered against its reference by
+ * multi-resolution demons (Section 1, Eq. 1), the lattice rotation is fitted
+ * to the displacement field at the ROI centres (Section 2, Eq. 2-5), the
+ * reference is remapped by that rotation (Eq. 12), and a second-pass ROI
+ * cross-correlation (Section 2) gives the shifts for the final deformation
+ * gradient F = F_inf R_finite (Eq. 3, Eq. 12).
+ *
+ * Conventions shared by every call
+ *   - All array arguments are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) owned by the caller, unless a call says otherwise.  The
+ *     library only allocates its own workspace inside the context.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  The caller synchronises before reading outputs.
+ *   - Images are FP32 row-major [n][H][W].  Index coordinates put pixel
+ *     centres on integers (x = column, y = row, rows downward); continuous
+ *     detector coordinates put them at (column + 0.5, row + 0.5).
+ *   - A displacement field is FP32 [B][2][H][W]: the x plane then the y
+ *     plane, in pixels.  The reference pattern is the moving image M, the
+ *     test pattern the fixed image; M warped by u is M(x - u(x)).
+ *   - Geometry: pattern centre at (xstar*W, ystar*H) continuous pixels,
+ *     detector distance Z* = zstar*W pixels, screen normal k = (0,0,1)
+ *     (Eq. 2).  Points are lifted to r = (x - xpc, y - ypc, Z*).
+ *   - 3x3 matrices are FP64 row-major [B][9].
+ *   - ROI centres roi_xy are int32 [N][2] (x, y) in continuous pixels; a
+ *     ROI of size S covers rows/columns [c - S/2, c + S/2).
+ *   - Return value: HREBSD_OK or a negative HREBSD_E* code (argument checks
+ *     happen before any launch; on a CUDA error the context stays usable
+ *     unless the error is sticky).  Problems of single pairs never fail a
+ *     call: they are reported as bits of pair_status[B].
+ */
+#ifndef HREBSD_H
+#define HREBSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HREBSD_OK 0
+#define HREBSD_EINVAL -1   /* bad argument (null pointer, size, unsupported parameter) */
+#define HREBSD_ECUDA -2    /* a CUDA runtime call or launch failed */
+#define HREBSD_ENOMEM -3   /* workspace allocation failed */
+#define HREBSD_ETIMEOUT -4 /* a bounded device-side wait expired */
+
+/* pair_status bits */
+#define HREBSD_PAIR_CAPPED 1      /* some pyramid level stopped at its iteration cap */
+#define HREBSD_PAIR_NONFINITE 2   /* the field or an input contained NaN/Inf */
+#define HREBSD_PAIR_FIT_FAILED 4  /* Eq. 3 fit degenerate (singular normal matrix) */
+
+typedef struct hrebsd_ctx hrebsd_ctx;
+
+/* Create a context on CUDA device `device` (made current for the calls of
+ * this context).  *ctx receives the handle.  Errors: EINVAL (null ctx or
+ * bad device), ECUDA. */
+int hrebsd_create(hrebsd_ctx **ctx, int device);
+
+/* Free the context and its workspace (synchronises the device first). */
+int hrebsd_destroy(hrebsd_ctx *ctx);
+
+/* Human-readable text of a status code (static storage, never NULL). */
+const char *hrebsd_status_string(int status);
+
+/* Kernel launches of this context since creation (for accounting). */
+long long hrebsd_launch_count(const hrebsd_ctx *ctx);
+
+/* Tracing: per kernel class, CUDA-event time of every launch (events are
+ * recorded on the launch stream around each kernel while enabled).  Classes:
+ * 0 demons iteration, 1 demons stop control, 2 demons pyramid/finalize/
+ * prolongation, 3 preprocess, 4 rotation fit, 5 remap, 6 ROI XCF,
+ * 7 deformation-gradient solve.  pixel_iters counts demons pixel-iterations
+ * (active pairs x level pixels, summed over iteration launches). */
+#define HREBSD_PROF_CLASSES 8
+typedef struct {
+    double ms[HREBSD_PROF_CLASSES];
+    long long launches[HREBSD_PROF_CLASSES];
+    long long pixel_iters;
+} hrebsd_profile;
+
+/* Enable (1) or disable (0) tracing; either call resets the counters. */
+int hrebsd_profile_enable(hrebsd_ctx *ctx, int enable);
+
+/* Synchronise the device and return the counters gathered since the last
+ * reset.  Errors: EINVAL (null pointers), ECUDA. */
+int hrebsd_profile_read(hrebsd_ctx *ctx, hrebsd_profile *out);
+
+typedef struct {
+    double xstar, ystar, zstar;
+} hrebsd_geometry;
+
+/* Demons parameters.  levels: pyramid levels (1..8; level 0 is the full
+ * size, level l is (H >> l) x (W >> l), both must stay >= 8 and H, W must be
+ * divisible by 2^(levels-1)).  max_iters[l]: iteration cap of level l
+ * (0..4096).  alpha: force weight of Eq. 1 (du = d grad F / (|grad F|^2 +
+ * alpha^2 d^2)).  sigma_update, sigma_field: Gaussian smoothing of the update
+ * and of the field (radius ceil(3 sigma) <= 6; 0 = none).  stop_window w and
+ * stop_tol: a level stops at iteration k >= w when E_{k-w} - E_k <
+ * stop_tol * E_{k-w} (E = SSD); w = 0 runs every level to its cap.
+ * start_level: first (coarsest) level to run, -1 = levels - 1. */
+typedef struct {
+    int levels;
+    int max_iters[8];
+    float alpha;
+    float sigma_update;
+    float sigma_field;
+    float stop_tol;
+    int stop_window;
+    int start_level;
+} hrebsd_demons_params;
+
+/* a1 -- intensity normalisation (Section 2) with static background
+ * correction (Section 3.3): for each of the n patterns in [n][H][W], if
+ * `flat` the least-squares quadric c0 + c1 x + c2 y + c3 x^2 + c4 xy + c5 y^2
+ * (x, y in [-1, 1] at pixel centres) is divided out, then the pattern is
+ * brought to zero mean and unit standard deviation (a constant pattern
+ * becomes all zeros).  in and out may alias.  Errors: EINVAL (n < 0, H or
+ * W < 2, null pointers with n > 0). */
+int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int flat, float *out,
+                            void *stream);
+
+/* a2-a4, a9 -- multi-resolution demons registration of B pairs (Section 1,
+ * Eq. 1).  ref [R][H][W] and test [B][H][W] must be preprocessed
+ * (hrebsd_preprocess_batch).  Pair b registers ref[ref_idx[b]] (moving) onto
+ * test[b] (fixed).  Per level, from params->start_level down to 0: the
+ * pyramid images are 2x2 box means; the field starts at zero on the first
+ * level (or at init_field [B][2][H>>s][W>>s], s the start level, if not
+ * NULL) and at twice the bilinear prolongation of the coarser result
+ * otherwise; each iteration warps M by u (bilinear, clamped), forms the
+ * force from the gradient of the test image (central differences, one-sided
+ * at borders; du = 0 where the denominator <= 1e-9), smooths du, adds it,
+ * smooths u (separable Gaussians, x pass then y pass, replicated borders).
+ * Pairs stop independently (stop rule above); the batch runs until every
+ * pair has stopped.  Outputs: field [B][2][H][W] (finest level), iters
+ * [B][levels] (updates applied per level, 0 for skipped levels),
+ * pair_status [B] (CAPPED, NONFINITE bits set; other bits cleared).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float *test, const int32_t *ref_idx,
+                                 int R, int B, int H, int W, const hrebsd_demons_params *params,
+                                 const float *init_field, float *field, int32_t *iters, int32_t *pair_status,
+                                 void *stream);
+
+/* a5 -- rotation fit (Section 2, Eq. 2-5).  The field [B][2][H][W] is
+ * sampled bilinearly at the N ROI centres c (index coordinates c - 0.5);
+ * with reference points r_i = c_i - u(c_i) and test points r'_i = c_i the
+ * Eq. 3 least-squares problem is solved in FP64 (linear start with
+ * F_33 = 1, Gauss-Newton, then det F = 1), and R_finite is the polar factor
+ * of F (Eq. 4-5, Newton polar iteration).  Outputs F_first, R_finite
+ * [B][9]; pair_status |= FIT_FAILED on a singular fit (then F_first =
+ * R_finite = I).  N >= 4.  pair_status may be NULL. */
+int hrebsd_fit_rotation(hrebsd_ctx *ctx, const float *field, int B, int H, int W, const int32_t *roi_xy, int N,
+                        const hrebsd_geometry *geom, double *F_first, double *R_finite, int32_t *pair_status,
+                        void *stream);
+
+/* a6 -- remap of the reference by R_finite (Section 2, Eq. 12 with cubic
+ * interpolation): remapped[b](x') = ref[ref_idx[b]] at the gnomonic
+ * projection of R_finite[b]^T r', Keys cubic convolution (a = -0.5),
+ * replicated borders.  remapped [B][H][W]. */
+int hrebsd_remap(hrebsd_ctx *ctx, const float *ref, const int32_t *ref_idx, const double *R_finite, int B, int H,
+                 int W, const hrebsd_geometry *geom, float *remapped, void *stream);
+
+/* a7 -- second-pass ROI cross-correlation (Section 2).  For each pair and
+ * ROI: zero mean over the ROI, symmetric Hann window if `window`
+ * (0.5 (1 - cos(2 pi n/(S-1)))), c = IFFT(FFT(test) conj(FFT(ref))), i.e.
+ * c(s) = sum_x test(x+s) ref(x); integer peak = first maximum in row-major
+ * order, wrapped to [-S/2, S/2); sub-pixel 3-point parabola per axis.
+ * S in {16, 32, 64, 128}; ROIs must lie inside the image.  Outputs
+ * q [B][N][2] (x, y shift: test(x + q) ~ ref(x)), peak [B][N][2],
+ * peak_height [B][N] (c0 / (|ref_w| |test_w|)), near_tie [B][N] (top two
+ * correlation values within 1e-6 |c0|; may be NULL). */
+int hrebsd_xcf_roi_batch(hrebsd_ctx *ctx, const float *remapped, const float *test, int B, int H, int W,
+                         const int32_t *roi_xy, int N, int S, int window, float *q, int32_t *peak,
+                         float *peak_height, int32_t *near_tie, void *stream);
+
+/* a8 -- second-pass deformation gradient (Eq. 3 on the XCF shifts, Eq. 12):
+ * r_i = c_i, r'_i = c_i + q_i, F_inf by the same FP64 fit as
+ * hrebsd_fit_rotation (det F_inf = 1), F = F_inf R_finite (R_finite may be
+ * NULL: F = F_inf).  F [B][9]; pair_status |= FIT_FAILED on a singular fit
+ * (may be NULL). */
+int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N, int B, int H, int W,
+                   const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HREBSD_H */

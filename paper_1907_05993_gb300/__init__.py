@@ -1,0 +1,207 @@
+"""GB300 (sm_103a) HR-EBSD demons remapping: Python binding of libhrebsd.
+
+The binding marshals arguments only: every step of the method runs in the
+CUDA kernels of ``libhrebsd.so`` behind the C ABI declared in
+``include/hrebsd.h``.  Functions carry the ABI names and take either torch
+CUDA tensors (their ``data_ptr``) or raw device addresses (ints).  A missing
+or unloadable library raises immediately; there is no CPU fallback.
+
+Method: Zhu, Kaufmann & Vecchio, "Novel Remapping Approach for HR-EBSD based
+on Demons Registration" (arXiv 1907.05993).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+__all__ = [
+    "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
+    "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
+    "hrebsd_demons_register_batch", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
+    "hrebsd_solve_F", "hrebsd_profile_enable", "hrebsd_profile_read", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+]
+
+PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
+
+_lib = None
+
+
+class HrebsdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().hrebsd_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} ({status})")
+        self.status = status
+
+
+class hrebsd_geometry(C.Structure):
+    _fields_ = [("xstar", C.c_double), ("ystar", C.c_double), ("zstar", C.c_double)]
+
+
+class hrebsd_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8), ("pixel_iters", C.c_longlong)]
+
+
+PROF_CLASSES = ("demons_iter", "demons_control", "demons_aux", "preprocess", "fit_rotation", "remap", "xcf",
+                "solve_F")
+
+
+class hrebsd_demons_params(C.Structure):
+    _fields_ = [("levels", C.c_int), ("max_iters", C.c_int * 8), ("alpha", C.c_float),
+                ("sigma_update", C.c_float), ("sigma_field", C.c_float), ("stop_tol", C.c_float),
+                ("stop_window", C.c_int), ("start_level", C.c_int)]
+
+
+def demons_params(levels, max_iters, alpha=1.0, sigma_update=1.0, sigma_field=1.0, stop_tol=0.0, stop_window=0,
+                  start_level=-1) -> hrebsd_demons_params:
+    p = hrebsd_demons_params()
+    p.levels = levels
+    caps = list(max_iters) if hasattr(max_iters, "__len__") else [max_iters] * levels
+    for i, c in enumerate(caps):
+        p.max_iters[i] = int(c)
+    p.alpha, p.sigma_update, p.sigma_field = alpha, sigma_update, sigma_field
+    p.stop_tol, p.stop_window, p.start_level = stop_tol, stop_window, start_level
+    return p
+
+
+def load(build: bool = False):
+    """Load libhrebsd.so (building it first if asked or if it is stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build or not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libhrebsd.so not found at {_build.LIB}: run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    vp, i, ll = C.c_void_p, C.c_int, C.c_longlong
+    sig = {
+        "hrebsd_create": (i, [C.POINTER(vp), i]),
+        "hrebsd_destroy": (i, [vp]),
+        "hrebsd_status_string": (C.c_char_p, [i]),
+        "hrebsd_launch_count": (ll, [vp]),
+        "hrebsd_profile_enable": (i, [vp, i]),
+        "hrebsd_profile_read": (i, [vp, C.POINTER(hrebsd_profile)]),
+        "hrebsd_preprocess_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
+        "hrebsd_demons_register_batch": (i, [vp, vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp,
+                                             vp, vp, vp]),
+        "hrebsd_fit_rotation": (i, [vp, vp, i, i, i, vp, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
+        "hrebsd_remap": (i, [vp, vp, vp, vp, i, i, i, C.POINTER(hrebsd_geometry), vp, vp]),
+        "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
+        "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _p(x, dtype=None):
+    """Device address of a torch CUDA tensor, an int address, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor (the library takes device pointers)")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and x.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {x.dtype}")
+    return x.data_ptr()
+
+
+def _s(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _chk(st, where):
+    if st != 0:
+        raise HrebsdError(st, where)
+
+
+def _t():
+    import torch
+    return torch
+
+
+def hrebsd_create(device: int = 0):
+    h = C.c_void_p()
+    _chk(load().hrebsd_create(C.byref(h), device), "hrebsd_create")
+    return h
+
+
+def hrebsd_destroy(ctx):
+    _chk(load().hrebsd_destroy(ctx), "hrebsd_destroy")
+
+
+def hrebsd_status_string(status: int) -> str:
+    return load().hrebsd_status_string(status).decode()
+
+
+def hrebsd_launch_count(ctx) -> int:
+    return int(load().hrebsd_launch_count(ctx))
+
+
+def hrebsd_profile_enable(ctx, enable: bool):
+    _chk(load().hrebsd_profile_enable(ctx, int(enable)), "hrebsd_profile_enable")
+
+
+def hrebsd_profile_read(ctx) -> dict:
+    """Per kernel class: {'ms', 'launches'}, plus 'pixel_iters' (synchronises the device)."""
+    p = hrebsd_profile()
+    _chk(load().hrebsd_profile_read(ctx, C.byref(p)), "hrebsd_profile_read")
+    out = {name: {"ms": p.ms[i], "launches": p.launches[i]} for i, name in enumerate(PROF_CLASSES)}
+    out["pixel_iters"] = p.pixel_iters
+    return out
+
+
+def hrebsd_preprocess_batch(ctx, inp, n, H, W, flat, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_preprocess_batch(ctx, _p(inp, f32), n, H, W, int(flat), _p(out, f32), _s(stream)),
+         "hrebsd_preprocess_batch")
+
+
+def hrebsd_demons_register_batch(ctx, ref, test, ref_idx, R, B, H, W, params, init_field, field, iters,
+                                 pair_status, stream=None):
+    t = _t()
+    _chk(load().hrebsd_demons_register_batch(ctx, _p(ref, t.float32), _p(test, t.float32), _p(ref_idx, t.int32), R,
+                                             B, H, W, C.byref(params), _p(init_field, t.float32),
+                                             _p(field, t.float32), _p(iters, t.int32), _p(pair_status, t.int32),
+                                             _s(stream)), "hrebsd_demons_register_batch")
+
+
+def hrebsd_fit_rotation(ctx, field, B, H, W, roi_xy, N, geom, F_first, R_finite, pair_status, stream=None):
+    t = _t()
+    _chk(load().hrebsd_fit_rotation(ctx, _p(field, t.float32), B, H, W, _p(roi_xy, t.int32), N, C.byref(geom),
+                                    _p(F_first, t.float64), _p(R_finite, t.float64), _p(pair_status, t.int32),
+                                    _s(stream)), "hrebsd_fit_rotation")
+
+
+def hrebsd_remap(ctx, ref, ref_idx, R_finite, B, H, W, geom, remapped, stream=None):
+    t = _t()
+    _chk(load().hrebsd_remap(ctx, _p(ref, t.float32), _p(ref_idx, t.int32), _p(R_finite, t.float64), B, H, W,
+                             C.byref(geom), _p(remapped, t.float32), _s(stream)), "hrebsd_remap")
+
+
+def hrebsd_xcf_roi_batch(ctx, remapped, test, B, H, W, roi_xy, N, S, window, q, peak, peak_height, near_tie,
+                         stream=None):
+    t = _t()
+    _chk(load().hrebsd_xcf_roi_batch(ctx, _p(remapped, t.float32), _p(test, t.float32), B, H, W, _p(roi_xy, t.int32),
+                                     N, S, int(window), _p(q, t.float32), _p(peak, t.int32),
+                                     _p(peak_height, t.float32), _p(near_tie, t.int32), _s(stream)),
+         "hrebsd_xcf_roi_batch")
+
+
+def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, stream=None):
+    t = _t()
+    _chk(load().hrebsd_solve_F(ctx, _p(q, t.float32), _p(roi_xy, t.int32), N, B, H, W, C.byref(geom),
+                               _p(R_finite, t.float64), _p(F, t.float64), _p(pair_status, t.int32), _s(stream)),
+         "hrebsd_solve_F")

@@ -1,0 +1,216 @@
+// Context, workspace and status handling of the HR-EBSD library.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include "internal.cuh"
+
+int hr_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    if (getenv("HREBSD_VERBOSE"))
+        fprintf(stderr, "hrebsd: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? HREBSD_ENOMEM : HREBSD_ECUDA;
+}
+
+int hr_set_device(hrebsd_ctx *ctx)
+{
+    int cur = -1;
+    HR_CHECK(cudaGetDevice(&cur));
+    if (cur != ctx->device) HR_CHECK(cudaSetDevice(ctx->device));
+    return HREBSD_OK;
+}
+
+int hr_ws(hrebsd_ctx *ctx, int slot, size_t bytes, void **out)
+{
+    if (slot < 0 || slot >= 16) return HREBSD_EINVAL;
+    hr_buf &b = ctx->ws[slot];
+    if (b.bytes < bytes) {
+        if (b.ptr) {
+            HR_CHECK(cudaDeviceSynchronize());
+            HR_CHECK(cudaFree(b.ptr));
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        size_t want = bytes + bytes / 8;   // headroom against repeated small growth
+        cudaError_t e = cudaMalloc(&b.ptr, want);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            b.ptr = nullptr;
+            return HREBSD_ENOMEM;
+        }
+        b.bytes = want;
+    }
+    *out = b.ptr;
+    return HREBSD_OK;
+}
+
+int hr_gauss_radius(float sigma)
+{
+    if (!(sigma > 0.0f)) return 0;
+    int r = (int)ceil(3.0 * (double)sigma);
+    return r;
+}
+
+int hr_gauss_taps(float sigma, int rad, float *taps)
+{
+    int r = hr_gauss_radius(sigma);
+    if (r > 6 || r > rad) return -1;
+    for (int k = 0; k <= 2 * rad; ++k) taps[k] = 0.0f;
+    if (r == 0) {
+        taps[rad] = 1.0f;
+        return 0;
+    }
+    double w[13], s = 0.0;
+    for (int k = -r; k <= r; ++k) {
+        w[k + r] = exp(-(double)(k * k) / (2.0 * (double)sigma * (double)sigma));
+        s += w[k + r];
+    }
+    for (int k = -r; k <= r; ++k) taps[rad + k] = (float)(w[k + r] / s);
+    return r;
+}
+
+static cudaEvent_t pool_get(hrebsd_ctx *ctx)
+{
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void hr_prof_begin(hrebsd_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx->prof_on) return;
+    ctx->cur_a = pool_get(ctx);
+    if (ctx->cur_a) cudaEventRecord(ctx->cur_a, st);
+}
+
+void hr_prof_end(hrebsd_ctx *ctx, int cls, cudaStream_t st)
+{
+    if (!ctx->prof_on || !ctx->cur_a) return;
+    cudaEvent_t b = pool_get(ctx);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    ctx->pending.push_back({cls, ctx->cur_a, b});
+    ctx->cur_a = nullptr;
+    // fold completed pairs now and then so that the pending list stays short
+    if (ctx->pending.size() > 4096) {
+        std::vector<hr_pending> keep;
+        for (auto &p : ctx->pending) {
+            float ms = 0.0f;
+            if (cudaEventQuery(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                ctx->prof_ms[p.cls] += ms;
+                ctx->prof_launches[p.cls]++;
+                ctx->pool.push_back(p.a);
+                ctx->pool.push_back(p.b);
+            } else {
+                keep.push_back(p);
+            }
+        }
+        (void)cudaGetLastError();
+        ctx->pending.swap(keep);
+    }
+}
+
+extern "C" {
+
+int hrebsd_profile_enable(hrebsd_ctx *ctx, int enable)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    int st = hr_set_device(ctx);
+    if (st) return st;
+    HR_CHECK(cudaDeviceSynchronize());
+    for (auto &p : ctx->pending) {
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < HREBSD_PROF_CLASSES; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_launches[i] = 0;
+    }
+    if (!ctx->d_pixiters) HR_CHECK(cudaMalloc(&ctx->d_pixiters, sizeof(unsigned long long)));
+    HR_CHECK(cudaMemset(ctx->d_pixiters, 0, sizeof(unsigned long long)));
+    ctx->prof_on = enable ? 1 : 0;
+    return HREBSD_OK;
+}
+
+int hrebsd_profile_read(hrebsd_ctx *ctx, hrebsd_profile *out)
+{
+    if (!ctx || !out) return HREBSD_EINVAL;
+    int st = hr_set_device(ctx);
+    if (st) return st;
+    HR_CHECK(cudaDeviceSynchronize());
+    for (auto &p : ctx->pending) {
+        float ms = 0.0f;
+        HR_CHECK(cudaEventElapsedTime(&ms, p.a, p.b));
+        ctx->prof_ms[p.cls] += ms;
+        ctx->prof_launches[p.cls]++;
+        ctx->pool.push_back(p.a);
+        ctx->pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < HREBSD_PROF_CLASSES; ++i) {
+        out->ms[i] = ctx->prof_ms[i];
+        out->launches[i] = ctx->prof_launches[i];
+    }
+    unsigned long long px = 0;
+    if (ctx->d_pixiters) HR_CHECK(cudaMemcpy(&px, ctx->d_pixiters, sizeof(px), cudaMemcpyDeviceToHost));
+    out->pixel_iters = (long long)px;
+    return HREBSD_OK;
+}
+
+int hrebsd_create(hrebsd_ctx **ctx, int device)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    *ctx = nullptr;
+    int n = 0;
+    HR_CHECK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return HREBSD_EINVAL;
+    HR_CHECK(cudaSetDevice(device));
+    hrebsd_ctx *c = new hrebsd_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return hr_cuda_error(e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
+    }
+    *ctx = c;
+    return HREBSD_OK;
+}
+
+int hrebsd_destroy(hrebsd_ctx *ctx)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    int st = hr_set_device(ctx);
+    cudaDeviceSynchronize();
+    for (auto &b : ctx->ws)
+        if (b.ptr) cudaFree(b.ptr);
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->d_pixiters) cudaFree(ctx->d_pixiters);
+    delete ctx;
+    return st;
+}
+
+const char *hrebsd_status_string(int status)
+{
+    switch (status) {
+    case HREBSD_OK: return "ok";
+    case HREBSD_EINVAL: return "invalid argument";
+    case HREBSD_ECUDA: return "CUDA error";
+    case HREBSD_ENOMEM: return "out of device memory";
+    case HREBSD_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+    }
+}
+
+long long hrebsd_launch_count(const hrebsd_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+}  // extern "C"

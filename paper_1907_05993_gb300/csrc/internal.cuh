@@ -1,0 +1,73 @@
+// Internal declarations of the HR-EBSD CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "hrebsd.h"
+
+#define HR_CHECK(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return hr_cuda_error(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define HR_LAUNCHED(ctx)                                                       \
+    do {                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess) return hr_cuda_error(e_, "kernel launch", __FILE__, __LINE__); \
+        (ctx)->launches++;                                                     \
+    } while (0)
+
+int hr_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// One growable device allocation owned by the context.
+struct hr_buf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+enum { PROF_ITER = 0, PROF_CTRL, PROF_DEMONS_AUX, PROF_PRE, PROF_FIT, PROF_REMAP, PROF_XCF, PROF_SOLVE };
+
+struct hr_pending {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct hrebsd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    long long launches = 0;
+    hr_buf ws[16];   // named workspace slots (see demons.cu)
+    // tracing
+    int prof_on = 0;
+    double prof_ms[HREBSD_PROF_CLASSES] = {};
+    long long prof_launches[HREBSD_PROF_CLASSES] = {};
+    unsigned long long *d_pixiters = nullptr;
+    std::vector<hr_pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t cur_a = nullptr;
+};
+
+// Bracket a launch with events when tracing is on.
+void hr_prof_begin(hrebsd_ctx *ctx, cudaStream_t st);
+void hr_prof_end(hrebsd_ctx *ctx, int cls, cudaStream_t st);
+// Device counter of demons pixel-iterations (NULL when tracing is off).
+static inline unsigned long long *hr_prof_pixiters(hrebsd_ctx *ctx) { return ctx->prof_on ? ctx->d_pixiters : nullptr; }
+
+// Make sure workspace slot `slot` holds at least `bytes`; returns the pointer
+// through *out.  Allocation is synchronous (cudaMalloc) and happens only on
+// growth.
+int hr_ws(hrebsd_ctx *ctx, int slot, size_t bytes, void **out);
+int hr_set_device(hrebsd_ctx *ctx);
+
+static inline cudaStream_t hr_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Gaussian taps as used by the demons field regularisation (radius
+// ceil(3 sigma), weights exp(-k^2/(2 sigma^2)) normalised to one), padded with
+// zeros to radius `rad`.  Returns the natural radius, or -1 if > 6.
+int hr_gauss_taps(float sigma, int rad, float *taps);
+int hr_gauss_radius(float sigma);

@@ -1,0 +1,83 @@
+// a6: remap of the reference pattern by R_finite (Section 2, Eq. 12).
+//
+// Output pixel x' (test frame) looks up the reference at the gnomonic
+// projection of R^T r', r' = (x' - xpc, y' - ypc, Z*): the reference point
+// that Eq. 2 maps onto x' under the pure rotation R.  The value is a Keys
+// (1981) cubic convolution (a = -0.5) over 4x4 reference pixels with
+// replicated borders.  One thread per output pixel; the references (a few
+// grains) are gathered through the read-only path and stay in L2, so HBM
+// traffic is the 4 B written per pixel.
+#include "internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ void keys_weights(float t, float *wt)
+{
+    // taps at offsets -1, 0, 1, 2 of the floor sample; t in [0, 1)
+    const float a = -0.5f;
+    const float s0 = t + 1.0f, s1 = t, s2 = 1.0f - t, s3 = 2.0f - t;
+    wt[0] = ((a * s0 - 5.0f * a) * s0 + 8.0f * a) * s0 - 4.0f * a;
+    wt[1] = ((a + 2.0f) * s1 - (a + 3.0f)) * s1 * s1 + 1.0f;
+    wt[2] = ((a + 2.0f) * s2 - (a + 3.0f)) * s2 * s2 + 1.0f;
+    wt[3] = ((a * s3 - 5.0f * a) * s3 + 8.0f * a) * s3 - 4.0f * a;
+}
+
+__global__ void remap_kernel(const float *__restrict__ ref, const int32_t *__restrict__ ref_idx,
+                             const double *__restrict__ Rf, int B, int H, int W, float xpc, float ypc, float zs,
+                             float *__restrict__ out)
+{
+    const size_t plane = (size_t)H * W;
+    const size_t total = (size_t)B * plane;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / plane);
+        const int rem = (int)(idx - (size_t)b * plane);
+        const int i = rem / W, j = rem - i * W;
+        const double *R = Rf + (size_t)b * 9;
+        const float dx = (float)j + 0.5f - xpc, dy = (float)i + 0.5f - ypc;
+        // v = R^T r'
+        const float v0 = fmaf((float)R[0], dx, fmaf((float)R[3], dy, (float)R[6] * zs));
+        const float v1 = fmaf((float)R[1], dx, fmaf((float)R[4], dy, (float)R[7] * zs));
+        const float v2 = fmaf((float)R[2], dx, fmaf((float)R[5], dy, (float)R[8] * zs));
+        const float iv = zs / v2;
+        const float x = fmaf(v0, iv, xpc - 0.5f), y = fmaf(v1, iv, ypc - 0.5f);
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const int x0 = (int)fx0, y0 = (int)fy0;
+        float wx[4], wy[4];
+        keys_weights(x - fx0, wx);
+        keys_weights(y - fy0, wy);
+        const float *M = ref + (size_t)__ldg(ref_idx + b) * plane;
+        float acc = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int yy = min(max(y0 - 1 + m, 0), H - 1);
+            const float *row = M + (size_t)yy * W;
+            float r = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) r = fmaf(wx[k], __ldg(row + min(max(x0 - 1 + k, 0), W - 1)), r);
+            acc = fmaf(wy[m], r, acc);
+        }
+        out[idx] = acc;
+    }
+}
+
+}  // namespace
+
+extern "C" int hrebsd_remap(hrebsd_ctx *ctx, const float *ref, const int32_t *ref_idx, const double *R_finite, int B,
+                            int H, int W, const hrebsd_geometry *g, float *remapped, void *stream)
+{
+    if (!ctx || !g || B < 0 || H < 2 || W < 2) return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!ref || !ref_idx || !R_finite || !remapped) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    size_t total = (size_t)B * H * W;
+    int grid = (int)((total + 255) / 256);
+    if (grid > ctx->num_sms * 32) grid = ctx->num_sms * 32;
+    hr_prof_begin(ctx, hr_stream(stream));
+    remap_kernel<<<grid, 256, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
+                                                      (float)(g->ystar * H), (float)(g->zstar * W), remapped);
+    hr_prof_end(ctx, PROF_REMAP, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}

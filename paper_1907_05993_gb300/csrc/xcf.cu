@@ -1,0 +1,256 @@
+// a7: second-pass ROI cross-correlation (Section 2).
+//
+// One CTA owns one (pair, ROI).  The two real ROIs (test t, remapped
+// reference r) are zero-meaned, Hann-windowed and packed into one complex
+// array z = t + i r in shared memory, so that a single complex 2-D FFT gives
+// both spectra: T(k) = (Z(k) + conj Z(-k))/2, R(k) = (Z(k) - conj Z(-k))/2i.
+// The cross-power T conj(R) is Hermitian; its inverse FFT is the real
+// correlation c(s) = sum_x t(x+s) r(x).  The FFTs are radix-2 decimation in
+// time over the shared-memory array (a 2-D bit-reversal, then row stages,
+// then column stages), with a twiddle table per CTA.  The peak search is a
+// CTA reduction of (value, first index) pairs by warp shuffles that also
+// keeps the runner-up for the near-tie flag.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+template <int S>
+__device__ __forceinline__ int bitrev(int v)
+{
+    constexpr int LOG = S == 16 ? 4 : S == 32 ? 5 : S == 64 ? 6 : 7;
+    return (int)(__brev((unsigned)v) >> (32 - LOG));
+}
+
+// In-place 2-D FFT of z [S][S] (row-major, row stride S).  sign = -1 forward,
+// +1 inverse (unscaled).  tw[j] = exp(-2 pi i j / S), j < S/2.
+template <int S, int NT>
+__device__ void fft2d(float2 *z, const float2 *tw, int sign)
+{
+    // 2-D bit-reversal permutation
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int y = idx / S, x = idx % S;
+        const int j = bitrev<S>(y) * S + bitrev<S>(x);
+        if (idx < j) {
+            float2 t = z[idx];
+            z[idx] = z[j];
+            z[j] = t;
+        }
+    }
+    __syncthreads();
+    // rows, then columns
+    for (int dim = 0; dim < 2; ++dim) {
+        const int es = dim == 0 ? 1 : S;        // element stride within one transform
+        const int ls = dim == 0 ? S : 1;        // stride between transforms
+        for (int half = 1; half < S; half <<= 1) {
+            const int tstep = S / (2 * half);
+            for (int b = threadIdx.x; b < S * S / 2; b += NT) {
+                const int line = b / (S / 2), bf = b % (S / 2);
+                const int grp = bf / half, j = bf % half;
+                const int i0 = grp * 2 * half + j, i1 = i0 + half;
+                float2 w = tw[j * tstep];
+                if (sign > 0) w.y = -w.y;
+                float2 *p0 = z + line * ls + i0 * es;
+                float2 *p1 = z + line * ls + i1 * es;
+                const float2 v = cmul(*p1, w), u = *p0;
+                *p0 = make_float2(u.x + v.x, u.y + v.y);
+                *p1 = make_float2(u.x - v.x, u.y - v.y);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int NT>
+__device__ float block_sum(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.0f;
+    for (int i = 0; i < NT / 32; ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+// (value, index) ordering: larger value first, then smaller index.
+__device__ __forceinline__ bool better(float v, int i, float bv, int bi) { return v > bv || (v == bv && i < bi); }
+
+template <int S, int NT>
+__global__ void __launch_bounds__(NT) xcf_kernel(const float *__restrict__ rem, const float *__restrict__ test, int B,
+                                                 int H, int W, const int32_t *__restrict__ roi, int N, int window,
+                                                 float *q, int32_t *peak, float *ph, int32_t *near_tie)
+{
+    extern __shared__ float2 z[];                 // [S][S]
+    __shared__ float2 tw[S / 2];
+    __shared__ float win[S];
+    __shared__ float red[NT / 32];
+    __shared__ float rv[NT / 32], rv2[NT / 32];
+    __shared__ int ri[NT / 32];
+
+    const int b = blockIdx.x / N, r = blockIdx.x % N;
+    const int cx = roi[2 * r], cy = roi[2 * r + 1];
+    const int x0 = cx - S / 2, y0 = cy - S / 2;
+    const size_t o = (size_t)blockIdx.x;
+    if (x0 < 0 || y0 < 0 || x0 + S > W || y0 + S > H) {   // ROI outside the image
+        if (threadIdx.x == 0) {
+            q[2 * o] = q[2 * o + 1] = __int_as_float(0x7fc00000);
+            peak[2 * o] = peak[2 * o + 1] = 0;
+            ph[o] = 0.0f;
+            if (near_tie) near_tie[o] = 0;
+        }
+        return;
+    }
+    for (int j = threadIdx.x; j < S / 2; j += NT) {
+        float s, c;
+        sincospif(-2.0f * (float)j / (float)S, &s, &c);
+        tw[j] = make_float2(c, s);
+    }
+    for (int n = threadIdx.x; n < S; n += NT)
+        win[n] = window ? 0.5f * (1.0f - cospif(2.0f * (float)n / (float)(S - 1))) : 1.0f;
+
+    const float *T = test + (size_t)b * H * W + (size_t)y0 * W + x0;
+    const float *Rr = rem + (size_t)b * H * W + (size_t)y0 * W + x0;
+    float st = 0.0f, sr = 0.0f;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int y = idx / S, x = idx % S;
+        const float tv = __ldg(T + (size_t)y * W + x), rv_ = __ldg(Rr + (size_t)y * W + x);
+        z[idx] = make_float2(tv, rv_);
+        st += tv;
+        sr += rv_;
+    }
+    const float mt = block_sum<NT>(st, red) * (1.0f / (S * S));
+    const float mr = block_sum<NT>(sr, red) * (1.0f / (S * S));
+    float nt = 0.0f, nr = 0.0f;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int y = idx / S, x = idx % S;
+        const float wgt = win[y] * win[x];
+        float2 v = z[idx];
+        v.x = (v.x - mt) * wgt;
+        v.y = (v.y - mr) * wgt;
+        z[idx] = v;
+        nt = fmaf(v.x, v.x, nt);
+        nr = fmaf(v.y, v.y, nr);
+    }
+    nt = sqrtf(block_sum<NT>(nt, red));
+    nr = sqrtf(block_sum<NT>(nr, red));   // (block_sum ends with a barrier: z is complete)
+
+    fft2d<S, NT>(z, tw, -1);
+
+    // cross-power P(k) = T(k) conj(R(k)), P(-k) = conj(P(k)); pairs (k, -k) in place
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int ky = idx / S, kx = idx % S;
+        const int m = ((S - ky) & (S - 1)) * S + ((S - kx) & (S - 1));
+        if (idx > m) continue;
+        const float2 zk = z[idx], zm = z[m];
+        const float2 Tk = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 Rk = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        const float2 P = make_float2(Tk.x * Rk.x + Tk.y * Rk.y, Tk.y * Rk.x - Tk.x * Rk.y);
+        z[idx] = P;
+        if (m != idx) z[m] = make_float2(P.x, -P.y);
+    }
+    __syncthreads();
+    fft2d<S, NT>(z, tw, +1);
+
+    // argmax of c = Re(z) / S^2 (first maximum in row-major order) and runner-up
+    const float scale = 1.0f / (float)(S * S);
+    float bv = -INFINITY, bv2 = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const float v = z[idx].x * scale;
+        if (better(v, idx, bv, bi)) {
+            bv2 = bv;
+            bv = v;
+            bi = idx;
+        } else if (v > bv2) {
+            bv2 = v;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const float ov2 = __shfl_xor_sync(0xffffffffu, bv2, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (better(ov, oi, bv, bi)) {
+            bv2 = fmaxf(bv, ov2);
+            bv = ov;
+            bi = oi;
+        } else {
+            bv2 = fmaxf(bv2, ov);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rv[threadIdx.x >> 5] = bv;
+        rv2[threadIdx.x >> 5] = bv2;
+        ri[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = rv[0], v2 = rv2[0];
+        int i = ri[0];
+        for (int k = 1; k < NT / 32; ++k) {
+            if (better(rv[k], ri[k], v, i)) {
+                v2 = fmaxf(v, rv2[k]);
+                v = rv[k];
+                i = ri[k];
+            } else {
+                v2 = fmaxf(v2, rv[k]);
+            }
+        }
+        const int py = i / S, px = i % S;
+        const float c0 = v;
+        const float cxm = z[py * S + ((px + S - 1) & (S - 1))].x * scale;
+        const float cxp = z[py * S + ((px + 1) & (S - 1))].x * scale;
+        const float cym = z[((py + S - 1) & (S - 1)) * S + px].x * scale;
+        const float cyp = z[((py + 1) & (S - 1)) * S + px].x * scale;
+        float dx = 0.0f, dy = 0.0f, den;
+        den = cxm - 2.0f * c0 + cxp;
+        if (den != 0.0f) dx = (cxm - cxp) / (2.0f * den);
+        den = cym - 2.0f * c0 + cyp;
+        if (den != 0.0f) dy = (cym - cyp) / (2.0f * den);
+        const int wx = px >= S / 2 ? px - S : px, wy = py >= S / 2 ? py - S : py;
+        peak[2 * o] = wx;
+        peak[2 * o + 1] = wy;
+        q[2 * o] = (float)wx + dx;
+        q[2 * o + 1] = (float)wy + dy;
+        ph[o] = (nr > 0.0f && nt > 0.0f) ? c0 / (nr * nt) : 0.0f;
+        if (near_tie) near_tie[o] = (c0 - v2) < 1e-6f * fabsf(c0);
+    }
+}
+
+template <int S, int NT>
+int launch_xcf(hrebsd_ctx *ctx, const float *rem, const float *test, int B, int H, int W, const int32_t *roi, int N,
+               int window, float *q, int32_t *peak, float *ph, int32_t *near_tie, cudaStream_t st)
+{
+    const size_t smem = sizeof(float2) * S * S;
+    if (smem > 48 * 1024) HR_CHECK(cudaFuncSetAttribute(xcf_kernel<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    hr_prof_begin(ctx, st);
+    xcf_kernel<S, NT><<<B * N, NT, smem, st>>>(rem, test, B, H, W, roi, N, window, q, peak, ph, near_tie);
+    hr_prof_end(ctx, PROF_XCF, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+}  // namespace
+
+extern "C" int hrebsd_xcf_roi_batch(hrebsd_ctx *ctx, const float *remapped, const float *test, int B, int H, int W,
+                                    const int32_t *roi_xy, int N, int S, int window, float *q, int32_t *peak,
+                                    float *peak_height, int32_t *near_tie, void *stream)
+{
+    if (!ctx || B < 0 || N < 0 || H < 2 || W < 2) return HREBSD_EINVAL;
+    if (S != 16 && S != 32 && S != 64 && S != 128) return HREBSD_EINVAL;
+    if ((long long)B * N > 0x7fffffffLL) return HREBSD_EINVAL;
+    if (B == 0 || N == 0) return HREBSD_OK;
+    if (!remapped || !test || !roi_xy || !q || !peak || !peak_height) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    cudaStream_t st = hr_stream(stream);
+    switch (S) {
+    case 16: return launch_xcf<16, 128>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
+    case 32: return launch_xcf<32, 256>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
+    case 64: return launch_xcf<64, 256>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
+    default: return launch_xcf<128, 512>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
+    }
+}

@@ -1,0 +1,329 @@
+"""CUDA library vs FP64 oracle, through the C ABI, on seeded synthetic patterns.
+
+Per-kernel tests feed both sides identical inputs (produced by the generator
+or by the oracle, rounded to FP32) and compare element by element.  End-to-end
+tests give both sides the same raw patterns and let each run its own chain.
+Tolerances (per pair): displacement field max |d| <= 1e-3 px, rotation
+<= 1e-5 rad, deformation-gradient components <= 1e-6, integer XCF peaks
+bit-exact (ROIs flagged as near ties on either side are excluded and counted).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth import kikuchi as K
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-3
+ROT_TOL = 1e-5
+F_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def lib(torch):
+    import paper_1907_05993_gb300 as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.hrebsd_create(0)
+    yield c
+    lib.hrebsd_destroy(c)
+
+
+def cuda(torch, a, dtype=None):
+    a = np.ascontiguousarray(a)
+    t = torch.from_numpy(a)
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rot_err(Ra, Rb):
+    return math.acos(float(np.clip((np.trace(np.asarray(Ra).T @ np.asarray(Rb)) - 1) / 2, -1, 1)))
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+# ------------------------------------------------------------------ a1
+@pytest.mark.parametrize("H,W,flat", [(128, 128, 1), (256, 256, 1), (100, 72, 1), (64, 48, 0)])
+def test_preprocess_parity(torch, lib, ctx, oracle, H, W, flat):
+    spec = K.ScanSpec(n_pairs=3, H=H, W=W, seed=11)
+    raw = np.stack([K.render_test(spec, p) for p in range(3)]).astype(np.float32)
+    out = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
+    lib.hrebsd_preprocess_batch(ctx, cuda(torch, raw), 3, H, W, flat, out)
+    got = out.cpu().numpy()
+    for i in range(3):
+        exp = oracle.preprocess(raw[i].astype(np.float64), bool(flat))
+        assert np.abs(got[i] - exp).max() < 2e-4
+
+
+def test_preprocess_constant_and_inplace(torch, lib, ctx):
+    x = torch.full((2, 32, 32), 7.0, device="cuda")
+    lib.hrebsd_preprocess_batch(ctx, x, 2, 32, 32, 1, x)
+    assert float(x.abs().max()) == 0.0
+
+
+# ------------------------------------------------------------------ a2-a4 (fixed iterations)
+def _pre_pair(oracle, spec, p, noise=True):
+    r = K.ref_index(spec, p)
+    ref = oracle.preprocess(K.render_ref(spec, r, noise).astype(np.float64), True)
+    test = oracle.preprocess(K.render_test(spec, p, noise).astype(np.float64), True)
+    return f32(ref), f32(test)
+
+
+def _gpu_register(torch, lib, ctx, refs, tests, ridx, params, init=None):
+    R, H, W = refs.shape
+    B = tests.shape[0]
+    field = torch.empty((B, 2, H, W), dtype=torch.float32, device="cuda")
+    iters = torch.empty((B, params.levels), dtype=torch.int32, device="cuda")
+    status = torch.empty((B,), dtype=torch.int32, device="cuda")
+    lib.hrebsd_demons_register_batch(ctx, cuda(torch, refs, torch.float32), cuda(torch, tests, torch.float32),
+                                     cuda(torch, ridx.astype(np.int32)), R, B, H, W, params,
+                                     None if init is None else cuda(torch, init, torch.float32), field, iters, status)
+    torch.cuda.synchronize()
+    return field.cpu().numpy().astype(np.float64), iters.cpu().numpy(), status.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W,levels,caps,sigma", [
+    (64, 64, 1, [30], 1.0),          # single level, 2x2 tiles
+    (96, 80, 2, [20, 20], 1.0),      # ragged tiles (80 = 2.5 tiles of 32)
+    (128, 128, 3, [50, 50, 50], 1.0),  # the single-pair workload
+    (64, 64, 2, [15, 15], 0.0),      # no smoothing (the paper's own setting)
+    (64, 64, 2, [15, 15], 1.6),      # radius 5
+])
+def test_demons_fixed_iterations_parity(torch, lib, ctx, oracle, H, W, levels, caps, sigma):
+    spec = K.ScanSpec(n_pairs=3, H=H, W=W, n_refs=2, mis_lo_deg=0.5, mis_hi_deg=2.5, seed=21)
+    pairs = [_pre_pair(oracle, spec, p) for p in range(3)]
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
+    tests = np.stack([t for _, t in pairs])
+    ridx = np.array([K.ref_index(spec, p) for p in range(3)])
+    params = lib.demons_params(levels, caps, 1.0, sigma, sigma, 0.0, 0)
+    field, iters, status = _gpu_register(torch, lib, ctx, refs, tests, ridx, params)
+    for b in range(3):
+        exp, it = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, 1.0, sigma, sigma)
+        assert list(iters[b]) == list(it) == list(caps)
+        if sigma > 0:
+            assert np.abs(field[b] - exp).max() <= FIELD_TOL, np.abs(field[b] - exp).max()
+        else:   # without regularisation demons diverges in flat regions; compare where it is stable
+            err = np.abs(field[b] - exp)
+            assert np.median(err) <= FIELD_TOL
+    assert np.all((status & lib.PAIR_CAPPED) != 0)
+
+
+def test_identical_pair_zero_field(torch, lib, ctx, oracle):
+    spec = K.ScanSpec(n_pairs=1, H=64, W=64, seed=5)
+    _, t = _pre_pair(oracle, spec, 0)
+    params = lib.demons_params(2, [10, 10], 1.0, 1.0, 1.0)
+    field, iters, status = _gpu_register(torch, lib, ctx, t[None], t[None], np.zeros(1, np.int32), params)
+    assert np.abs(field).max() == 0.0
+
+
+def test_init_field_and_start_level(torch, lib, ctx, oracle):
+    spec = K.ScanSpec(n_pairs=2, H=64, W=64, seed=9, mis_lo_deg=1, mis_hi_deg=2)
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, 0).astype(np.float64)))])
+    tests = np.stack([_pre_pair(oracle, spec, p)[1] for p in range(2)])
+    rng = np.random.default_rng(3)
+    init = f32(rng.normal(0, 0.3, (2, 2, 32, 32)))
+    params = lib.demons_params(3, [8, 8, 8], 1.0, 1.0, 1.0, 0.0, 0, 1)
+    field, iters, _ = _gpu_register(torch, lib, ctx, refs, tests, np.zeros(2, np.int32), params, init)
+    for b in range(2):
+        exp, it = oracle.demons_register(refs[0], tests[b], 3, [8, 8, 8], 1.0, 1.0, 1.0, start_level=1, init=init[b])
+        assert list(iters[b]) == [8, 8, 0] == list(it)
+        assert np.abs(field[b] - exp).max() <= FIELD_TOL
+
+
+def test_stop_rule_agreement(torch, lib, ctx, oracle):
+    """Each side decides its own stop; counts agree within +-1 on >= 90 % of (pair, level)."""
+    spec = K.ScanSpec(n_pairs=8, H=64, W=64, n_refs=2, seed=33, mis_lo_deg=0, mis_hi_deg=4)
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
+    tests = np.stack([_pre_pair(oracle, spec, p)[1] for p in range(8)])
+    ridx = np.array([K.ref_index(spec, p) for p in range(8)])
+    params = lib.demons_params(3, [60, 60, 60], 1.0, 1.0, 1.0, 1e-4, 5)
+    field, iters, status = _gpu_register(torch, lib, ctx, refs, tests, ridx, params)
+    close, same, total = 0, 0, 0
+    for b in range(8):
+        exp, it = oracle.demons_register(refs[ridx[b]], tests[b], 3, [60] * 3, 1.0, 1.0, 1.0, 5, 1e-4)
+        close += int(np.sum(np.abs(np.asarray(it) - iters[b]) <= 1))
+        total += 3
+        if list(it) == list(iters[b]):
+            same += 1
+            assert np.abs(field[b] - exp).max() <= FIELD_TOL
+    assert close >= 0.9 * total and same >= 1
+
+
+# ------------------------------------------------------------------ a5 (same field on both sides)
+def test_fit_rotation_parity(torch, lib, ctx, oracle):
+    H = W = 128
+    geom = K.Geometry()
+    roi = K.roi_grid(H, W, 32, True)
+    rng = np.random.default_rng(7)
+    fields = []
+    for b in range(6):
+        F = K.axis_angle(rng.normal(size=3), math.radians(rng.uniform(0.2, 10))) @ (
+            np.eye(3) + np.diag(rng.normal(0, 5e-4, 3)))
+        Y, X = np.mgrid[0:H, 0:W].astype(float)
+        pts = np.c_[X.ravel() + 0.5 - 64, Y.ravel() + 0.5 - 64, np.full(H * W, 76.8)]
+        v = (np.linalg.inv(F) @ pts.T).T
+        src = 76.8 * v[:, :2] / v[:, 2:3]
+        fields.append((pts[:, :2] - src).T.reshape(2, H, W) + rng.normal(0, 0.05, (2, H, W)))
+    fields = f32(np.stack(fields))
+    B = len(fields)
+    F1 = torch.empty((B, 9), dtype=torch.float64, device="cuda")
+    Rf = torch.empty((B, 9), dtype=torch.float64, device="cuda")
+    st = torch.zeros((B,), dtype=torch.int32, device="cuda")
+    g = lib.hrebsd_geometry(geom.xstar, geom.ystar, geom.zstar)
+    lib.hrebsd_fit_rotation(ctx, cuda(torch, fields, torch.float32), B, H, W, cuda(torch, roi), len(roi), g, F1, Rf, st)
+    F1, Rf = F1.cpu().numpy().reshape(B, 3, 3), Rf.cpu().numpy().reshape(B, 3, 3)
+    for b in range(B):
+        eF, eR = oracle.fit_rotation(fields[b], roi, geom)
+        assert np.abs(F1[b] - eF).max() < 1e-9
+        assert np.abs(Rf[b] - eR).max() < 1e-9
+    assert int(st.abs().max()) == 0
+
+
+# ------------------------------------------------------------------ a6
+def test_remap_parity(torch, lib, ctx, oracle):
+    spec = K.ScanSpec(n_pairs=1, H=128, W=128, n_refs=2, seed=4)
+    geom = spec.geom
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
+    rng = np.random.default_rng(2)
+    Rs = np.stack([K.axis_angle(rng.normal(size=3), math.radians(a)) for a in (0.0, 1.5, 6.0, 12.0)])
+    ridx = np.array([0, 1, 1, 0], np.int32)
+    out = torch.empty((4, 128, 128), dtype=torch.float32, device="cuda")
+    g = lib.hrebsd_geometry(geom.xstar, geom.ystar, geom.zstar)
+    lib.hrebsd_remap(ctx, cuda(torch, refs, torch.float32), cuda(torch, ridx), cuda(torch, Rs.reshape(4, 9)), 4, 128,
+                     128, g, out)
+    got = out.cpu().numpy()
+    for b in range(4):
+        exp = oracle.remap(refs[ridx[b]], Rs[b], geom)
+        assert np.abs(got[b] - exp).max() < 2e-4
+
+
+# ------------------------------------------------------------------ a7
+@pytest.mark.parametrize("H,S,window", [(128, 32, 1), (256, 64, 1), (64, 16, 0), (256, 128, 1)])
+def test_xcf_parity(torch, lib, ctx, oracle, H, S, window):
+    spec = K.ScanSpec(n_pairs=4, H=H, W=H, n_refs=1, seed=17, mis_lo_deg=0.0, mis_hi_deg=0.6)
+    a = np.stack([_pre_pair(oracle, spec, p) for p in range(4)])
+    refs, tests = a[:, 0], a[:, 1]
+    if S == 128:
+        roi = np.array([[128, 128], [100, 140]], np.int32)
+    else:
+        roi = K.roi_grid(H, H, S, False) if S >= 32 else np.array([[16, 16], [32, 40], [48, 24]], np.int32)
+    N = len(roi)
+    B = 4
+    q = torch.empty((B, N, 2), dtype=torch.float32, device="cuda")
+    pk = torch.empty((B, N, 2), dtype=torch.int32, device="cuda")
+    ph = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    tie = torch.empty((B, N), dtype=torch.int32, device="cuda")
+    lib.hrebsd_xcf_roi_batch(ctx, cuda(torch, refs, torch.float32), cuda(torch, tests, torch.float32), B, H, H,
+                             cuda(torch, roi), N, S, window, q, pk, ph, tie)
+    q, pk, ph, tie = q.cpu().numpy(), pk.cpu().numpy(), ph.cpu().numpy(), tie.cpu().numpy().astype(bool)
+    excluded = 0
+    for b in range(B):
+        eq, epk, eph, etie = oracle.xcf_roi(refs[b], tests[b], roi, S, window=bool(window))
+        ok = ~(etie | tie[b])
+        excluded += int((~ok).sum())
+        assert np.array_equal(pk[b][ok], epk[ok])
+        assert np.abs(q[b][ok] - eq[ok]).max() < 2e-3
+        assert np.abs(ph[b][ok] - eph[ok]).max() < 1e-4
+    assert excluded <= B * N // 10
+
+
+def test_xcf_integer_shift_exact(torch, lib, ctx):
+    rng = np.random.default_rng(8)
+    S = 32
+    base = rng.normal(size=(1, S, S)).astype(np.float32)
+    shifted = np.roll(base, (2, -5), axis=(1, 2))
+    q = torch.empty((1, 1, 2), dtype=torch.float32, device="cuda")
+    pk = torch.empty((1, 1, 2), dtype=torch.int32, device="cuda")
+    ph = torch.empty((1, 1), dtype=torch.float32, device="cuda")
+    lib.hrebsd_xcf_roi_batch(ctx, cuda(torch, base), cuda(torch, shifted), 1, S, S, cuda(torch, np.array([[16, 16]], np.int32)),
+                             1, S, 0, q, pk, ph, None)
+    assert tuple(pk.cpu().numpy()[0, 0]) == (-5, 2)
+    assert np.abs(q.cpu().numpy()[0, 0] - [-5, 2]).max() < 1e-4
+    assert abs(float(ph[0, 0]) - 1.0) < 1e-5
+
+
+def test_xcf_roi_outside_image_is_nan(torch, lib, ctx):
+    img = torch.randn((1, 64, 64), device="cuda")
+    q = torch.zeros((1, 1, 2), dtype=torch.float32, device="cuda")
+    pk = torch.zeros((1, 1, 2), dtype=torch.int32, device="cuda")
+    ph = torch.zeros((1, 1), dtype=torch.float32, device="cuda")
+    lib.hrebsd_xcf_roi_batch(ctx, img, img, 1, 64, 64, torch.tensor([[10, 32]], dtype=torch.int32, device="cuda"), 1,
+                             32, 1, q, pk, ph, None)
+    assert bool(torch.isnan(q).all())
+
+
+# ------------------------------------------------------------------ a8
+def test_solve_F_parity(torch, lib, ctx, oracle):
+    H = W = 256
+    geom = K.Geometry()
+    roi = K.roi_grid(H, W, 64, False)
+    rng = np.random.default_rng(5)
+    B = 5
+    q = f32(rng.normal(0, 0.4, (B, len(roi), 2)))
+    Rs = np.stack([K.axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, 12))) for _ in range(B)])
+    F = torch.empty((B, 9), dtype=torch.float64, device="cuda")
+    g = lib.hrebsd_geometry(geom.xstar, geom.ystar, geom.zstar)
+    lib.hrebsd_solve_F(ctx, cuda(torch, q, torch.float32), cuda(torch, roi), len(roi), B, H, W, g,
+                       cuda(torch, Rs.reshape(B, 9)), F, None)
+    F = F.cpu().numpy().reshape(B, 3, 3)
+    for b in range(B):
+        assert np.abs(F[b] - oracle.solve_F(q[b], roi, H, W, geom, Rs[b])).max() < 1e-10
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_batch_and_bad_args(torch, lib, ctx):
+    p = lib.demons_params(2, [5, 5])
+    lib.hrebsd_demons_register_batch(ctx, 0, 0, 0, 1, 0, 64, 64, p, None, 0, 0, 0)   # B = 0: no-op
+    with pytest.raises(lib.HrebsdError):
+        lib.hrebsd_demons_register_batch(ctx, 0, 0, 0, 1, 1, 60, 64, lib.demons_params(4, [5] * 4), None, 0, 0, 0)
+    with pytest.raises(lib.HrebsdError):
+        lib.hrebsd_xcf_roi_batch(ctx, 0, 0, 1, 64, 64, 0, 1, 48, 1, 0, 0, 0, None)
+
+
+def test_nonfinite_input_flagged(torch, lib, ctx, oracle):
+    spec = K.ScanSpec(n_pairs=2, H=64, W=64, seed=6)
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, 0).astype(np.float64)))])
+    tests = np.stack([_pre_pair(oracle, spec, p)[1] for p in range(2)])
+    tests[1, 10, 10] = np.nan
+    params = lib.demons_params(2, [5, 5])
+    field, iters, status = _gpu_register(torch, lib, ctx, refs, tests, np.zeros(2, np.int32), params)
+    assert (status[1] & lib.PAIR_NONFINITE) and not (status[0] & lib.PAIR_NONFINITE)
+    assert np.isfinite(field[0]).all()
+
+
+# ------------------------------------------------------------------ end to end
+def test_pipeline_single_pair_workload(torch, lib, oracle):
+    """The single-pair workload (128x128, 3 levels x 50, 21 ROIs of 32x32): both sides from raw patterns."""
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    spec = K.config1()
+    refs, tests, ridx, Ft = K.make_scan(spec)
+    roi = K.roi_grid(128, 128, 32, True)
+    pipe = Pipeline(PipelineConfig(128, 128, roi, 32, 3, (50, 50, 50)))
+    out = pipe.run(cuda(torch, refs), cuda(torch, tests), cuda(torch, ridx))
+    torch.cuda.synchronize()
+    exp = oracle.pipeline(refs[0].astype(np.float64), tests[0].astype(np.float64), roi, 32, spec.geom, 3, [50] * 3)
+    field = out["field"].cpu().numpy()[0]
+    assert np.abs(field - exp["field"]).max() <= FIELD_TOL
+    Rg = out["R_finite"].cpu().numpy().reshape(3, 3)
+    assert rot_err(Rg, exp["R_finite"]) <= ROT_TOL
+    Fg = out["F"].cpu().numpy().reshape(3, 3)
+    assert np.abs(Fg - exp["F"]).max() <= F_TOL
+    tie = out["near_tie"].cpu().numpy()[0].astype(bool) | exp["near_tie"]
+    assert np.array_equal(out["peak"].cpu().numpy()[0][~tie], exp["peak"][~tie])
+    pipe.close()
