@@ -74,9 +74,10 @@ __device__ __forceinline__ float bilinear_clamped(const float *__restrict__ M, i
     float fx = x - (float)x0, fy = y - (float)y0;
     const float *p = M + (size_t)y0 * w + x0;
     float a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + w), d = __ldg(p + w + 1);
-    float top = fmaf(fx, b - a, a);
-    float bot = fmaf(fx, d - c, c);
-    return fmaf(fy, bot - top, top);
+    // (1 - f) a + f b: exact at both nodes (f = 0 and f = 1)
+    float top = fmaf(fx, b, (1.0f - fx) * a);
+    float bot = fmaf(fx, d, (1.0f - fx) * c);
+    return fmaf(fy, bot, (1.0f - fy) * top);
 }
 
 template <int RAD>

@@ -166,9 +166,9 @@ __device__ float bilinear_clamped(const float *M, int h, int w, float x, float y
     int y0 = min((int)floorf(y), h - 2);
     float fx = x - (float)x0, fy = y - (float)y0;
     const float *p = M + (size_t)y0 * w + x0;
-    float top = fmaf(fx, p[1] - p[0], p[0]);
-    float bot = fmaf(fx, p[w + 1] - p[w], p[w]);
-    return fmaf(fy, bot - top, top);
+    float top = fmaf(fx, p[1], (1.0f - fx) * p[0]);
+    float bot = fmaf(fx, p[w + 1], (1.0f - fx) * p[w]);
+    return fmaf(fy, bot, (1.0f - fy) * top);
 }
 
 __device__ void set_identity(double *M)
