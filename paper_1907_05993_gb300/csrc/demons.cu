@@ -1,26 +1,30 @@
 // a2-a4, a9: batched multi-resolution demons registration (Section 1, Eq. 1).
 //
-// Data layout (HBM): every buffer is pair-major, [B][h][w] for images and
-// [B][2][h][w] for fields (x plane, then y plane), so that a tile of one pair
-// is a set of contiguous row segments.  The reference pyramid ([R][h][w],
-// R <= a few grains) is small and stays in L2; the per-pair test pyramid and
-// the field buffers stream from HBM.
+// Data layout (HBM): every buffer is pair-major.  Images are [B][h][w]
+// FP32; the internal field buffers are [B][h][w] float2 (u_x, u_y
+// interleaved), so that one 8-byte access moves both components and the two
+// planes of every stencil run through packed FP32x2 FMAs.  The caller's
+// field is the planar [B][2][h][w] of the ABI; only the last step writes it.
+// The reference pyramid ([R][h][w], a few grains) is small and stays in L2;
+// the per-pair test pyramid and the field buffers stream from HBM.
 //
 // One demons iteration u_{k+1} = G_f * (u_k + G_u * du(u_k)) is ONE fused
-// kernel launch over every (active pair, tile).  The launch stores the
+// kernel launch over every (active pair, 64x32 tile).  The launch stores the
 // unsmoothed field s_{k+1} = u_k + G_u * du(u_k) instead of u_{k+1}; the next
 // launch recomputes u_{k+1} = G_f * s_{k+1} on the fly from a tile with a
 // 2r halo (r the Gaussian radius).  This keeps the expensive part (warp +
-// force) on a halo of r instead of 2r and costs one smoothing pass that would
-// otherwise be a separate read+write of the field.  Per pixel-iteration the
-// kernel reads the test image (4 B) and s (8 B) and writes s (8 B); the
-// bilinear gathers of the moving image hit the L2-resident reference pyramid.
+// force) on a halo of r instead of 2r and saves a separate smoothing pass.
+// Per pixel-iteration HBM sees the test image (4 B) and s (8 B) read and s
+// (8 B) written; the bilinear gathers of the moving image hit the
+// L2-resident reference pyramid.  The separable passes keep a sliding window
+// of RUN + 2r samples per thread in registers (RUN outputs per thread) and
+// use packed FP32x2 FMAs for the two field components.
 //
 // Border handling: every Gaussian pass has replicated borders.  Tiles load s
 // with clamped addresses (so out-of-image halo values are the replicated
 // ones) and evaluate the force at the clamped position of every halo point;
 // with that, every value the passes read at an in-image position is exact, and
-// out-of-image values are never consumed.
+// out-of-image values are never consumed by an in-image output.
 //
 // Uneven work (a9): pairs stop independently (stop rule on the SSD history).
 // A small control kernel after each iteration compacts the list of active
@@ -35,10 +39,16 @@ int hr_launch_reduce2(hrebsd_ctx *ctx, const float *in, float *out, int n, int H
 
 namespace {
 
-constexpr int TX = 32;
-constexpr int TY = 32;
+constexpr int TX = 64;           // tile width (outputs)
+constexpr int TY = 32;           // tile height
+constexpr int RUN = 8;           // outputs per thread in a separable pass
 constexpr int kIterThreads = 256;
 constexpr int kMaxRad = 6;
+
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+// Row stride (in float2) with an odd number of 16-byte slots, so that float4
+// accesses of consecutive rows by consecutive threads hit distinct banks.
+__host__ __device__ constexpr int pad_stride(int n) { return (n % 4 == 2) ? n : n + 2; }
 
 struct Taps {
     float up[2 * kMaxRad + 1];   // G_u (update smoothing), centred at index RAD
@@ -49,8 +59,8 @@ struct IterArgs {
     const float *Ftest;      // test level images [B][h][w]
     const float *Mref;       // reference level images [R][h][w]
     const int *ref_idx;      // [B]
-    const float *in;         // k == 0: u_0 [B][2][h][w]; k > 0: s_k
-    float *out;              // s_{k+1}
+    const float2 *in;        // k == 0: u_0 [B][h][w]; k > 0: s_k
+    float2 *out;             // s_{k+1}
     float *part;             // SSD partials [B][tiles]
     const int *active;       // active pair list
     const int *n_active;     // its length
@@ -64,46 +74,151 @@ struct IterArgs {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// Bilinear sample of M at index coordinates (x, y), clamped to the image.
+// Bilinear sample of M at index coordinates (x, y), clamped to the image;
+// (1 - f) a + f b per axis, exact at the nodes.
 __device__ __forceinline__ float bilinear_clamped(const float *__restrict__ M, int h, int w, float x, float y)
 {
     x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
     y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
-    int x0 = min((int)floorf(x), w - 2);
-    int y0 = min((int)floorf(y), h - 2);
+    int x0 = min((int)x, w - 2);   // x >= 0: truncation is floor
+    int y0 = min((int)y, h - 2);
     float fx = x - (float)x0, fy = y - (float)y0;
-    const float *p = M + (size_t)y0 * w + x0;
+    const float *p = M + y0 * w + x0;
     float a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + w), d = __ldg(p + w + 1);
-    // (1 - f) a + f b: exact at both nodes (f = 0 and f = 1)
     float top = fmaf(fx, b, (1.0f - fx) * a);
     float bot = fmaf(fx, d, (1.0f - fx) * c);
     return fmaf(fy, bot, (1.0f - fy) * top);
 }
 
+__device__ __forceinline__ float2 bilinear2_clamped(const float2 *__restrict__ M, int h, int w, float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    int x0 = min((int)x, w - 2);
+    int y0 = min((int)y, h - 2);
+    float fx = x - (float)x0, fy = y - (float)y0;
+    const float2 *p = M + y0 * w + x0;
+    float2 a = p[0], b = p[1], c = p[w], d = p[w + 1];
+    float2 top = make_float2(fmaf(fx, b.x, (1.0f - fx) * a.x), fmaf(fx, b.y, (1.0f - fx) * a.y));
+    float2 bot = make_float2(fmaf(fx, d.x, (1.0f - fx) * c.x), fmaf(fx, d.y, (1.0f - fx) * c.y));
+    return make_float2(fmaf(fy, bot.x, (1.0f - fy) * top.x), fmaf(fy, bot.y, (1.0f - fy) * top.y));
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <int RAD>
-struct IterSmem {
-    static constexpr int AW = TX + 4 * RAD, AH = TY + 4 * RAD;   // s tile (T + 2r halo)
-    static constexpr int BW = TX + 2 * RAD, BH = TY + 2 * RAD;   // u, du (T + r halo)
-    static constexpr int FW = BW + 2, FH = BH + 2;               // test image (T + r + 1)
-    static constexpr int A_ELEMS = 2 * (AW * AH > BW * BH ? AW * AH : BW * BH);
-    static constexpr int X_ELEMS = 2 * (AH * BW > BH * TX ? AH * BW : BH * TX);
-    static constexpr int U_ELEMS = 2 * BW * BH;
-    static constexpr int F_ELEMS = FW * FH;
-    static constexpr int TOTAL = A_ELEMS + X_ELEMS + U_ELEMS + F_ELEMS;
+struct Geo {
+    static constexpr int BW = TX + 2 * RAD, BH = TY + 2 * RAD;       // u and du (T + r)
+    static constexpr int BWP = round_up(BW, RUN), BHP = round_up(BH, RUN);
+    static constexpr int AW = TX + 4 * RAD, AH = TY + 4 * RAD;       // s (T + 2r)
+    static constexpr int AHP = BHP + 2 * RAD;                        // rows read by padded y-pass runs
+    static constexpr int AST = pad_stride(BWP + 2 * RAD);            // s tile row stride (>= AW)
+    static constexpr int XST = pad_stride(BWP);                      // x-pass of s row stride
+    static constexpr int UST = BWP;                                  // u row stride
+    static constexpr int DST = pad_stride(BWP);                      // du row stride
+    static constexpr int XDST = pad_stride(TX);                      // x-pass of du row stride
+    static constexpr int FW = BW + 2, FH = BH + 2;                   // test image (T + r + 1)
+    static constexpr int SA = (AHP * AST > BH * DST) ? AHP * AST : BH * DST;   // float2
+    static constexpr int SX = (AHP * XST > BH * XDST) ? AHP * XST : BH * XDST; // float2
+    static constexpr int SU = BHP * UST;                                        // float2
+    static constexpr int SF = FH * FW;                                          // float
+    static constexpr size_t BYTES = (size_t)(SA + SX + SU) * 8 + (size_t)SF * 4;
 };
 
+// Separable pass over a run of RUN outputs along a row (x pass) of float2
+// data: out[o] = sum_k t[k] in[o + k], k = 0..2r.  `in` and `out` 16-byte aligned.
 template <int RAD>
-__global__ void __launch_bounds__(kIterThreads) demons_iter_kernel(IterArgs a)
+__device__ __forceinline__ void run_x(const float2 *in, float2 *out, const float2 (&t)[2 * RAD + 1])
 {
-    using L = IterSmem<RAD>;
-    extern __shared__ float sm[];
-    float *bufA = sm;                        // s tile, later du
-    float *bufX = bufA + L::A_ELEMS;         // x-pass results
-    float *bufU = bufX + L::X_ELEMS;         // u on T + r
-    float *bufF = bufU + L::U_ELEMS;         // test image on T + r + 1
-    __shared__ float red[kIterThreads / 32];
+    constexpr int NW = RUN + 2 * RAD;
+    float2 win[NW];
+    const float4 *in4 = reinterpret_cast<const float4 *>(in);
+#pragma unroll
+    for (int j = 0; j < NW / 2; ++j) {
+        float4 v = in4[j];
+        win[2 * j] = make_float2(v.x, v.y);
+        win[2 * j + 1] = make_float2(v.z, v.w);
+    }
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+#pragma unroll
+    for (int o = 0; o < RUN; o += 2) {
+        float2 a0 = __fmul2_rn(t[0], win[o]);
+        float2 a1 = __fmul2_rn(t[0], win[o + 1]);
+#pragma unroll
+        for (int k = 1; k <= 2 * RAD; ++k) {
+            a0 = ffma2(t[k], win[o + k], a0);
+            a1 = ffma2(t[k], win[o + 1 + k], a1);
+        }
+        out4[o / 2] = make_float4(a0.x, a0.y, a1.x, a1.y);
+    }
+}
 
-    const int tid = threadIdx.x;
+// Same along a column: in[j * stride], j = 0..RUN + 2r - 1 -> acc[o].
+template <int RAD>
+__device__ __forceinline__ void run_y(const float2 *in, int stride, const float2 (&t)[2 * RAD + 1], float2 (&acc)[RUN])
+{
+    constexpr int NW = RUN + 2 * RAD;
+    float2 win[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) win[j] = in[j * stride];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o) {
+        float2 v = __fmul2_rn(t[0], win[o]);
+#pragma unroll
+        for (int k = 1; k <= 2 * RAD; ++k) v = ffma2(t[k], win[o + k], v);
+        acc[o] = v;
+    }
+}
+
+// One item of work: a tile of one active pair.
+struct TileRef {
+    int pair, tile, x0, y0;
+};
+
+__device__ __forceinline__ TileRef tile_of(const IterArgs &a, long long item)
+{
+    TileRef t;
+    t.pair = a.active[item / a.tiles];
+    t.tile = (int)(item % a.tiles);
+    t.x0 = (t.tile % a.tiles_x) * TX;
+    t.y0 = (t.tile / a.tiles_x) * TY;
+    return t;
+}
+
+// IN_S: the input is s (k > 0) and u = G_f * s is formed from an s tile with a
+// 2r halo; otherwise the input is u itself (first iteration of a level).
+// The input and test-image tiles of the NEXT item are loaded into registers
+// while the current item is computed (register-staged prefetch), so their
+// latency overlaps the passes instead of stalling the CTA.
+template <int RAD, bool IN_S>
+__global__ void __launch_bounds__(kIterThreads, 2) demons_iter_kernel(IterArgs a)
+{
+    using L = Geo<RAD>;
+    constexpr int NT = kIterThreads;
+    constexpr bool SMOOTH_IN = IN_S && RAD > 0;
+    constexpr int IW = SMOOTH_IN ? L::AW : L::BW;     // input tile columns
+    constexpr int IH = SMOOTH_IN ? L::AH : L::BH;     // input tile rows
+    constexpr int IOFF = SMOOTH_IN ? 2 * RAD : RAD;   // input tile halo
+    constexpr int IST = SMOOTH_IN ? L::AST : L::UST;  // its shared-memory row stride
+    constexpr int NIN = IW * IH, NPI = (NIN + NT - 1) / NT;
+    constexpr int NF = L::FW * L::FH, NPF = (NF + NT - 1) / NT;
+    constexpr int NPTS = L::BW * L::BH;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float2 *sA = reinterpret_cast<float2 *>(smraw);   // s tile, later du
+    float2 *sX = sA + L::SA;                          // x-pass results
+    float2 *sU = sX + L::SX;                          // u on T + r
+    float *sF = reinterpret_cast<float *>(sU + L::SU);   // test image on T + r + 1
+    float2 *sIn = SMOOTH_IN ? sA : sU;
+    __shared__ float red[NT / 32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 tf[2 * RAD + 1], tu[2 * RAD + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * RAD; ++k) {
+        tf[k] = make_float2(a.taps.f[k], a.taps.f[k]);
+        tu[k] = make_float2(a.taps.up[k], a.taps.up[k]);
+    }
     const int n_active = *a.n_active;
     if (blockIdx.x == 0 && tid == 0) {
         *a.n_next_reset = 0;
@@ -113,142 +228,144 @@ __global__ void __launch_bounds__(kIterThreads) demons_iter_kernel(IterArgs a)
     const int h = a.h, w = a.w;
     const size_t plane = (size_t)h * w;
 
-    for (long long item = blockIdx.x; item < work; item += gridDim.x) {
-        const int pair = a.active[item / a.tiles];
-        const int tile = (int)(item % a.tiles);
-        const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
-        const float *Fimg = a.Ftest + (size_t)pair * plane;
-        const float *M = a.Mref + (size_t)__ldg(a.ref_idx + pair) * plane;
-        const float *src = a.in + (size_t)pair * 2 * plane;
+    float2 pin[NPI];
+    float pf[NPF];
+    auto fetch = [&](const TileRef &t) {
+        const float2 *src = a.in + (size_t)t.pair * plane;
+        const float *Fimg = a.Ftest + (size_t)t.pair * plane;
+#pragma unroll
+        for (int j = 0; j < NPI; ++j) {
+            const int idx = tid + j * NT;
+            if (idx < NIN) {
+                const int r = idx / IW, c = idx - r * IW;
+                const int gy = clampi(t.y0 - IOFF + r, 0, h - 1), gx = clampi(t.x0 - IOFF + c, 0, w - 1);
+                pin[j] = __ldg(src + (size_t)gy * w + gx);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            const int idx = tid + j * NT;
+            if (idx < NF) {
+                const int r = idx / L::FW, c = idx - r * L::FW;
+                const int gy = clampi(t.y0 - RAD - 1 + r, 0, h - 1), gx = clampi(t.x0 - RAD - 1 + c, 0, w - 1);
+                pf[j] = __ldg(Fimg + (size_t)gy * w + gx);
+            }
+        }
+    };
+    auto commit = [&]() {
+#pragma unroll
+        for (int j = 0; j < NPI; ++j) {
+            const int idx = tid + j * NT;
+            if (idx < NIN) {
+                const int r = idx / IW, c = idx - r * IW;
+                sIn[r * IST + c] = pin[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            const int idx = tid + j * NT;
+            if (idx < NF) sF[idx] = pf[j];
+        }
+    };
 
-        // ---- test image on T + r + 1 (clamped addresses)
-        for (int idx = tid; idx < L::FW * L::FH; idx += kIterThreads) {
-            int ly = idx / L::FW, lx = idx - ly * L::FW;
-            int gy = clampi(y0 - RAD - 1 + ly, 0, h - 1), gx = clampi(x0 - RAD - 1 + lx, 0, w - 1);
-            bufF[idx] = __ldg(Fimg + (size_t)gy * w + gx);
-        }
-        if (a.in_is_s && RAD > 0) {
-            // ---- s on T + 2r, then u = G_f * s on T + r (x pass, y pass)
-            for (int idx = tid; idx < L::AW * L::AH; idx += kIterThreads) {
-                int ly = idx / L::AW, lx = idx - ly * L::AW;
-                int gy = clampi(y0 - 2 * RAD + ly, 0, h - 1), gx = clampi(x0 - 2 * RAD + lx, 0, w - 1);
-                size_t g = (size_t)gy * w + gx;
-                bufA[idx] = __ldg(src + g);
-                bufA[L::AW * L::AH + idx] = __ldg(src + plane + g);
+    long long item = blockIdx.x;
+    if (item < work) {
+        fetch(tile_of(a, item));
+        commit();
+    }
+    for (; item < work; item += gridDim.x) {
+        __syncthreads();   // the tiles of `item` are in shared memory
+        const TileRef cur = tile_of(a, item);
+        const long long next = item + gridDim.x;
+        if (next < work) fetch(tile_of(a, next));   // in flight during this item
+        const int x0 = cur.x0, y0 = cur.y0;
+        const float *M = a.Mref + (size_t)__ldg(a.ref_idx + cur.pair) * plane;
+
+        if (SMOOTH_IN) {
+            // ---- u = G_f * s on T + r: x pass (rows of T + 2r), then y pass
+            constexpr int NSX = L::BWP / RUN;
+            for (int it = tid; it < NSX * L::AHP; it += NT) {
+                const int seg = it / L::AHP, row = it - seg * L::AHP;
+                run_x<RAD>(sA + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
             }
             __syncthreads();
-            for (int idx = tid; idx < L::AH * L::BW; idx += kIterThreads) {
-                int ly = idx / L::BW, lx = idx - ly * L::BW;
-                const float *r0 = bufA + ly * L::AW + lx;
-                const float *r1 = r0 + L::AW * L::AH;
-                float s0 = 0.0f, s1 = 0.0f;
+            constexpr int NSY = L::BHP / RUN;
+            for (int it = tid; it < NSY * L::BWP; it += NT) {
+                const int seg = it / L::BWP, col = it - seg * L::BWP;
+                float2 acc[RUN];
+                run_y<RAD>(sX + seg * RUN * L::XST + col, L::XST, tf, acc);
 #pragma unroll
-                for (int k = 0; k <= 2 * RAD; ++k) {
-                    s0 = fmaf(a.taps.f[k], r0[k], s0);
-                    s1 = fmaf(a.taps.f[k], r1[k], s1);
-                }
-                bufX[idx] = s0;
-                bufX[L::AH * L::BW + idx] = s1;
+                for (int o = 0; o < RUN; ++o) sU[(seg * RUN + o) * L::UST + col] = acc[o];
             }
             __syncthreads();
-            for (int idx = tid; idx < L::BH * L::BW; idx += kIterThreads) {
-                int ly = idx / L::BW, lx = idx - ly * L::BW;
-                const float *c0 = bufX + ly * L::BW + lx;
-                const float *c1 = c0 + L::AH * L::BW;
-                float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-                for (int k = 0; k <= 2 * RAD; ++k) {
-                    s0 = fmaf(a.taps.f[k], c0[k * L::BW], s0);
-                    s1 = fmaf(a.taps.f[k], c1[k * L::BW], s1);
-                }
-                bufU[idx] = s0;
-                bufU[L::BW * L::BH + idx] = s1;
-            }
-        } else {
-            // ---- u itself on T + r (first iteration of a level, or no field smoothing)
-            for (int idx = tid; idx < L::BW * L::BH; idx += kIterThreads) {
-                int ly = idx / L::BW, lx = idx - ly * L::BW;
-                int gy = clampi(y0 - RAD + ly, 0, h - 1), gx = clampi(x0 - RAD + lx, 0, w - 1);
-                size_t g = (size_t)gy * w + gx;
-                bufU[idx] = __ldg(src + g);
-                bufU[L::BW * L::BH + idx] = __ldg(src + plane + g);
-            }
         }
-        __syncthreads();
 
         // ---- warp + force at the clamped position of every point of T + r
         float ssd = 0.0f;
-        float *du0 = bufA, *du1 = bufA + L::BW * L::BH;
-        for (int idx = tid; idx < L::BW * L::BH; idx += kIterThreads) {
-            int ly = idx / L::BW, lx = idx - ly * L::BW;
-            int vy = y0 - RAD + ly, vx = x0 - RAD + lx;
-            int qy = clampi(vy, 0, h - 1), qx = clampi(vx, 0, w - 1);
-            int qly = qy - (y0 - RAD), qlx = qx - (x0 - RAD);   // local (B) coordinates of q
-            float ux = bufU[qly * L::BW + qlx], uy = bufU[L::BW * L::BH + qly * L::BW + qlx];
-            const float *fc = bufF + (qly + 1) * L::FW + (qlx + 1);
-            int xl = max(qx - 1, 0) - qx, xr = min(qx + 1, w - 1) - qx;
-            int yl = max(qy - 1, 0) - qy, yr = min(qy + 1, h - 1) - qy;
-            float gx = (fc[xr] - fc[xl]) * ((xr - xl) == 2 ? 0.5f : 1.0f);
-            float gy = (fc[yr * L::FW] - fc[yl * L::FW]) * ((yr - yl) == 2 ? 0.5f : 1.0f);
-            float mw = bilinear_clamped(M, h, w, (float)qx - ux, (float)qy - uy);
-            float d = mw - fc[0];
-            float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
-            float dx = 0.0f, dy = 0.0f;
-            if (den > 1e-9f) {
-                float t = d / den;
-                dx = t * gx;
-                dy = t * gy;
-            }
-            du0[idx] = dx;
-            du1[idx] = dy;
-            if (vy == qy && vx == qx && ly >= RAD && ly < RAD + TY && lx >= RAD && lx < RAD + TX)
-                ssd = fmaf(d, d, ssd);
+        float2 *sD = sA;
+        auto force = [&](int idx, float2 &du, float &d2) {
+            const int r = idx / L::BW, c = idx - r * L::BW;
+            const int vy = y0 - RAD + r, vx = x0 - RAD + c;
+            const int qy = clampi(vy, 0, h - 1), qx = clampi(vx, 0, w - 1);
+            const int qly = qy - (y0 - RAD), qlx = qx - (x0 - RAD);
+            const float2 u = sU[qly * L::UST + qlx];
+            const float *fc = sF + (qly + 1) * L::FW + (qlx + 1);
+            const int xl = qx > 0 ? -1 : 0, xr = qx < w - 1 ? 1 : 0;
+            const int yl = qy > 0 ? -L::FW : 0, yr = qy < h - 1 ? L::FW : 0;
+            const float gx = (fc[xr] - fc[xl]) * ((xr - xl) == 2 ? 0.5f : 1.0f);
+            const float gy = (fc[yr] - fc[yl]) * ((yr - yl) == 2 * L::FW ? 0.5f : 1.0f);
+            const float mw = bilinear_clamped(M, h, w, (float)qx - u.x, (float)qy - u.y);
+            const float d = mw - fc[0];
+            const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
+            const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
+            du = make_float2(t * gx, t * gy);
+            const bool in_T = r >= RAD && r < RAD + TY && c >= RAD && c < RAD + TX && vy < h && vx < w;
+            d2 = in_T ? d * d : 0.0f;
+        };
+        for (int i0 = tid; i0 < NPTS; i0 += 2 * NT) {
+            const int i1 = i0 + NT;
+            float2 du0, du1 = make_float2(0.0f, 0.0f);
+            float e0, e1 = 0.0f;
+            force(i0, du0, e0);
+            if (i1 < NPTS) force(i1, du1, e1);
+            sD[(i0 / L::BW) * L::DST + i0 % L::BW] = du0;
+            if (i1 < NPTS) sD[(i1 / L::BW) * L::DST + i1 % L::BW] = du1;
+            ssd += e0 + e1;
         }
         __syncthreads();
         // ---- G_u * du: x pass on rows of T + r, columns of T
-        for (int idx = tid; idx < L::BH * TX; idx += kIterThreads) {
-            int ly = idx / TX, lx = idx - ly * TX;
-            const float *r0 = du0 + ly * L::BW + lx;
-            const float *r1 = du1 + ly * L::BW + lx;
-            float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-            for (int k = 0; k <= 2 * RAD; ++k) {
-                s0 = fmaf(a.taps.up[k], r0[k], s0);
-                s1 = fmaf(a.taps.up[k], r1[k], s1);
-            }
-            bufX[idx] = s0;
-            bufX[L::BH * TX + idx] = s1;
+        constexpr int NSXD = TX / RUN;
+        for (int it = tid; it < NSXD * L::BH; it += NT) {
+            const int seg = it / L::BH, row = it - seg * L::BH;
+            run_x<RAD>(sD + row * L::DST + seg * RUN, sX + row * L::XDST + seg * RUN, tu);
         }
         __syncthreads();
         // ---- y pass, s_{k+1} = u_k + G_u * du on T
-        float *dst = a.out + (size_t)pair * 2 * plane;
-        for (int idx = tid; idx < TY * TX; idx += kIterThreads) {
-            int ly = idx / TX, lx = idx - ly * TX;
-            int gy = y0 + ly, gx = x0 + lx;
-            if (gy >= h || gx >= w) continue;
-            const float *c0 = bufX + ly * TX + lx;
-            const float *c1 = c0 + L::BH * TX;
-            float s0 = 0.0f, s1 = 0.0f;
+        float2 *dst = a.out + (size_t)cur.pair * plane;
+        for (int it = tid; it < (TY / RUN) * TX; it += NT) {
+            const int seg = it / TX, col = it - seg * TX;
+            float2 acc[RUN];
+            run_y<RAD>(sX + seg * RUN * L::XDST + col, L::XDST, tu, acc);
+            const int gx = x0 + col;
 #pragma unroll
-            for (int k = 0; k <= 2 * RAD; ++k) {
-                s0 = fmaf(a.taps.up[k], c0[k * TX], s0);
-                s1 = fmaf(a.taps.up[k], c1[k * TX], s1);
+            for (int o = 0; o < RUN; ++o) {
+                const int gy = y0 + seg * RUN + o;
+                if (gy < h && gx < w) {
+                    const float2 u = sU[(seg * RUN + o + RAD) * L::UST + col + RAD];
+                    dst[(size_t)gy * w + gx] = __fadd2_rn(u, acc[o]);
+                }
             }
-            int u_idx = (ly + RAD) * L::BW + lx + RAD;
-            size_t g = (size_t)gy * w + gx;
-            dst[g] = bufU[u_idx] + s0;
-            dst[plane + g] = bufU[L::BW * L::BH + u_idx] + s1;
         }
-        // ---- SSD partial of this tile
+        // ---- SSD partial of this tile; then the prefetched tiles go to shared memory
         for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
-        if ((tid & 31) == 0) red[tid >> 5] = ssd;
+        if (lane == 0) red[warp] = ssd;
         __syncthreads();
         if (tid == 0) {
             float t = 0.0f;
-            for (int i = 0; i < kIterThreads / 32; ++i) t += red[i];
-            a.part[(size_t)pair * a.tiles + tile] = t;
+            for (int i = 0; i < NT / 32; ++i) t += red[i];
+            a.part[(size_t)cur.pair * a.tiles + cur.tile] = t;
         }
-        __syncthreads();
+        if (next < work) commit();
     }
 }
 
@@ -292,82 +409,88 @@ __global__ void demons_control_kernel(CtrlArgs c)
 }
 
 // Final field of a level: u = u_0 when no update was applied, else G_f * s_n.
-template <int RAD>
-__global__ void __launch_bounds__(256) demons_finalize_kernel(const float *u0, const float *s0, const float *s1,
+// PLANAR writes the ABI layout [B][2][h][w], otherwise interleaved float2.
+template <int RAD, bool PLANAR>
+__global__ void __launch_bounds__(256) demons_finalize_kernel(const float2 *u0, const float2 *s0, const float2 *s1,
                                                               const int32_t *iters, int levels, int level,
                                                               float *uout, int B, int h, int w, int tiles_x,
                                                               int tiles, Taps taps)
 {
     constexpr int AW = TX + 2 * RAD, AH = TY + 2 * RAD;
-    __shared__ float sa[2 * AW * AH];
-    __shared__ float sx[2 * AH * TX];
+    extern __shared__ __align__(16) unsigned char fin_smem[];
+    float2 *sa = reinterpret_cast<float2 *>(fin_smem);   // [AH][AW]
+    float2 *sx = sa + AW * AH;                            // [AH][TX]
     const size_t plane = (size_t)h * w;
     for (long long item = blockIdx.x; item < (long long)B * tiles; item += gridDim.x) {
         const int pair = (int)(item / tiles), tile = (int)(item % tiles);
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
         const int n = iters[(size_t)pair * levels + level];
-        const float *src = (n == 0 ? u0 : ((n & 1) ? s1 : s0)) + (size_t)pair * 2 * plane;
-        float *dst = uout + (size_t)pair * 2 * plane;
+        const float2 *src = (n == 0 ? u0 : ((n & 1) ? s1 : s0)) + (size_t)pair * plane;
+        auto put = [&](int gy, int gx, float2 v) {
+            size_t g = (size_t)gy * w + gx;
+            if (PLANAR) {
+                uout[(size_t)pair * 2 * plane + g] = v.x;
+                uout[(size_t)pair * 2 * plane + plane + g] = v.y;
+            } else {
+                reinterpret_cast<float2 *>(uout)[(size_t)pair * plane + g] = v;
+            }
+        };
         if (n == 0 || RAD == 0) {
             for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
                 int gy = y0 + idx / TX, gx = x0 + idx % TX;
-                if (gy < h && gx < w) {
-                    size_t g = (size_t)gy * w + gx;
-                    dst[g] = src[g];
-                    dst[plane + g] = src[plane + g];
-                }
+                if (gy < h && gx < w) put(gy, gx, src[(size_t)gy * w + gx]);
             }
             continue;
         }
         for (int idx = threadIdx.x; idx < AW * AH; idx += blockDim.x) {
             int ly = idx / AW, lx = idx - ly * AW;
             int gy = clampi(y0 - RAD + ly, 0, h - 1), gx = clampi(x0 - RAD + lx, 0, w - 1);
-            size_t g = (size_t)gy * w + gx;
-            sa[idx] = src[g];
-            sa[AW * AH + idx] = src[plane + g];
+            sa[idx] = src[(size_t)gy * w + gx];
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < AH * TX; idx += blockDim.x) {
             int ly = idx / TX, lx = idx - ly * TX;
-            float a0 = 0.0f, a1 = 0.0f;
-            for (int k = 0; k <= 2 * RAD; ++k) {
-                a0 = fmaf(taps.f[k], sa[ly * AW + lx + k], a0);
-                a1 = fmaf(taps.f[k], sa[AW * AH + ly * AW + lx + k], a1);
-            }
-            sx[idx] = a0;
-            sx[AH * TX + idx] = a1;
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int k = 0; k <= 2 * RAD; ++k) acc = ffma2(make_float2(taps.f[k], taps.f[k]), sa[ly * AW + lx + k], acc);
+            sx[idx] = acc;
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
             int ly = idx / TX, lx = idx - ly * TX;
             int gy = y0 + ly, gx = x0 + lx;
             if (gy >= h || gx >= w) continue;
-            float a0 = 0.0f, a1 = 0.0f;
-            for (int k = 0; k <= 2 * RAD; ++k) {
-                a0 = fmaf(taps.f[k], sx[(ly + k) * TX + lx], a0);
-                a1 = fmaf(taps.f[k], sx[AH * TX + (ly + k) * TX + lx], a1);
-            }
-            size_t g = (size_t)gy * w + gx;
-            dst[g] = a0;
-            dst[plane + g] = a1;
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int k = 0; k <= 2 * RAD; ++k) acc = ffma2(make_float2(taps.f[k], taps.f[k]), sx[(ly + k) * TX + lx], acc);
+            put(gy, gx, acc);
         }
         __syncthreads();
     }
 }
 
-// Prolongation (Section 1): fine(x_f) = 2 * bilinear(coarse, (x_f + 0.5)/2 - 0.5).
-__global__ void prolong_kernel(const float *__restrict__ uc, float *__restrict__ uf, int B, int h, int w)
+// Prolongation (Section 1): fine(x_f) = 2 * bilinear(coarse, (x_f + 0.5)/2 - 0.5), interleaved fields.
+__global__ void prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B, int h, int w)
 {
     const int H = 2 * h, W = 2 * w;
-    const size_t total = (size_t)B * 2 * H * W;
+    const size_t total = (size_t)B * H * W;
     for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        size_t pl = idx / ((size_t)H * W);   // pair * 2 + component
-        int rem = (int)(idx - pl * H * W);
+        size_t b = idx / ((size_t)H * W);
+        int rem = (int)(idx - b * H * W);
         int i = rem / W, j = rem - i * W;
-        const float *c = uc + pl * h * w;
         float x = ((float)j + 0.5f) * 0.5f - 0.5f, y = ((float)i + 0.5f) * 0.5f - 0.5f;
-        uf[idx] = 2.0f * bilinear_clamped(c, h, w, x, y);
+        float2 v = bilinear2_clamped(uc + b * h * w, h, w, x, y);
+        uf[idx] = make_float2(2.0f * v.x, 2.0f * v.y);
+    }
+}
+
+// Planar [B][2][h][w] -> interleaved [B][h][w] float2 (the optional initial field).
+__global__ void interleave_kernel(const float *__restrict__ in, float2 *__restrict__ out, int B, int h, int w)
+{
+    const size_t plane = (size_t)h * w, total = (size_t)B * plane;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        size_t b = idx / plane, p = idx - b * plane;
+        out[idx] = make_float2(in[b * 2 * plane + p], in[b * 2 * plane + plane + p]);
     }
 }
 
@@ -377,15 +500,16 @@ __global__ void iota_kernel(int *a, int n, int *count)
     if (blockIdx.x == 0 && threadIdx.x == 0) *count = n;
 }
 
-template <int RAD>
-int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t st)
+template <int RAD, bool IN_S>
+int launch_iter_t(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t st)
 {
-    constexpr size_t smem = IterSmem<RAD>::TOTAL * sizeof(float);
+    constexpr size_t smem = Geo<RAD>::BYTES;
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        HR_CHECK(cudaFuncSetAttribute(demons_iter_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, demons_iter_kernel<RAD>, kIterThreads, smem));
+        HR_CHECK(cudaFuncSetAttribute(demons_iter_kernel<RAD, IN_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, demons_iter_kernel<RAD, IN_S>, kIterThreads, smem));
         if (occ < 1) occ = 1;
         configured_dev = ctx->device;
     }
@@ -393,10 +517,16 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    demons_iter_kernel<RAD><<<grid, kIterThreads, smem, st>>>(a);
+    demons_iter_kernel<RAD, IN_S><<<grid, kIterThreads, smem, st>>>(a);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
+}
+
+template <int RAD>
+int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t st)
+{
+    return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
 int dispatch_iter(hrebsd_ctx *ctx, int rad, const IterArgs &a, int max_items, cudaStream_t st)
@@ -413,14 +543,23 @@ int dispatch_iter(hrebsd_ctx *ctx, int rad, const IterArgs &a, int max_items, cu
     }
 }
 
-int dispatch_finalize(hrebsd_ctx *ctx, int rad, const float *u0, const float *s0, const float *s1,
+int dispatch_finalize(hrebsd_ctx *ctx, int rad, bool planar, const float2 *u0, const float2 *s0, const float2 *s1,
                       const int32_t *iters, int levels, int level, float *uout, int B, int h, int w, int tiles_x,
                       int tiles, const Taps &taps, cudaStream_t st)
 {
     long long items = (long long)B * tiles;
     int grid = (int)(items < ctx->num_sms * 8LL ? items : ctx->num_sms * 8LL);
+    const size_t smem = (size_t)((TX + 2 * rad) * (TY + 2 * rad) + (TY + 2 * rad) * TX) * sizeof(float2);
     hr_prof_begin(ctx, st);
-#define HR_FIN(R) demons_finalize_kernel<R><<<grid, 256, 0, st>>>(u0, s0, s1, iters, levels, level, uout, B, h, w, tiles_x, tiles, taps)
+#define HR_FIN(R)                                                                                                  \
+    do {                                                                                                           \
+        auto kt = demons_finalize_kernel<R, true>;                                                                 \
+        auto kf = demons_finalize_kernel<R, false>;                                                                \
+        HR_CHECK(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                \
+        HR_CHECK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));                \
+        if (planar) kt<<<grid, 256, smem, st>>>(u0, s0, s1, iters, levels, level, uout, B, h, w, tiles_x, tiles, taps); \
+        else kf<<<grid, 256, smem, st>>>(u0, s0, s1, iters, levels, level, uout, B, h, w, tiles_x, tiles, taps);  \
+    } while (0)
     switch (rad) {
     case 0: HR_FIN(0); break;
     case 1: HR_FIN(1); break;
@@ -494,9 +633,18 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
     HR_CHECK(cudaMemsetAsync(iters, 0, sizeof(int32_t) * B * L, st));
     HR_CHECK(cudaMemsetAsync(status, 0, sizeof(int32_t) * B, st));
     {
-        size_t n0 = (size_t)B * 2 * (H >> start) * (W >> start) * 4;
-        if (init_field) HR_CHECK(cudaMemcpyAsync(u0, init_field, n0, cudaMemcpyDeviceToDevice, st));
-        else HR_CHECK(cudaMemsetAsync(u0, 0, n0, st));
+        const int hs = H >> start, ws = W >> start;
+        size_t n0 = (size_t)B * hs * ws;
+        if (init_field) {
+            int grid = (int)((n0 + 255) / 256);
+            if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+            hr_prof_begin(ctx, st);
+            interleave_kernel<<<grid, 256, 0, st>>>(init_field, (float2 *)u0, B, hs, ws);
+            hr_prof_end(ctx, PROF_DEMONS_AUX, st);
+            HR_LAUNCHED(ctx);
+        } else {
+            HR_CHECK(cudaMemsetAsync(u0, 0, n0 * sizeof(float2), st));
+        }
     }
 
     for (int l = start; l >= 0; --l) {
@@ -513,8 +661,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             a.Ftest = tl[l];
             a.Mref = rl[l];
             a.ref_idx = ref_idx;
-            a.in = k == 0 ? (const float *)u0 : ((k & 1) ? (const float *)s1 : (const float *)s0);
-            a.out = ((k + 1) & 1) ? (float *)s1 : (float *)s0;
+            a.in = k == 0 ? (const float2 *)u0 : ((k & 1) ? (const float2 *)s1 : (const float2 *)s0);
+            a.out = ((k + 1) & 1) ? (float2 *)s1 : (float2 *)s0;
             a.part = (float *)part;
             a.active = cur;
             a.n_active = cnt + (k & 1);
@@ -553,15 +701,15 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             HR_LAUNCHED(ctx);
         }
         float *dst = l == 0 ? field : (float *)uout;
-        if ((e = dispatch_finalize(ctx, rad, (const float *)u0, (const float *)s0, (const float *)s1, iters, L, l,
-                                   dst, B, h, w, tiles_x, tiles, taps, st)))
+        if ((e = dispatch_finalize(ctx, rad, l == 0, (const float2 *)u0, (const float2 *)s0, (const float2 *)s1,
+                                   iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
             return e;
         if (l > 0) {
-            size_t total = (size_t)B * 2 * (2 * h) * (2 * w);
+            size_t total = (size_t)B * (2 * h) * (2 * w);
             int grid = (int)((total + 255) / 256);
             if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
             hr_prof_begin(ctx, st);
-            prolong_kernel<<<grid, 256, 0, st>>>((const float *)uout, (float *)u0, B, h, w);
+            prolong_kernel<<<grid, 256, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
             HR_LAUNCHED(ctx);
         }
