@@ -47,6 +47,7 @@ extern "C" {
 #define HREBSD_ECUDA -2    /* a CUDA runtime call or launch failed */
 #define HREBSD_ENOMEM -3   /* workspace allocation failed */
 #define HREBSD_ETIMEOUT -4 /* a bounded device-side wait expired */
+#define HREBSD_ESCRATCH -5 /* request larger than the static scratch of hrebsd_demons_register_batch_noalloc */
 
 /* pair_status bits */
 #define HREBSD_PAIR_CAPPED 1      /* some pyramid level stopped at its iteration cap */
@@ -143,6 +144,30 @@ int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float 
                                  int R, int B, int H, int W, const hrebsd_demons_params *params,
                                  const float *init_field, float *field, int32_t *iters, int32_t *pair_status,
                                  void *stream);
+
+/* Allocation-free variant of hrebsd_demons_register_batch (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory:
+ * code recorded into a CUDA graph, where cudaMalloc cannot be captured, and
+ * hosts or plugins that fix the device-memory budget or own the allocator).
+ * Same arguments, outputs and results as hrebsd_demons_register_batch, but
+ * the workspace is a static device array of HREBSD_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) inside this library, held by every process that loads it on each
+ * device it uses, until exit; the call never calls cudaMalloc/cudaFree or any
+ * allocating routine.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress) with that device current: make that first
+ * call outside any stream capture.  The whole batch must fit: about
+ * 8 B x 3 x H x W + 8 B x H x W / 4 + 4 B x H x W / 3 per pair plus small
+ * per-pair lists (about 9 pairs of 256 x 256 with 4 levels, or 37 pairs of
+ * 128 x 128 with 3 levels);
+ * larger requests return HREBSD_ESCRATCH before any launch.  All calls share
+ * the array and it keeps the last call's contents (every slot is written
+ * before it is read), so calls that overlap on the GPU race: serialise them.
+ * Tracing (hrebsd_profile_*) does not record this call. */
+#define HREBSD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, const float *test,
+                                         const int32_t *ref_idx, int R, int B, int H, int W,
+                                         const hrebsd_demons_params *params, const float *init_field, float *field,
+                                         int32_t *iters, int32_t *pair_status, void *stream);
 
 /* a5 -- rotation fit (Section 2, Eq. 2-5).  The field [B][2][H][W] is
  * sampled bilinearly at the N ROI centres c (index coordinates c - 0.5);

@@ -19,11 +19,13 @@ from . import _build
 __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
-    "hrebsd_demons_register_batch", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
+    "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_profile_enable", "hrebsd_profile_read", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
+ESCRATCH = -5
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
 
@@ -86,6 +88,8 @@ def load(build: bool = False):
         "hrebsd_preprocess_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
         "hrebsd_demons_register_batch": (i, [vp, vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp,
                                              vp, vp, vp]),
+        "hrebsd_demons_register_batch_noalloc": (i, [vp, vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_demons_params),
+                                                     vp, vp, vp, vp, vp]),
         "hrebsd_fit_rotation": (i, [vp, vp, i, i, i, vp, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
         "hrebsd_remap": (i, [vp, vp, vp, vp, i, i, i, C.POINTER(hrebsd_geometry), vp, vp]),
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
@@ -176,6 +180,17 @@ def hrebsd_demons_register_batch(ctx, ref, test, ref_idx, R, B, H, W, params, in
                                              B, H, W, C.byref(params), _p(init_field, t.float32),
                                              _p(field, t.float32), _p(iters, t.int32), _p(pair_status, t.int32),
                                              _s(stream)), "hrebsd_demons_register_batch")
+
+
+def hrebsd_demons_register_batch_noalloc(ctx, ref, test, ref_idx, R, B, H, W, params, init_field, field, iters,
+                                         pair_status, stream=None):
+    """Same as hrebsd_demons_register_batch with the library's static scratch (no device allocation)."""
+    t = _t()
+    _chk(load().hrebsd_demons_register_batch_noalloc(ctx, _p(ref, t.float32), _p(test, t.float32),
+                                                     _p(ref_idx, t.int32), R, B, H, W, C.byref(params),
+                                                     _p(init_field, t.float32), _p(field, t.float32),
+                                                     _p(iters, t.int32), _p(pair_status, t.int32), _s(stream)),
+         "hrebsd_demons_register_batch_noalloc")
 
 
 def hrebsd_fit_rotation(ctx, field, B, H, W, roi_xy, N, geom, F_first, R_finite, pair_status, stream=None):

@@ -83,14 +83,14 @@ static cudaEvent_t pool_get(hrebsd_ctx *ctx)
 
 void hr_prof_begin(hrebsd_ctx *ctx, cudaStream_t st)
 {
-    if (!ctx->prof_on) return;
+    if (!ctx->prof_on || ctx->no_events) return;
     ctx->cur_a = pool_get(ctx);
     if (ctx->cur_a) cudaEventRecord(ctx->cur_a, st);
 }
 
 void hr_prof_end(hrebsd_ctx *ctx, int cls, cudaStream_t st)
 {
-    if (!ctx->prof_on || !ctx->cur_a) return;
+    if (!ctx->prof_on || ctx->no_events || !ctx->cur_a) return;
     cudaEvent_t b = pool_get(ctx);
     if (!b) return;
     cudaEventRecord(b, st);
@@ -207,6 +207,7 @@ const char *hrebsd_status_string(int status)
     case HREBSD_ECUDA: return "CUDA error";
     case HREBSD_ENOMEM: return "out of device memory";
     case HREBSD_ETIMEOUT: return "bounded device wait expired";
+    case HREBSD_ESCRATCH: return "request exceeds the static scratch array of the allocation-free entry point";
     default: return "unknown status";
     }
 }

@@ -576,12 +576,38 @@ int dispatch_finalize(hrebsd_ctx *ctx, int rad, bool planar, const float2 *u0, c
     return HREBSD_OK;
 }
 
-enum { WS_TPYR = 0, WS_RPYR, WS_U0, WS_S0, WS_S1, WS_UOUT, WS_PART, WS_HIST, WS_LIST };
+enum { WS_TPYR = 0, WS_RPYR, WS_U0, WS_S0, WS_S1, WS_UOUT, WS_PART, WS_HIST, WS_LIST, WS_COUNT };
 
 // Register B pairs (all buffers already offset to this chunk).
+// Bytes of each workspace slot for B pairs (WS_* order).
+void slot_bytes(int R, int B, int H, int W, const hrebsd_demons_params *p, size_t *bytes)
+{
+    const int L = p->levels;
+    int cap_max = 0;
+    for (int l = 0; l < L; ++l) cap_max = p->max_iters[l] > cap_max ? p->max_iters[l] : cap_max;
+    size_t pyr_px = 0, rpyr_px = 0;
+    for (int l = 1; l < L; ++l) {
+        pyr_px += (size_t)B * (H >> l) * (W >> l);
+        rpyr_px += (size_t)R * (H >> l) * (W >> l);
+    }
+    const size_t field_elems = (size_t)B * 2 * H * W;
+    const int tiles0 = ((W + TX - 1) / TX) * ((H + TY - 1) / TY);
+    bytes[WS_TPYR] = pyr_px * 4 + 16;
+    bytes[WS_RPYR] = rpyr_px * 4 + 16;
+    bytes[WS_U0] = field_elems * 4;
+    bytes[WS_S0] = field_elems * 4;
+    bytes[WS_S1] = field_elems * 4;
+    bytes[WS_UOUT] = (L > 1 ? field_elems / 4 : 1) * 4;
+    bytes[WS_PART] = (size_t)B * tiles0 * 4;
+    bytes[WS_HIST] = (size_t)B * (cap_max + 1) * 8;
+    bytes[WS_LIST] = ((size_t)2 * B + 64) * 4;
+}
+
+// Register B pairs (all buffers already offset to this chunk).  `given`
+// (nullable) supplies the workspace slots; otherwise they come from the context.
 int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const int32_t *ref_idx, int R, int B,
                    int H, int W, const hrebsd_demons_params *p, const float *init_field, float *field,
-                   int32_t *iters, int32_t *status, cudaStream_t st)
+                   int32_t *iters, int32_t *status, cudaStream_t st, void *const *given = nullptr)
 {
     const int L = p->levels;
     const int start = (p->start_level < 0 || p->start_level >= L) ? L - 1 : p->start_level;
@@ -603,15 +629,14 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
     void *tpyr = nullptr, *rpyr = nullptr, *u0 = nullptr, *s0 = nullptr, *s1 = nullptr, *uout = nullptr;
     void *part = nullptr, *hist = nullptr, *lists = nullptr;
     int e;
-    if ((e = hr_ws(ctx, WS_TPYR, pyr_px * 4 + 16, &tpyr))) return e;
-    if ((e = hr_ws(ctx, WS_RPYR, rpyr_px * 4 + 16, &rpyr))) return e;
-    if ((e = hr_ws(ctx, WS_U0, field_elems * 4, &u0))) return e;
-    if ((e = hr_ws(ctx, WS_S0, field_elems * 4, &s0))) return e;
-    if ((e = hr_ws(ctx, WS_S1, field_elems * 4, &s1))) return e;
-    if ((e = hr_ws(ctx, WS_UOUT, (L > 1 ? field_elems / 4 : 1) * 4, &uout))) return e;
-    if ((e = hr_ws(ctx, WS_PART, (size_t)B * tiles0 * 4, &part))) return e;
-    if ((e = hr_ws(ctx, WS_HIST, (size_t)B * (cap_max + 1) * 8, &hist))) return e;
-    if ((e = hr_ws(ctx, WS_LIST, ((size_t)2 * B + 64) * 4, &lists))) return e;
+    size_t sb[WS_COUNT];
+    slot_bytes(R, B, H, W, p, sb);
+    void **slot_ptr[WS_COUNT] = {&tpyr, &rpyr, &u0, &s0, &s1, &uout, &part, &hist, &lists};
+    for (int k = 0; k < WS_COUNT; ++k) {
+        if (given) *slot_ptr[k] = given[k];
+        else if ((e = hr_ws(ctx, k, sb[k], slot_ptr[k]))) return e;
+    }
+    (void)pyr_px; (void)rpyr_px; (void)field_elems; (void)tiles0;
     int *list0 = (int *)lists, *list1 = list0 + B, *cnt = list1 + B;   // cnt[0], cnt[1]
 
     // pyramids (level pointers)
@@ -717,12 +742,9 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
     return HREBSD_OK;
 }
 
-}  // namespace
-
-extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float *test,
-                                            const int32_t *ref_idx, int R, int B, int H, int W,
-                                            const hrebsd_demons_params *p, const float *init_field, float *field,
-                                            int32_t *iters, int32_t *pair_status, void *stream)
+int check_register_args(hrebsd_ctx *ctx, const float *ref, const float *test, const int32_t *ref_idx, int R, int B,
+                        int H, int W, const hrebsd_demons_params *p, float *field, int32_t *iters,
+                        int32_t *pair_status)
 {
     if (!ctx || !p || B < 0 || R < 1) return HREBSD_EINVAL;
     if (p->levels < 1 || p->levels > 8) return HREBSD_EINVAL;
@@ -735,7 +757,20 @@ extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, c
     if (hr_gauss_radius(p->sigma_update) > kMaxRad || hr_gauss_radius(p->sigma_field) > kMaxRad) return HREBSD_EINVAL;
     if (B == 0) return HREBSD_OK;
     if (!ref || !test || !ref_idx || !field || !iters || !pair_status) return HREBSD_EINVAL;
-    int e = hr_set_device(ctx);
+    return HREBSD_OK;
+}
+
+}  // namespace
+
+extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float *test,
+                                            const int32_t *ref_idx, int R, int B, int H, int W,
+                                            const hrebsd_demons_params *p, const float *init_field, float *field,
+                                            int32_t *iters, int32_t *pair_status, void *stream)
+{
+    int e = check_register_args(ctx, ref, test, ref_idx, R, B, H, W, p, field, iters, pair_status);
+    if (e || B == 0) return e;
+    const int L = p->levels;
+    e = hr_set_device(ctx);
     if (e) return e;
     // pairs are processed in chunks so that the workspace stays bounded (~24 GB at 256x256)
     const size_t per_pair = (size_t)H * W * 4 * 2 * 4;   // u0, s0, s1 (+ pyramids), bytes
@@ -752,4 +787,66 @@ extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, c
         if (e) return e;
     }
     return HREBSD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free registration.  Some callers cannot call cudaMalloc: code
+// that runs inside a CUDA graph capture (allocation is not a capturable
+// operation and would break the capture), hosts that enforce a fixed
+// device-memory budget set up before launch, and plugins whose host
+// application owns the allocator.  For them the workspace of the registration
+// lives in one static device array of HREBSD_NOALLOC_SCRATCH_BYTES, which
+// every process that loads this library holds on each device it uses until
+// exit.  All calls share it and it keeps the previous call's contents: every
+// slot is written before it is read (the initial field is zeroed explicitly),
+// so nothing leaks from one call into the next, but calls that overlap on the
+// GPU (different streams, or different host threads) race on the array and
+// must be serialised by the caller.
+namespace {
+
+__device__ __align__(256) unsigned char hr_noalloc_scratch[HREBSD_NOALLOC_SCRATCH_BYTES];
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device address).
+int noalloc_scratch_address(int device, unsigned char **out)
+{
+    static unsigned char *addr[256] = {};
+    if (device < 0 || device >= 256) return HREBSD_EINVAL;
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, hr_noalloc_scratch);
+        if (e != cudaSuccess) return hr_cuda_error(e, "cudaGetSymbolAddress(hr_noalloc_scratch)", __FILE__, __LINE__);
+        addr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = addr[device];
+    return HREBSD_OK;
+}
+
+}  // namespace
+
+extern "C" int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, const float *test,
+                                                    const int32_t *ref_idx, int R, int B, int H, int W,
+                                                    const hrebsd_demons_params *p, const float *init_field,
+                                                    float *field, int32_t *iters, int32_t *pair_status,
+                                                    void *stream)
+{
+    int e = check_register_args(ctx, ref, test, ref_idx, R, B, H, W, p, field, iters, pair_status);
+    if (e || B == 0) return e;
+    size_t sb[WS_COUNT], off[WS_COUNT], total = 0;
+    slot_bytes(R, B, H, W, p, sb);
+    for (int k = 0; k < WS_COUNT; ++k) {
+        off[k] = total;
+        total += (sb[k] + 255) / 256 * 256;
+    }
+    if (total > (size_t)HREBSD_NOALLOC_SCRATCH_BYTES) return HREBSD_ESCRATCH;
+    if ((e = hr_set_device(ctx))) return e;
+    unsigned char *base = nullptr;
+    if ((e = noalloc_scratch_address(ctx->device, &base))) return e;
+    void *given[WS_COUNT];
+    for (int k = 0; k < WS_COUNT; ++k) given[k] = base + off[k];
+    ctx->no_events = 1;   // tracing would create CUDA events; skip it for this call
+    e = register_chunk(ctx, ref, test, ref_idx, R, B, H, W, p, init_field, field, iters, pair_status,
+                       hr_stream(stream), given);
+    ctx->no_events = 0;
+    return e;
 }

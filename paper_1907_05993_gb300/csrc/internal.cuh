@@ -44,6 +44,7 @@ struct hrebsd_ctx {
     hr_buf ws[16];   // named workspace slots (see demons.cu)
     // tracing
     int prof_on = 0;
+    int no_events = 0;   // set while a call must not create CUDA events
     double prof_ms[HREBSD_PROF_CLASSES] = {};
     long long prof_launches[HREBSD_PROF_CLASSES] = {};
     unsigned long long *d_pixiters = nullptr;
