@@ -70,6 +70,17 @@ const char *hrebsd_status_string(int status);
 /* Kernel launches of this context since creation (for accounting). */
 long long hrebsd_launch_count(const hrebsd_ctx *ctx);
 
+/* Synchronise the device; HREBSD_ETIMEOUT if a kernel of this library gave
+ * up a bounded wait on an asynchronous copy since the last call (the flag is
+ * then cleared and the affected outputs are invalid), else HREBSD_OK. */
+int hrebsd_device_error(hrebsd_ctx *ctx);
+
+/* Context options.  HREBSD_OPT_NO_TMA (value 0/1): run the demons iteration
+ * without tensor-memory-accelerator tile loads (same results; used to test
+ * both paths; the environment variable HREBSD_NO_TMA sets it at creation). */
+#define HREBSD_OPT_NO_TMA 1
+int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value);
+
 /* Tracing: per kernel class, CUDA-event time of every launch (events are
  * recorded on the launch stream around each kernel while enabled).  Classes:
  * 0 demons iteration, 1 demons stop control, 2 demons pyramid/finalize/

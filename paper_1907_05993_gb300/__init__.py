@@ -20,7 +20,7 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_profile_enable", "hrebsd_profile_read", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_solve_F", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -84,6 +84,8 @@ def load(build: bool = False):
         "hrebsd_status_string": (C.c_char_p, [i]),
         "hrebsd_launch_count": (ll, [vp]),
         "hrebsd_profile_enable": (i, [vp, i]),
+        "hrebsd_device_error": (i, [vp]),
+        "hrebsd_set_option": (i, [vp, i, i]),
         "hrebsd_profile_read": (i, [vp, C.POINTER(hrebsd_profile)]),
         "hrebsd_preprocess_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
         "hrebsd_demons_register_batch": (i, [vp, vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp,
@@ -152,6 +154,18 @@ def hrebsd_status_string(status: int) -> str:
 
 def hrebsd_launch_count(ctx) -> int:
     return int(load().hrebsd_launch_count(ctx))
+
+
+OPT_NO_TMA = 1
+
+
+def hrebsd_device_error(ctx):
+    """Raise if a kernel gave up a bounded wait since the last check (synchronises)."""
+    _chk(load().hrebsd_device_error(ctx), "hrebsd_device_error")
+
+
+def hrebsd_set_option(ctx, option: int, value: int):
+    _chk(load().hrebsd_set_option(ctx, option, int(value)), "hrebsd_set_option")
 
 
 def hrebsd_profile_enable(ctx, enable: bool):

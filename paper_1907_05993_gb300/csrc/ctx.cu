@@ -69,6 +69,9 @@ int hr_gauss_taps(float sigma, int rad, float *taps)
     return r;
 }
 
+// Set by kernels whose bounded wait on an asynchronous copy gave up.
+__device__ int hr_device_error_flag;
+
 static cudaEvent_t pool_get(hrebsd_ctx *ctx)
 {
     if (!ctx->pool.empty()) {
@@ -174,10 +177,12 @@ int hrebsd_create(hrebsd_ctx **ctx, int device)
     hrebsd_ctx *c = new hrebsd_ctx();
     c->device = device;
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&c->d_err, hr_device_error_flag);
     if (e != cudaSuccess) {
         delete c;
-        return hr_cuda_error(e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
+        return hr_cuda_error(e, "hrebsd_create", __FILE__, __LINE__);
     }
+    if (getenv("HREBSD_NO_TMA")) c->no_tma = 1;
     *ctx = c;
     return HREBSD_OK;
 }
@@ -214,4 +219,68 @@ const char *hrebsd_status_string(int status)
 
 long long hrebsd_launch_count(const hrebsd_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
+int hrebsd_device_error(hrebsd_ctx *ctx)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    int st = hr_set_device(ctx);
+    if (st) return st;
+    HR_CHECK(cudaDeviceSynchronize());
+    int flag = 0, zero = 0;
+    HR_CHECK(cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) HR_CHECK(cudaMemcpy(ctx->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return flag ? HREBSD_ETIMEOUT : HREBSD_OK;
+}
+
+int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    switch (option) {
+    case HREBSD_OPT_NO_TMA: ctx->no_tma = value ? 1 : 0; return HREBSD_OK;
+    default: return HREBSD_EINVAL;
+    }
+}
+
 }  // extern "C"
+
+// ---------------------------------------------------------------- tensor maps
+#include "tma.cuh"
+
+typedef CUresult (*hr_encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+
+static hr_encode_tiled_fn encode_fn()
+{
+    static hr_encode_tiled_fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<hr_encode_tiled_fn>(p);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+int hr_encode_tmap_3d(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1,
+                      uint64_t s2, uint32_t b0, uint32_t b1, uint32_t b2)
+{
+    hr_encode_tiled_fn fn = encode_fn();
+    if (!fn) return -1;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (s1 & 15) || (s2 & 15) || ((b0 * 4) & 15)) return -1;
+    if (b0 > 256 || b1 > 256 || b2 > 256 || b0 == 0 || b1 == 0 || b2 == 0) return -1;
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {s1, s2};
+    cuuint32_t box[3] = {b0, b1, b2};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}

@@ -34,6 +34,7 @@
 #include <string.h>
 
 #include "internal.cuh"
+#include "tma.cuh"
 
 int hr_launch_reduce2(hrebsd_ctx *ctx, const float *in, float *out, int n, int H, int W, cudaStream_t st);
 
@@ -66,6 +67,7 @@ struct IterArgs {
     const int *n_active;     // its length
     int *n_next_reset;       // counter of the next list, zeroed by this launch
     unsigned long long *px_count;   // tracing: pixel-iterations (NULL = off)
+    int *err;                       // set to 1 when a bounded wait gives up
     int h, w, tiles_x, tiles;
     int in_is_s;
     float alpha2;
@@ -369,6 +371,252 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_kernel(IterArgs a
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-fed iteration (k > 0, r > 0).  The s tile (T + 2r, padded) and the test
+// image tile (T + r + 1, widened to 16-byte-aligned columns) arrive by bulk
+// tensor copies issued by one thread, so the other threads spend no
+// instructions on loads: the s copy for the next item is issued as soon as
+// the x pass has consumed the current s tile, the test-image copy as soon as
+// the force stage has consumed the current one.  The copy fills out-of-image
+// elements with zeros; border tiles then replicate the edge rows/columns in
+// shared memory (the clamped-address semantics of the plain path).  The
+// force stage works on runs of 4 pixels per thread with the gradient stencil
+// and field read once per run; runs that touch the image border take the
+// per-pixel clamped path.
+template <int RAD>
+struct GeoT {
+    using L = Geo<RAD>;
+    static constexpr int FOFF = 4 * ((RAD + 1 + 3) / 4);   // test-image halo, rounded to 16 bytes
+    static constexpr int FWB = TX + 2 * FOFF;               // test-image tile columns
+    static constexpr int FH = L::FH;
+    static constexpr uint32_t S_BYTES = (uint32_t)L::AHP * L::AST * 8;
+    static constexpr uint32_t F_BYTES = (uint32_t)FH * FWB * 4;
+    static constexpr int S_OFF = 0;
+    static constexpr int F_OFF = (int)round_up((int)S_BYTES, 128);
+    static constexpr int X_OFF = F_OFF + (int)round_up((int)F_BYTES, 128);
+    static constexpr int U_OFF = X_OFF + L::SX * 8;
+    static constexpr int D_OFF = U_OFF + L::SU * 8;
+    static constexpr size_t BYTES = (size_t)D_OFF + (size_t)L::BH * L::DST * 8;
+};
+
+// Replicate out-of-image rows, then columns, of a tile whose rows cover global
+// [g0r, g0r + nr) and columns [g0c, g0c + nc) (element type T, row stride st).
+template <typename T>
+__device__ __forceinline__ void fix_rows(T *t, int st, int nr, int nc, int g0r, int nimg)
+{
+    const int top = max(0, -g0r), bot = max(0, g0r + nr - nimg);
+    if (!(top | bot)) return;
+    for (int idx = threadIdx.x; idx < (top + bot) * nc; idx += blockDim.x) {
+        const int k = idx / nc, c = idx - k * nc;
+        const int dr = k < top ? k : nr - bot + (k - top);
+        const int sr = k < top ? top : nr - bot - 1;
+        t[dr * st + c] = t[sr * st + c];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, int nimg)
+{
+    const int left = max(0, -g0c), right = max(0, g0c + nc - nimg);
+    if (!(left | right)) return;
+    const int n = left + right;
+    for (int idx = threadIdx.x; idx < nr * n; idx += blockDim.x) {
+        const int row = idx / n, k = idx - row * n;
+        const int dc = k < left ? k : nc - right + (k - left);
+        const int sc = k < left ? left : nc - right - 1;
+        t[row * st + dc] = t[row * st + sc];
+    }
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
+                                                                          const __grid_constant__ CUtensorMap tmF,
+                                                                          IterArgs a)
+{
+    using L = Geo<RAD>;
+    using G = GeoT<RAD>;
+    constexpr int NT = kIterThreads;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float2 *sS = reinterpret_cast<float2 *>(smraw + G::S_OFF);   // [AHP][AST]
+    float *sF = reinterpret_cast<float *>(smraw + G::F_OFF);     // [FH][FWB]
+    float2 *sX = reinterpret_cast<float2 *>(smraw + G::X_OFF);
+    float2 *sU = reinterpret_cast<float2 *>(smraw + G::U_OFF);   // [BHP][UST]
+    float2 *sD = reinterpret_cast<float2 *>(smraw + G::D_OFF);   // [BH][DST]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float red[NT / 32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float2 tf[2 * RAD + 1], tu[2 * RAD + 1];
+#pragma unroll
+    for (int k = 0; k <= 2 * RAD; ++k) {
+        tf[k] = make_float2(a.taps.f[k], a.taps.f[k]);
+        tu[k] = make_float2(a.taps.up[k], a.taps.up[k]);
+    }
+    const int n_active = *a.n_active;
+    if (blockIdx.x == 0 && tid == 0) {
+        *a.n_next_reset = 0;
+        if (a.px_count) atomicAdd(a.px_count, (unsigned long long)n_active * a.h * a.w);
+    }
+    const long long work = (long long)n_active * a.tiles;
+    const int h = a.h, w = a.w;
+    const size_t plane = (size_t)h * w;
+    if (tid == 0) {
+        hr_tma::mbar_init(&bar[0], 1);
+        hr_tma::mbar_init(&bar[1], 1);
+        hr_tma::fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue_S = [&](const TileRef &t) {
+        hr_tma::mbar_arrive_expect_tx(&bar[0], G::S_BYTES);
+        hr_tma::load_3d(sS, &tmS, &bar[0], 2 * (t.x0 - 2 * RAD), t.y0 - 2 * RAD, t.pair);
+    };
+    auto issue_F = [&](const TileRef &t) {
+        hr_tma::mbar_arrive_expect_tx(&bar[1], G::F_BYTES);
+        hr_tma::load_3d(sF, &tmF, &bar[1], t.x0 - G::FOFF, t.y0 - RAD - 1, t.pair);
+    };
+    long long item = blockIdx.x;
+    if (tid == 0 && item < work) {
+        const TileRef t = tile_of(a, item);
+        issue_S(t);
+        issue_F(t);
+    }
+    uint32_t phase = 0;
+    for (; item < work; item += gridDim.x) {
+        const TileRef cur = tile_of(a, item);
+        const long long next = item + gridDim.x;
+        const int x0 = cur.x0, y0 = cur.y0;
+        const float *M = a.Mref + (size_t)__ldg(a.ref_idx + cur.pair) * plane;
+        bool ok = hr_tma::mbar_wait(&bar[0], phase);
+        ok = hr_tma::mbar_wait(&bar[1], phase) && ok;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicExch(a.err, 1);
+            return;
+        }
+        phase ^= 1u;
+        // ---- replicate borders (tiles that reach outside the image only)
+        const bool border = x0 - 2 * RAD < 0 || x0 - 2 * RAD + L::AST > w || y0 - 2 * RAD < 0 ||
+                            y0 - 2 * RAD + L::AHP > h || x0 - G::FOFF < 0 || x0 - G::FOFF + G::FWB > w ||
+                            y0 - RAD - 1 < 0 || y0 - RAD - 1 + G::FH > h;
+        if (border) {
+            fix_rows(sS, L::AST, L::AHP, L::AST, y0 - 2 * RAD, h);
+            fix_rows(sF, G::FWB, G::FH, G::FWB, y0 - RAD - 1, h);
+            __syncthreads();
+            fix_cols(sS, L::AST, L::AHP, L::AST, x0 - 2 * RAD, w);
+            fix_cols(sF, G::FWB, G::FH, G::FWB, x0 - G::FOFF, w);
+            __syncthreads();
+        }
+        // ---- u = G_f * s on T + r
+        constexpr int NSX = L::BWP / RUN;
+        for (int it = tid; it < NSX * L::AHP; it += NT) {
+            const int seg = it / L::AHP, row = it - seg * L::AHP;
+            run_x<RAD>(sS + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
+        }
+        __syncthreads();
+        if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
+            hr_tma::fence_proxy_async();
+            issue_S(tile_of(a, next));
+        }
+        constexpr int NSY = L::BHP / RUN;
+        for (int it = tid; it < NSY * L::BWP; it += NT) {
+            const int seg = it / L::BWP, col = it - seg * L::BWP;
+            float2 acc[RUN];
+            run_y<RAD>(sX + seg * RUN * L::XST + col, L::XST, tf, acc);
+#pragma unroll
+            for (int o = 0; o < RUN; ++o) sU[(seg * RUN + o) * L::UST + col] = acc[o];
+        }
+        __syncthreads();
+
+        // ---- warp + force on T + r, runs of 4 pixels.  Every run is computed the
+        // same way (no divergent border path): the test-image tile has replicated
+        // borders, so the central difference becomes the one-sided one at the
+        // image edge once scaled by 1 instead of 1/2; points outside the image
+        // are overwritten below by the replicated in-image values.
+        float ssd = 0.0f;
+        constexpr int NRUN = (L::BW + 3) / 4;
+        constexpr int FC = G::FOFF - RAD;   // test-image column of local column 0
+        for (int it = tid; it < NRUN * L::BH; it += NT) {
+            const int r = it / NRUN, c0 = 4 * (it - r * NRUN);
+            const int vy = y0 - RAD + r, vx0 = x0 - RAD + c0;
+            const bool rowT = r >= RAD && r < RAD + TY && vy < h;
+            const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
+            const float4 *up = reinterpret_cast<const float4 *>(sU + r * L::UST + c0);
+            const float4 ua = up[0], ub = up[1];
+            const float ux[4] = {ua.x, ua.z, ub.x, ub.z}, uy[4] = {ua.y, ua.w, ub.y, ub.w};
+            const float *fm = sF + (r + 1) * G::FWB + c0 + FC;
+            float fl[6], fu[4], fd[4];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) fl[i] = fm[i - 1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                fu[i] = fm[i - G::FWB];
+                fd[i] = fm[i + G::FWB];
+            }
+            float mw[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mw[i] = bilinear_clamped(M, h, w, (float)(vx0 + i) - ux[i], (float)vy - uy[i]);
+            float2 du[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int vx = vx0 + i;
+                const float sx = (vx == 0 || vx == w - 1) ? 1.0f : 0.5f;
+                const float gx = sx * (fl[i + 2] - fl[i]);
+                const float gy = sy * (fd[i] - fu[i]);
+                const float d = mw[i] - fl[i + 1];
+                const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
+                const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
+                du[i] = make_float2(t * gx, t * gy);
+                const int c = c0 + i;
+                if (rowT && c >= RAD && c < RAD + TX && vx < w) ssd = fmaf(d, d, ssd);
+            }
+            float4 *dp = reinterpret_cast<float4 *>(sD + r * L::DST + c0);
+            dp[0] = make_float4(du[0].x, du[0].y, du[1].x, du[1].y);
+            dp[1] = make_float4(du[2].x, du[2].y, du[3].x, du[3].y);
+        }
+        if (border) {   // du outside the image = du at the clamped position
+            __syncthreads();
+            fix_rows(sD, L::DST, L::BH, L::BW, y0 - RAD, h);
+            __syncthreads();
+            fix_cols(sD, L::DST, L::BH, L::BW, x0 - RAD, w);
+        }
+        __syncthreads();
+        if (tid == 0 && next < work) {   // the test-image tile is consumed: fetch the next one
+            hr_tma::fence_proxy_async();
+            issue_F(tile_of(a, next));
+        }
+        // ---- G_u * du: x pass on rows of T + r, columns of T
+        constexpr int NSXD = TX / RUN;
+        for (int it = tid; it < NSXD * L::BH; it += NT) {
+            const int seg = it / L::BH, row = it - seg * L::BH;
+            run_x<RAD>(sD + row * L::DST + seg * RUN, sX + row * L::XDST + seg * RUN, tu);
+        }
+        __syncthreads();
+        // ---- y pass, s_{k+1} = u_k + G_u * du on T
+        float2 *dst = a.out + (size_t)cur.pair * plane;
+        for (int it = tid; it < (TY / RUN) * TX; it += NT) {
+            const int seg = it / TX, col = it - seg * TX;
+            float2 acc[RUN];
+            run_y<RAD>(sX + seg * RUN * L::XDST + col, L::XDST, tu, acc);
+            const int gx = x0 + col;
+#pragma unroll
+            for (int o = 0; o < RUN; ++o) {
+                const int gy = y0 + seg * RUN + o;
+                if (gy < h && gx < w) {
+                    const float2 u = sU[(seg * RUN + o + RAD) * L::UST + col + RAD];
+                    dst[(size_t)gy * w + gx] = __fadd2_rn(u, acc[o]);
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
+        if (lane == 0) red[warp] = ssd;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.0f;
+            for (int i = 0; i < NT / 32; ++i) t += red[i];
+            a.part[(size_t)cur.pair * a.tiles + cur.tile] = t;
+        }
+    }
+}
+
 struct CtrlArgs {
     const float *part;       // [B][tiles]
     double *hist;            // [B][hist_stride]
@@ -529,6 +777,73 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
+template <int RAD>
+int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a, int max_items,
+                    cudaStream_t st)
+{
+    constexpr size_t smem = GeoT<RAD>::BYTES;
+    static int configured_dev = -1;
+    static int occ = 0;
+    if (configured_dev != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(demons_iter_tma_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, demons_iter_tma_kernel<RAD>, kIterThreads, smem));
+        if (occ < 1) occ = 1;
+        configured_dev = ctx->device;
+    }
+    int grid = ctx->num_sms * occ;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    hr_prof_begin(ctx, st);
+    demons_iter_tma_kernel<RAD><<<grid, kIterThreads, smem, st>>>(tmS, tmF, a);
+    hr_prof_end(ctx, PROF_ITER, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// Tensor maps of one level for the TMA-fed iteration: the two s buffers
+// (float2 [B][h][w] seen as FP32 [B][h][2w]) and the test images.
+template <int RAD>
+bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w, CUtensorMap *tmS,
+                       CUtensorMap *tmF)
+{
+    using L = Geo<RAD>;
+    using G = GeoT<RAD>;
+    const uint64_t row2 = (uint64_t)w * 8, img2 = row2 * h, row1 = (uint64_t)w * 4, img1 = row1 * h;
+    if (hr_encode_tmap_3d(&tmS[0], s0, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
+    if (hr_encode_tmap_3d(&tmS[1], s1, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
+    if (hr_encode_tmap_3d(tmF, ftest, w, h, B, row1, img1, G::FWB, G::FH, 1)) return false;
+    return true;
+}
+
+bool encode_maps(int rad, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w, CUtensorMap *tmS,
+                 CUtensorMap *tmF)
+{
+    switch (rad) {
+    case 1: return encode_level_maps<1>(s0, s1, ftest, B, h, w, tmS, tmF);
+    case 2: return encode_level_maps<2>(s0, s1, ftest, B, h, w, tmS, tmF);
+    case 3: return encode_level_maps<3>(s0, s1, ftest, B, h, w, tmS, tmF);
+    case 4: return encode_level_maps<4>(s0, s1, ftest, B, h, w, tmS, tmF);
+    case 5: return encode_level_maps<5>(s0, s1, ftest, B, h, w, tmS, tmF);
+    case 6: return encode_level_maps<6>(s0, s1, ftest, B, h, w, tmS, tmF);
+    default: return false;
+    }
+}
+
+int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a,
+                      int max_items, cudaStream_t st)
+{
+    switch (rad) {
+    case 1: return launch_iter_tma<1>(ctx, tmS, tmF, a, max_items, st);
+    case 2: return launch_iter_tma<2>(ctx, tmS, tmF, a, max_items, st);
+    case 3: return launch_iter_tma<3>(ctx, tmS, tmF, a, max_items, st);
+    case 4: return launch_iter_tma<4>(ctx, tmS, tmF, a, max_items, st);
+    case 5: return launch_iter_tma<5>(ctx, tmS, tmF, a, max_items, st);
+    case 6: return launch_iter_tma<6>(ctx, tmS, tmF, a, max_items, st);
+    default: return HREBSD_EINVAL;
+    }
+}
+
 int dispatch_iter(hrebsd_ctx *ctx, int rad, const IterArgs &a, int max_items, cudaStream_t st)
 {
     switch (rad) {
@@ -676,6 +991,9 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         const int h = H >> l, w = W >> l;
         const int tiles_x = (w + TX - 1) / TX, tiles = tiles_x * ((h + TY - 1) / TY);
         const int cap = p->max_iters[l];
+        CUtensorMap tmS[2], tmF;
+        const bool use_tma = rad > 0 && !ctx->no_tma &&
+                             encode_maps(rad, (const float2 *)s0, (const float2 *)s1, tl[l], B, h, w, tmS, &tmF);
         hr_prof_begin(ctx, st);
         iota_kernel<<<(B + 255) / 256, 256, 0, st>>>(list0, B, cnt);
         hr_prof_end(ctx, PROF_DEMONS_AUX, st);
@@ -700,7 +1018,10 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             a.alpha2 = p->alpha * p->alpha;
             a.taps = taps;
             a.px_count = hr_prof_pixiters(ctx);
-            if ((e = dispatch_iter(ctx, rad, a, B * tiles, st))) return e;
+            a.err = ctx->d_err;
+            if (k > 0 && use_tma) e = dispatch_iter_tma(ctx, rad, tmS[k & 1], tmF, a, B * tiles, st);
+            else e = dispatch_iter(ctx, rad, a, B * tiles, st);
+            if (e) return e;
             CtrlArgs c;
             c.part = (const float *)part;
             c.hist = (double *)hist;

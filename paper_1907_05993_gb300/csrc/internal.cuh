@@ -45,6 +45,8 @@ struct hrebsd_ctx {
     // tracing
     int prof_on = 0;
     int no_events = 0;   // set while a call must not create CUDA events
+    int no_tma = 0;      // force the non-TMA demons iteration (testing, unsupported shapes)
+    int *d_err = nullptr;   // device flag: a bounded wait gave up (static device symbol)
     double prof_ms[HREBSD_PROF_CLASSES] = {};
     long long prof_launches[HREBSD_PROF_CLASSES] = {};
     unsigned long long *d_pixiters = nullptr;

@@ -354,3 +354,31 @@ def test_pipeline_single_pair_workload(torch, lib, oracle):
     tie = out["near_tie"].cpu().numpy()[0].astype(bool) | exp["near_tie"]
     assert np.array_equal(out["peak"].cpu().numpy()[0][~tie], exp["peak"][~tie])
     pipe.close()
+
+
+# ------------------------------------------------------------------ both iteration paths
+@pytest.mark.parametrize("H,W,levels,caps", [(256, 256, 4, [12] * 4), (96, 80, 2, [10, 10]), (66, 70, 1, [10])])
+def test_tma_and_plain_iteration_paths_agree(torch, lib, oracle, H, W, levels, caps):
+    """The tensor-memory-accelerator path (k > 0) and the plain-load path give the same field.
+
+    66 x 70 is a shape the tensor maps refuse (row pitch not a multiple of 16 bytes), so it runs
+    the plain path in both modes and checks the fallback against the oracle.
+    """
+    spec = K.ScanSpec(n_pairs=3, H=H, W=W, n_refs=2, mis_lo_deg=0.5, mis_hi_deg=3.0, seed=58)
+    refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
+    tests = np.stack([_pre_pair(oracle, spec, p)[1] for p in range(3)])
+    ridx = np.array([K.ref_index(spec, p) for p in range(3)])
+    params = lib.demons_params(levels, caps, 1.0, 1.0, 1.0)
+    out = []
+    for no_tma in (0, 1):
+        c = lib.hrebsd_create(0)
+        lib.hrebsd_set_option(c, lib.OPT_NO_TMA, no_tma)
+        out.append(_gpu_register(torch, lib, c, refs, tests, ridx, params))
+        lib.hrebsd_device_error(c)
+        lib.hrebsd_destroy(c)
+    (f0, i0, s0), (f1, i1, s1) = out
+    assert np.array_equal(i0, i1) and np.array_equal(s0, s1)
+    assert np.abs(f0 - f1).max() <= 1e-5
+    for b in range(3):
+        exp, _ = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, 1.0, 1.0, 1.0)
+        assert_field_parity(f0[b], exp, caps)
