@@ -220,6 +220,235 @@ __global__ void __launch_bounds__(NT) xcf_kernel(const float *__restrict__ rem, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// S = 64 (the batched-scan ROIs): radix-8 transforms in registers.  A 64-point
+// line transform is 8 x 8 (Cooley-Tukey): eight 8-point DFTs over the stride-8
+// subsequences, a twiddle W64^(n2 k1), eight 8-point DFTs over n2, natural-
+// order output.  512 threads = 64 lines x 8; thread (line = tid % 64,
+// t = tid / 64) so that a warp touches 32 consecutive rows or columns and the
+// twiddles are warp-uniform.  Rows are padded to 65 elements (conflict-free
+// column access).  4 shared-memory passes per 2-D transform instead of 12
+// radix-2 stages.
+namespace r8 {
+
+constexpr int S = 64, ZS = 65, NT = 512;
+
+// multiply by s*i (s = -1: forward twiddle sign)
+template <int SG>
+__device__ __forceinline__ float2 mul_si(float2 z) { return SG < 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x); }
+
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// 4-point DFT with sign SG, in place on (a0, a1, a2, a3)
+template <int SG>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    const float2 t0 = add(a0, a2), t1 = sub(a0, a2), t2 = add(a1, a3), t3 = mul_si<SG>(sub(a1, a3));
+    a0 = add(t0, t2);
+    a2 = sub(t0, t2);
+    a1 = add(t1, t3);
+    a3 = sub(t1, t3);
+}
+
+// 8-point DFT with sign SG: X[k] = sum_n x[n] exp(SG 2 pi i n k / 8)
+template <int SG>
+__device__ __forceinline__ void dft8(float2 (&x)[8])
+{
+    float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+    float2 o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+    dft4<SG>(e0, e1, e2, e3);
+    dft4<SG>(o0, o1, o2, o3);
+    const float c = 0.70710678118654752f;
+    const float2 w1o1 = make_float2(c * (o1.x - SG * o1.y), c * (o1.y + SG * o1.x));   // (c, SG c) * o1
+    const float2 w2o2 = mul_si<SG>(o2);
+    const float2 w3o3 = make_float2(c * (-o3.x - SG * o3.y), c * (-o3.y + SG * o3.x));  // (-c, SG c) * o3
+    x[0] = add(e0, o0);
+    x[4] = sub(e0, o0);
+    x[1] = add(e1, w1o1);
+    x[5] = sub(e1, w1o1);
+    x[2] = add(e2, w2o2);
+    x[6] = sub(e2, w2o2);
+    x[3] = add(e3, w3o3);
+    x[7] = sub(e3, w3o3);
+}
+
+// One 64-point pass over all 64 lines.  ROWS: line = row, element stride 1;
+// else line = column, element stride ZS.  tw[j] = exp(-2 pi i j / 64).
+template <int SG, bool ROWS>
+__device__ __forceinline__ void pass64(float2 *z, const float2 *tw)
+{
+    const int line = threadIdx.x & 63, t = threadIdx.x >> 6;
+    const int ls = ROWS ? ZS : 1, es = ROWS ? 1 : ZS;
+    float2 *zl = z + line * ls;
+    float2 v[8];
+    // stage 1: DFT over n1 of x[8 n1 + t], twiddle W64^(t k1)
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) v[n1] = zl[(8 * n1 + t) * es];
+    dft8<SG>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+        float2 w = tw[t * k1];
+        if (SG > 0) w.y = -w.y;
+        v[k1] = make_float2(v[k1].x * w.x - v[k1].y * w.y, v[k1].x * w.y + v[k1].y * w.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) zl[(8 * t + k1) * es] = v[k1];
+    __syncthreads();
+    // stage 2: DFT over n2 of Y'[n2][k1 = t] -> X[t + 8 k2]
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) v[n2] = zl[(8 * n2 + t) * es];
+    dft8<SG>(v);
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) zl[(t + 8 * k2) * es] = v[k2];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) xcf64_kernel(const float *__restrict__ rem, const float *__restrict__ test, int B,
+                                                   int H, int W, const int32_t *__restrict__ roi, int N, int window,
+                                                   float *q, int32_t *peak, float *ph, int32_t *near_tie)
+{
+    __shared__ float2 z[S * ZS];
+    __shared__ float2 tw[S];
+    __shared__ float win[S];
+    __shared__ float red[NT / 32];
+    __shared__ float rv[NT / 32], rv2[NT / 32];
+    __shared__ int ri[NT / 32];
+
+    const int b = blockIdx.x / N, r = blockIdx.x % N;
+    const int cx = roi[2 * r], cy = roi[2 * r + 1];
+    const int x0 = cx - S / 2, y0 = cy - S / 2;
+    const size_t o = (size_t)blockIdx.x;
+    if (x0 < 0 || y0 < 0 || x0 + S > W || y0 + S > H) {   // ROI outside the image
+        if (threadIdx.x == 0) {
+            q[2 * o] = q[2 * o + 1] = __int_as_float(0x7fc00000);
+            peak[2 * o] = peak[2 * o + 1] = 0;
+            ph[o] = 0.0f;
+            if (near_tie) near_tie[o] = 0;
+        }
+        return;
+    }
+    if (threadIdx.x < S) {
+        float sn, cs;
+        sincospif(-2.0f * (float)threadIdx.x / (float)S, &sn, &cs);
+        tw[threadIdx.x] = make_float2(cs, sn);
+        win[threadIdx.x] = window ? 0.5f * (1.0f - cospif(2.0f * (float)threadIdx.x / (float)(S - 1))) : 1.0f;
+    }
+    const float *T = test + (size_t)b * H * W + (size_t)y0 * W + x0;
+    const float *Rr = rem + (size_t)b * H * W + (size_t)y0 * W + x0;
+    float st = 0.0f, sr = 0.0f;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int y = idx / S, x = idx % S;
+        const float tv = __ldg(T + (size_t)y * W + x), rv_ = __ldg(Rr + (size_t)y * W + x);
+        z[y * ZS + x] = make_float2(tv, rv_);
+        st += tv;
+        sr += rv_;
+    }
+    const float mt = block_sum<NT>(st, red) * (1.0f / (S * S));
+    const float mr = block_sum<NT>(sr, red) * (1.0f / (S * S));
+    float nt = 0.0f, nr = 0.0f;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int y = idx / S, x = idx % S;
+        const float wgt = win[y] * win[x];
+        float2 v = z[y * ZS + x];
+        v.x = (v.x - mt) * wgt;
+        v.y = (v.y - mr) * wgt;
+        z[y * ZS + x] = v;
+        nt = fmaf(v.x, v.x, nt);
+        nr = fmaf(v.y, v.y, nr);
+    }
+    nt = sqrtf(block_sum<NT>(nt, red));
+    nr = sqrtf(block_sum<NT>(nr, red));   // ends with a barrier: z complete
+
+    pass64<-1, true>(z, tw);
+    pass64<-1, false>(z, tw);
+
+    // cross-power P(k) = T(k) conj(R(k)), P(-k) = conj(P(k)); pairs (k, -k) in place
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const int ky = idx / S, kx = idx % S;
+        const int my = (S - ky) & (S - 1), mx = (S - kx) & (S - 1);
+        const int m = my * S + mx;
+        if (idx > m) continue;
+        const float2 zk = z[ky * ZS + kx], zm = z[my * ZS + mx];
+        const float2 Tk = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 Rk = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        const float2 P = make_float2(Tk.x * Rk.x + Tk.y * Rk.y, Tk.y * Rk.x - Tk.x * Rk.y);
+        z[ky * ZS + kx] = P;
+        if (m != idx) z[my * ZS + mx] = make_float2(P.x, -P.y);
+    }
+    __syncthreads();
+    pass64<1, true>(z, tw);
+    pass64<1, false>(z, tw);
+
+    // argmax of c = Re(z) / S^2 (first maximum in row-major order) and runner-up
+    const float scale = 1.0f / (float)(S * S);
+    float bv = -INFINITY, bv2 = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int idx = threadIdx.x; idx < S * S; idx += NT) {
+        const float v = z[(idx / S) * ZS + idx % S].x * scale;
+        if (better(v, idx, bv, bi)) {
+            bv2 = bv;
+            bv = v;
+            bi = idx;
+        } else if (v > bv2) {
+            bv2 = v;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const float ov2 = __shfl_xor_sync(0xffffffffu, bv2, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (better(ov, oi, bv, bi)) {
+            bv2 = fmaxf(bv, ov2);
+            bv = ov;
+            bi = oi;
+        } else {
+            bv2 = fmaxf(bv2, ov);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        rv[threadIdx.x >> 5] = bv;
+        rv2[threadIdx.x >> 5] = bv2;
+        ri[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = rv[0], v2 = rv2[0];
+        int i = ri[0];
+        for (int k = 1; k < NT / 32; ++k) {
+            if (better(rv[k], ri[k], v, i)) {
+                v2 = fmaxf(v, rv2[k]);
+                v = rv[k];
+                i = ri[k];
+            } else {
+                v2 = fmaxf(v2, rv[k]);
+            }
+        }
+        const int py = i / S, px = i % S;
+        const float c0 = v;
+        const float cxm = z[py * ZS + ((px + S - 1) & (S - 1))].x * scale;
+        const float cxp = z[py * ZS + ((px + 1) & (S - 1))].x * scale;
+        const float cym = z[((py + S - 1) & (S - 1)) * ZS + px].x * scale;
+        const float cyp = z[((py + 1) & (S - 1)) * ZS + px].x * scale;
+        float dx = 0.0f, dy = 0.0f, den;
+        den = cxm - 2.0f * c0 + cxp;
+        if (den != 0.0f) dx = (cxm - cxp) / (2.0f * den);
+        den = cym - 2.0f * c0 + cyp;
+        if (den != 0.0f) dy = (cym - cyp) / (2.0f * den);
+        const int wx = px >= S / 2 ? px - S : px, wy = py >= S / 2 ? py - S : py;
+        peak[2 * o] = wx;
+        peak[2 * o + 1] = wy;
+        q[2 * o] = (float)wx + dx;
+        q[2 * o + 1] = (float)wy + dy;
+        ph[o] = (nr > 0.0f && nt > 0.0f) ? c0 / (nr * nt) : 0.0f;
+        if (near_tie) near_tie[o] = (c0 - v2) < 1e-6f * fabsf(c0);
+    }
+}
+
+}  // namespace r8
+
 template <int S, int NT>
 int launch_xcf(hrebsd_ctx *ctx, const float *rem, const float *test, int B, int H, int W, const int32_t *roi, int N,
                int window, float *q, int32_t *peak, float *ph, int32_t *near_tie, cudaStream_t st)
@@ -250,7 +479,14 @@ extern "C" int hrebsd_xcf_roi_batch(hrebsd_ctx *ctx, const float *remapped, cons
     switch (S) {
     case 16: return launch_xcf<16, 128>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
     case 32: return launch_xcf<32, 256>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
-    case 64: return launch_xcf<64, 256>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
+    case 64: {
+        hr_prof_begin(ctx, st);
+        r8::xcf64_kernel<<<B * N, r8::NT, 0, st>>>(remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height,
+                                                   near_tie);
+        hr_prof_end(ctx, PROF_XCF, st);
+        HR_LAUNCHED(ctx);
+        return HREBSD_OK;
+    }
     default: return launch_xcf<128, 512>(ctx, remapped, test, B, H, W, roi_xy, N, window, q, peak, peak_height, near_tie, st);
     }
 }
