@@ -85,9 +85,9 @@ int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value);
  * recorded on the launch stream around each kernel while enabled).  Classes:
  * 0 demons iteration, 1 demons stop control, 2 demons pyramid/finalize/
  * prolongation, 3 preprocess, 4 rotation fit, 5 remap, 6 ROI XCF,
- * 7 deformation-gradient solve.  pixel_iters counts demons pixel-iterations
+ * 7 deformation-gradient solve, 8 learned initialiser.  pixel_iters counts demons pixel-iterations
  * (active pairs x level pixels, summed over iteration launches). */
-#define HREBSD_PROF_CLASSES 8
+#define HREBSD_PROF_CLASSES 9
 typedef struct {
     double ms[HREBSD_PROF_CLASSES];
     long long launches[HREBSD_PROF_CLASSES];
@@ -220,6 +220,36 @@ int hrebsd_xcf_roi_batch(hrebsd_ctx *ctx, const float *remapped, const float *te
 int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N, int B, int H, int W,
                    const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
                    void *stream);
+
+/* a10 -- learned initialiser of the coarse field (project addition; the paper
+ * has none: its future-work remark is to optimise the multi-resolution
+ * demons).  A 4-level U-Net (3x3 convolutions 16-32-64-128, 2x2 max-pool,
+ * nearest x2 up-sampling, skip concatenations, 1x1 head, ReLU after every 3x3
+ * convolution) maps the 64x64 (reference, test) pair to the field at the 64x64
+ * pyramid level (x plane, y plane, 64x64-level pixels), to be passed as
+ * init_field of hrebsd_demons_register_batch with start_level = log2(H/64).
+ * BF16 tensor-core convolutions, FP32 accumulation and FP32 master weights.
+ * Parameter vector (host FP32, hrebsd_cnn_num_params entries): per 3x3 layer
+ * in the order e1a e1b e2a e2b e3a e3b ba bb d3a d3b d2a d2b d1a d1b the
+ * weights [cout][ky*3+kx][cin padded to 16] then the bias [cout]; then the head
+ * weights [2][16] and bias [2].  The network lives in the context (allocated
+ * on first use). */
+long long hrebsd_cnn_num_params(hrebsd_ctx *ctx);
+/* Set the parameters (params_host may be NULL: keep) and reset Adam. */
+int hrebsd_cnn_init(hrebsd_ctx *ctx, const float *params_host, long long n_params);
+/* Copy parameters and the gradients of the last training step to the host (either may be NULL). */
+int hrebsd_cnn_get_params(hrebsd_ctx *ctx, float *params_host, float *grads_host);
+/* Inference on x [B][2][64][64] BF16 (channel 0 reference, 1 test) -> field64 [B][2][64][64] FP32. */
+int hrebsd_cnn_infer(hrebsd_ctx *ctx, const uint16_t *x_bf16, int B, float *field64, void *stream);
+/* Inference from preprocessed patterns (as for the registration): the input is
+ * the (H/64 x W/64)-block mean of ref[ref_idx[b]] and test[b]; H = W, a multiple of 64. */
+int hrebsd_cnn_infer_patterns(hrebsd_ctx *ctx, const float *ref, const float *test, const int32_t *ref_idx, int B,
+                              int H, int W, float *field64, void *stream);
+/* One training step: forward, MSE loss against target [B][2][64][64] FP32 (its
+ * value to *loss_out, a device float, may be NULL), backward, and one Adam
+ * update (beta 0.9 / 0.999, eps 1e-8) with step size lr (lr = 0: gradients only). */
+int hrebsd_cnn_train_step(hrebsd_ctx *ctx, const uint16_t *x_bf16, const float *target, int B, float lr,
+                          float *loss_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -152,7 +152,9 @@ def forward(p, x, bf16=True):
 
 
 def backward(p, c, dout, bf16=True):
-    """Gradients of every parameter for the output gradient dout."""
+    """Gradients of every parameter for the output gradient dout.  With bf16=True
+    the gradient of each convolution's pre-activation is rounded to BF16 (the
+    precision it is stored in as a tensor-core operand); everything else is FP64."""
     q = bf16_round if bf16 else (lambda a: a)
     g = {}
     g["head.w"] = np.einsum("nohw,nchw->oc", dout, c["d1"])[:, :, None, None]
@@ -160,7 +162,7 @@ def backward(p, c, dout, bf16=True):
     dd1 = np.einsum("oc,nohw->nchw", q(p["head.w"])[:, :, 0, 0], dout)
 
     def block_bwd(name, dout_post):
-        dpre = dout_post * (c[name + ".out"] > 0)
+        dpre = q(dout_post * (c[name + ".out"] > 0))   # stored in BF16 as a tensor-core operand
         g[name + ".w"], g[name + ".b"] = conv3x3_wgrad(dpre, c[name + ".in"])
         return conv3x3_dgrad(dpre, q(p[name + ".w"]))
 

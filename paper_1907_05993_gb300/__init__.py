@@ -42,11 +42,11 @@ class hrebsd_geometry(C.Structure):
 
 
 class hrebsd_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8), ("pixel_iters", C.c_longlong)]
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_longlong * 9), ("pixel_iters", C.c_longlong)]
 
 
 PROF_CLASSES = ("demons_iter", "demons_control", "demons_aux", "preprocess", "fit_rotation", "remap", "xcf",
-                "solve_F")
+                "solve_F", "cnn")
 
 
 class hrebsd_demons_params(C.Structure):
@@ -96,6 +96,12 @@ def load(build: bool = False):
         "hrebsd_remap": (i, [vp, vp, vp, vp, i, i, i, C.POINTER(hrebsd_geometry), vp, vp]),
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
         "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
+        "hrebsd_cnn_num_params": (ll, [vp]),
+        "hrebsd_cnn_init": (i, [vp, vp, ll]),
+        "hrebsd_cnn_get_params": (i, [vp, vp, vp]),
+        "hrebsd_cnn_infer": (i, [vp, vp, i, vp, vp]),
+        "hrebsd_cnn_infer_patterns": (i, [vp, vp, vp, vp, i, i, i, vp, vp]),
+        "hrebsd_cnn_train_step": (i, [vp, vp, vp, i, C.c_float, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -234,3 +240,48 @@ def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, s
     _chk(load().hrebsd_solve_F(ctx, _p(q, t.float32), _p(roi_xy, t.int32), N, B, H, W, C.byref(geom),
                                _p(R_finite, t.float64), _p(F, t.float64), _p(pair_status, t.int32), _s(stream)),
          "hrebsd_solve_F")
+
+
+# ------------------------------------------------------------------ learned initialiser
+def hrebsd_cnn_num_params(ctx) -> int:
+    n = int(load().hrebsd_cnn_num_params(ctx))
+    if n < 0:
+        raise HrebsdError(-2, "hrebsd_cnn_num_params")
+    return n
+
+
+def hrebsd_cnn_init(ctx, params=None):
+    """params: host float32 numpy vector in the library's layout (None keeps the current ones)."""
+    import numpy as np
+    if params is None:
+        _chk(load().hrebsd_cnn_init(ctx, None, 0), "hrebsd_cnn_init")
+        return
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _chk(load().hrebsd_cnn_init(ctx, a.ctypes.data, a.size), "hrebsd_cnn_init")
+
+
+def hrebsd_cnn_get_params(ctx):
+    """(params, grads of the last training step) as float32 numpy vectors."""
+    import numpy as np
+    n = hrebsd_cnn_num_params(ctx)
+    p, g = np.empty(n, np.float32), np.empty(n, np.float32)
+    _chk(load().hrebsd_cnn_get_params(ctx, p.ctypes.data, g.ctypes.data), "hrebsd_cnn_get_params")
+    return p, g
+
+
+def hrebsd_cnn_infer(ctx, x_bf16, B, field64, stream=None):
+    t = _t()
+    _chk(load().hrebsd_cnn_infer(ctx, _p(x_bf16, t.bfloat16), B, _p(field64, t.float32), _s(stream)),
+         "hrebsd_cnn_infer")
+
+
+def hrebsd_cnn_infer_patterns(ctx, ref, test, ref_idx, B, H, W, field64, stream=None):
+    t = _t()
+    _chk(load().hrebsd_cnn_infer_patterns(ctx, _p(ref, t.float32), _p(test, t.float32), _p(ref_idx, t.int32), B, H, W,
+                                          _p(field64, t.float32), _s(stream)), "hrebsd_cnn_infer_patterns")
+
+
+def hrebsd_cnn_train_step(ctx, x_bf16, target, B, lr, loss_out=None, stream=None):
+    t = _t()
+    _chk(load().hrebsd_cnn_train_step(ctx, _p(x_bf16, t.bfloat16), _p(target, t.float32), B, float(lr),
+                                      _p(loss_out, t.float32), _s(stream)), "hrebsd_cnn_train_step")

@@ -1,0 +1,741 @@
+// a10 (project addition, no counterpart in the paper): learned initialiser of
+// the coarse demons field.  A 4-level U-Net (3x3 convolutions, 16-32-64-128
+// channels, max-pool, nearest up-sampling, skip concatenations, 1x1 head)
+// maps the 64x64 reference/test pair to the 2-channel field at that level.
+// Training (MSE, Adam) and inference run on this library's kernels:
+// implicit-GEMM convolutions on BF16 tensor cores with FP32 accumulation
+// (cnn_kernels.cuh), and small element-wise kernels below.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cnn_kernels.cuh"
+#include "internal.cuh"
+
+using namespace hr_cnn;
+
+namespace {
+
+constexpr int NCONV = 14;
+struct LayerDef {
+    int cin, cout, res;   // res: spatial size at batch-level 64
+};
+// forward order: e1a e1b e2a e2b e3a e3b ba bb d3a d3b d2a d2b d1a d1b
+constexpr LayerDef kLayers[NCONV] = {{2, 16, 64},   {16, 16, 64},  {16, 32, 32}, {32, 32, 32}, {32, 64, 16},
+                                     {64, 64, 16},  {64, 128, 8},  {128, 128, 8}, {192, 64, 16}, {64, 64, 16},
+                                     {96, 32, 32},  {32, 32, 32},  {48, 16, 64}, {16, 16, 64}};
+constexpr int HEAD_CIN = 16, HEAD_COUT = 2;
+
+__host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
+
+// ------------------------------------------------------------------ element-wise kernels
+// Input of the network from preprocessed patterns: box mean of f x f blocks
+// (f = H / 64) of ref[ref_idx[b]] and test[b] -> NHWC BF16, channels (ref, test, 0...).
+__global__ void pack_patterns_kernel(const float *ref, const float *test, const int32_t *ref_idx, int B, int H, int W,
+                                     bf16 *x)
+{
+    const int f = H / 64;
+    const size_t total = (size_t)B * 64 * 64;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(i / 4096), rem = (int)(i % 4096), yy = rem / 64, xx = rem % 64;
+        const float *r = ref + (size_t)ref_idx[b] * H * W, *t = test + (size_t)b * H * W;
+        float sr = 0.0f, st = 0.0f;
+        for (int dy = 0; dy < f; ++dy)
+            for (int dx = 0; dx < f; ++dx) {
+                const size_t o = (size_t)(yy * f + dy) * W + xx * f + dx;
+                sr += r[o];
+                st += t[o];
+            }
+        const float s = 1.0f / (f * f);
+        bf16 *o = x + i * 16;
+        o[0] = __float2bfloat16_rn(sr * s);
+        o[1] = __float2bfloat16_rn(st * s);
+        for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+// NCHW BF16 [B][2][64][64] -> NHWC BF16 padded to 16 channels.
+__global__ void pack_nchw_kernel(const bf16 *in, int B, bf16 *x)
+{
+    const size_t total = (size_t)B * 4096;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / 4096, p = i % 4096;
+        bf16 *o = x + i * 16;
+        o[0] = in[b * 8192 + p];
+        o[1] = in[b * 8192 + 4096 + p];
+        for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+    }
+}
+
+// 2x2 max-pool of NHWC BF16 (stride xs, offset xo, C channels) -> dense [N][h/2][w/2][C]
+// plus the argmax (0..3, first maximum in row-major order of the 2x2 window).
+__global__ void maxpool_kernel(const bf16 *x, int xs, int xo, int C, int N, int H, int W, bf16 *y, uint8_t *arg)
+{
+    const int h = H / 2, w = W / 2;
+    const size_t total = (size_t)N * h * w * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int xx = (int)(q % w), yy = (int)((q / w) % h), n = (int)(q / ((size_t)w * h));
+        float best = -INFINITY;
+        int bi = 0;
+        for (int k = 0; k < 4; ++k) {
+            const size_t src = ((size_t)(n * H + 2 * yy + k / 2) * W + 2 * xx + k % 2) * xs + xo + c;
+            const float v = __bfloat162float(x[src]);
+            if (v > best) {
+                best = v;
+                bi = k;
+            }
+        }
+        y[i] = __float2bfloat16_rn(best);
+        arg[i] = (uint8_t)bi;
+    }
+}
+
+// d_in[p][c] (FP32, dense [N][H][W][C]) = routed dy from the pool + skip gradient (stride ss, offset so).
+__global__ void maxpool_bwd_kernel(const float *dy, const uint8_t *arg, int C, int N, int H, int W, const float *skip,
+                                   int ss, int so, float *dx)
+{
+    const size_t total = (size_t)N * H * W * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((size_t)W * H));
+        const size_t pi = ((size_t)(n * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C + c;
+        const int k = (yy & 1) * 2 + (xx & 1);
+        float v = arg[pi] == k ? dy[pi] : 0.0f;
+        if (skip) v += skip[q * ss + so + c];
+        dx[i] = v;
+    }
+}
+
+// Nearest up-sampling x2 of dense [N][h][w][C] BF16 into y (stride ys, offset yo).
+__global__ void up2_kernel(const bf16 *x, int C, int N, int h, int w, bf16 *y, int ys, int yo)
+{
+    const int H = 2 * h, W = 2 * w;
+    const size_t total = (size_t)N * H * W * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((size_t)W * H));
+        y[q * ys + yo + c] = x[((size_t)(n * h + yy / 2) * w + xx / 2) * C + c];
+    }
+}
+
+// Adjoint of up2: dx[N][h][w][C] = sum of the 4 children of dy (stride ys, offset yo).
+__global__ void up2_bwd_kernel(const float *dy, int ys, int yo, int C, int N, int h, int w, float *dx)
+{
+    const int W = 2 * w;
+    const size_t total = (size_t)N * h * w * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int xx = (int)(q % w), yy = (int)((q / w) % h), n = (int)(q / ((size_t)w * h));
+        float s = 0.0f;
+        for (int k = 0; k < 4; ++k) s += dy[((size_t)(n * 2 * h + 2 * yy + k / 2) * W + 2 * xx + k % 2) * ys + yo + c];
+        dx[i] = s;
+    }
+}
+
+// dpre (BF16 dense [P][C]) = dpost (FP32, stride ds, offset do) * (out > 0), out BF16 (stride os, offset oo).
+__global__ void relu_bwd_kernel(const float *dpost, int ds, int dof, const bf16 *out, int os, int oo, int C, size_t P,
+                                bf16 *dpre)
+{
+    const size_t total = P * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i / C;
+        const int c = (int)(i % C);
+        const float g = __bfloat162float(out[p * os + oo + c]) > 0.0f ? dpost[p * ds + dof + c] : 0.0f;
+        dpre[i] = __float2bfloat16_rn(g);
+    }
+}
+
+// db[o] += sum_p dpre[p][o]
+__global__ void bias_grad_kernel(const bf16 *dpre, int C, size_t P, float *db)
+{
+    __shared__ float part[256];
+    const int c = threadIdx.x % C, lane_rows = blockDim.x / C;
+    float s = 0.0f;
+    if ((int)threadIdx.x < lane_rows * C)
+        for (size_t p = (size_t)blockIdx.x * lane_rows + threadIdx.x / C; p < P; p += (size_t)gridDim.x * lane_rows)
+            s += __bfloat162float(dpre[p * C + c]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < C) {
+        float t = 0.0f;
+        for (int r = 0; r < lane_rows; ++r) t += part[r * C + threadIdx.x];
+        atomicAdd(db + threadIdx.x, t);
+    }
+}
+
+// 1x1 head: out[b][o][y][x] (FP32 planar) = bias[o] + sum_c w[o][c] d1[p][c]
+__global__ void head_fwd_kernel(const bf16 *d1, const bf16 *w, const float *bias, int N, float *out)
+{
+    const size_t total = (size_t)N * 4096;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / 4096, p = i % 4096;
+        float a0 = bias[0], a1 = bias[1];
+        for (int c = 0; c < HEAD_CIN; ++c) {
+            const float v = __bfloat162float(d1[i * HEAD_CIN + c]);
+            a0 = fmaf(__bfloat162float(w[c]), v, a0);
+            a1 = fmaf(__bfloat162float(w[HEAD_CIN + c]), v, a1);
+        }
+        out[b * 8192 + p] = a0;
+        out[b * 8192 + 4096 + p] = a1;
+    }
+}
+
+// MSE gradient and loss: dout = 2 (pred - target) / count; loss += sum d^2 / count.
+__global__ void mse_kernel(const float *pred, const float *target, size_t count, float *dout, float *loss)
+{
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = pred[i] - target[i];
+        dout[i] = 2.0f * d / (float)count;
+        s = fmaf(d, d, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] / (float)count);
+}
+
+// Head backward: dd1[p][c] = sum_o w[o][c] dout[o][p]; dw[o][c] += sum_p dout[o][p] d1[p][c]; db[o] += sum_p dout.
+__global__ void head_bwd_kernel(const float *dout, const bf16 *d1, const bf16 *w, int N, float *dd1, float *dw,
+                                float *db)
+{
+    __shared__ float red[256][HEAD_COUT * (HEAD_CIN + 1)];
+    float acc[HEAD_COUT * (HEAD_CIN + 1)];
+    for (int k = 0; k < HEAD_COUT * (HEAD_CIN + 1); ++k) acc[k] = 0.0f;
+    const size_t total = (size_t)N * 4096;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / 4096, p = i % 4096;
+        const float g0 = dout[b * 8192 + p], g1 = dout[b * 8192 + 4096 + p];
+        for (int c = 0; c < HEAD_CIN; ++c) {
+            const float v = __bfloat162float(d1[i * HEAD_CIN + c]);
+            dd1[i * HEAD_CIN + c] = __bfloat162float(w[c]) * g0 + __bfloat162float(w[HEAD_CIN + c]) * g1;
+            acc[c] = fmaf(g0, v, acc[c]);
+            acc[HEAD_CIN + 1 + c] = fmaf(g1, v, acc[HEAD_CIN + 1 + c]);
+        }
+        acc[HEAD_CIN] += g0;
+        acc[2 * HEAD_CIN + 1] += g1;
+    }
+    for (int k = 0; k < HEAD_COUT * (HEAD_CIN + 1); ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < HEAD_COUT * (HEAD_CIN + 1)) {
+        float s = 0.0f;
+        for (int t = 0; t < (int)blockDim.x; ++t) s += red[t][threadIdx.x];
+        const int o = threadIdx.x / (HEAD_CIN + 1), c = threadIdx.x % (HEAD_CIN + 1);
+        if (c < HEAD_CIN) atomicAdd(dw + o * HEAD_CIN + c, s);
+        else atomicAdd(db + o, s);
+    }
+}
+
+// Adam (Kingma & Ba) on FP32 master weights, bias-corrected step size lr_t.
+__global__ void adam_kernel(float *w, const float *g, float *m, float *v, size_t n, float lr_t, float b1, float b2,
+                            float eps)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr_t * mi / (sqrtf(vi) + eps);
+    }
+}
+
+// FP32 master weights are kept in the forward layout [co][tap][cinp] (channels
+// padded to 16; the padded entries see zero inputs, so their gradients are zero
+// and they stay at zero).  -> BF16 copy of the same layout, and the BF16
+// input-gradient layout [ci][tap'][co] with tap' = 8 - tap (the flipped
+// kernel with input and output channels exchanged).
+__global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp, bf16 *wf, bf16 *wd)
+{
+    const int total = co * 9 * cinp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c = i % cinp, tap = (i / cinp) % 9, o = i / (cinp * 9);
+        const float v = c < ci ? w[i] : 0.0f;
+        wf[i] = __float2bfloat16_rn(v);
+        if (wd && c < ci) wd[((size_t)c * 9 + (8 - tap)) * co + o] = __float2bfloat16_rn(v);
+    }
+}
+
+__global__ void cast_bf16_kernel(const float *w, int n, bf16 *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = __float2bfloat16_rn(w[i]);
+}
+
+int grid_for(hrebsd_ctx *ctx, size_t n)
+{
+    size_t g = (n + 255) / 256;
+    size_t cap = (size_t)ctx->num_sms * 16;
+    return (int)(g < cap ? (g ? g : 1) : cap);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ network object
+struct hr_cnn_net {
+    // parameters (FP32 master), gradients, Adam moments: one flat buffer each
+    size_t n_params = 0;
+    size_t w_off[NCONV + 1], b_off[NCONV + 1];   // index NCONV = head
+    float *W = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+    bf16 *wf[NCONV + 1] = {}, *wd[NCONV] = {};
+    int step = 0;
+    // activations for a batch capacity
+    int cap = 0;
+    bf16 *x = nullptr;                              // [B][64][64][16]
+    bf16 *act[NCONV] = {};                          // outputs (the ones not in concat buffers)
+    bf16 *cat1 = nullptr, *cat2 = nullptr, *cat3 = nullptr;
+    bf16 *pool[3] = {};
+    uint8_t *parg[3] = {};
+    float *out = nullptr, *dout = nullptr, *loss = nullptr;
+    float *g_a = nullptr, *g_b = nullptr, *g_c = nullptr;   // FP32 gradient scratch (largest activation)
+    float *g_cat = nullptr;                                 // FP32 gradient of a concat input
+    bf16 *dpre = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int net_alloc(std::vector<void *> &allocs, size_t bytes, void **p)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HREBSD_ENOMEM;
+    }
+    allocs.push_back(*p);
+    return HREBSD_OK;
+}
+
+void net_free_acts(hr_cnn_net *n)
+{
+    // activations are the allocations after the parameter block (index >= 4 + 15 + 14)
+    const size_t keep = 4 + (NCONV + 1) + NCONV;
+    for (size_t i = keep; i < n->allocs.size(); ++i) cudaFree(n->allocs[i]);
+    if (n->allocs.size() > keep) n->allocs.resize(keep);
+    n->cap = 0;
+}
+
+int ensure_net(hrebsd_ctx *ctx)
+{
+    if (ctx->cnn) return HREBSD_OK;
+    hr_cnn_net *n = new hr_cnn_net();
+    size_t off = 0;
+    for (int l = 0; l <= NCONV; ++l) {   // [co][9][cinp] + bias per conv, head [2][16] + bias
+        const int co = l < NCONV ? kLayers[l].cout : HEAD_COUT;
+        n->w_off[l] = off;
+        off += l < NCONV ? (size_t)co * 9 * pad16(kLayers[l].cin) : (size_t)co * HEAD_CIN;
+        n->b_off[l] = off;
+        off += co;
+    }
+    n->n_params = off;
+    int e;
+    void *p;
+    float **bufs[4] = {&n->W, &n->G, &n->M, &n->V};
+    for (auto b : bufs) {
+        if ((e = net_alloc(n->allocs, off * sizeof(float), &p))) { delete n; return e; }
+        *b = (float *)p;
+        HR_CHECK(cudaMemset(p, 0, off * sizeof(float)));
+    }
+    for (int l = 0; l <= NCONV; ++l) {
+        const int ci = l < NCONV ? kLayers[l].cin : HEAD_CIN, co = l < NCONV ? kLayers[l].cout : HEAD_COUT;
+        const size_t sz = l < NCONV ? (size_t)co * 9 * pad16(ci) : (size_t)co * ci;
+        if ((e = net_alloc(n->allocs, sz * sizeof(bf16), &p))) { delete n; return e; }
+        n->wf[l] = (bf16 *)p;
+    }
+    for (int l = 0; l < NCONV; ++l) {
+        if ((e = net_alloc(n->allocs, (size_t)kLayers[l].cin * 9 * kLayers[l].cout * sizeof(bf16), &p))) { delete n; return e; }
+        n->wd[l] = (bf16 *)p;
+    }
+    ctx->cnn = n;
+    return HREBSD_OK;
+}
+
+int ensure_acts(hrebsd_ctx *ctx, int B)
+{
+    hr_cnn_net *n = ctx->cnn;
+    if (n->cap >= B) return HREBSD_OK;
+    HR_CHECK(cudaDeviceSynchronize());
+    net_free_acts(n);
+    int e;
+    void *p;
+    const size_t px64 = (size_t)B * 4096;
+#define NA(ptr, bytes)                                                        \
+    do {                                                                      \
+        if ((e = net_alloc(n->allocs, (bytes), &p))) return e;                \
+        ptr = decltype(ptr)(p);                                               \
+    } while (0)
+    NA(n->x, px64 * 16 * sizeof(bf16));
+    for (int l = 0; l < NCONV; ++l) {
+        const size_t px = (size_t)B * kLayers[l].res * kLayers[l].res;
+        NA(n->act[l], px * kLayers[l].cout * sizeof(bf16));
+    }
+    NA(n->cat1, px64 * 48 * sizeof(bf16));
+    NA(n->cat2, px64 / 4 * 96 * sizeof(bf16));
+    NA(n->cat3, px64 / 16 * 192 * sizeof(bf16));
+    NA(n->pool[0], px64 / 4 * 16 * sizeof(bf16));
+    NA(n->pool[1], px64 / 16 * 32 * sizeof(bf16));
+    NA(n->pool[2], px64 / 64 * 64 * sizeof(bf16));
+    NA(n->parg[0], px64 / 4 * 16);
+    NA(n->parg[1], px64 / 16 * 32);
+    NA(n->parg[2], px64 / 64 * 64);
+    NA(n->out, px64 * 2 * sizeof(float));
+    NA(n->dout, px64 * 2 * sizeof(float));
+    NA(n->loss, sizeof(float));
+    const size_t gmax = px64 * 48;   // largest activation (cat1) in elements
+    NA(n->g_a, gmax * sizeof(float));
+    NA(n->g_b, gmax * sizeof(float));
+    NA(n->g_c, gmax * sizeof(float));
+    NA(n->g_cat, gmax * sizeof(float));
+    NA(n->dpre, gmax * sizeof(bf16));
+#undef NA
+    n->cap = B;
+    return HREBSD_OK;
+}
+
+int refresh_bf16(hrebsd_ctx *ctx, cudaStream_t st)
+{
+    hr_cnn_net *n = ctx->cnn;
+    for (int l = 0; l < NCONV; ++l) {
+        const int ci = kLayers[l].cin, co = kLayers[l].cout;
+        weights_to_bf16_kernel<<<grid_for(ctx, (size_t)co * 9 * pad16(ci)), 256, 0, st>>>(n->W + n->w_off[l], ci, co,
+                                                                                          pad16(ci), n->wf[l], n->wd[l]);
+        HR_LAUNCHED(ctx);
+    }
+    cast_bf16_kernel<<<1, 64, 0, st>>>(n->W + n->w_off[NCONV], HEAD_COUT * HEAD_CIN, n->wf[NCONV]);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// One convolution launch.
+int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w, const float *bias, int cout, void *y,
+         int ys, int yo, int y_fp32, int relu, int N, int res, cudaStream_t st)
+{
+    ConvArgs a;
+    a.x = x;
+    a.xs = xs;
+    a.xo = xo;
+    a.cin = cin;
+    a.w = w;
+    a.bias = bias;
+    a.cout = cout;
+    a.y = y;
+    a.ys = ys;
+    a.yo = yo;
+    a.y_fp32 = y_fp32;
+    a.relu = relu;
+    a.N = N;
+    a.H = res;
+    a.W = res;
+    const int P = N * res * res;
+    dim3 grid((P + 63) / 64, (cout + 63) / 64);
+    hr_prof_begin(ctx, st);
+    conv3x3_kernel<<<grid, 128, 0, st>>>(a);
+    hr_prof_end(ctx, PROF_CNN, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+int wgrad(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs, int xo, int cin, float *dw, int N, int res,
+          cudaStream_t st)
+{
+    WgradArgs a;
+    a.dy = dy;
+    a.cout = cout;
+    a.x = x;
+    a.xs = xs;
+    a.xo = xo;
+    a.cin = cin;
+    a.dw = dw;
+    a.N = N;
+    a.H = res;
+    a.W = res;
+    const int P = N * res * res;
+    a.chunk = 2048;
+    dim3 grid((P + a.chunk - 1) / a.chunk, 9 * ((cin + 63) / 64), (cout + 63) / 64);
+    hr_prof_begin(ctx, st);
+    conv3x3_wgrad_kernel<<<grid, 128, 0, st>>>(a);
+    hr_prof_end(ctx, PROF_CNN, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// Where each conv reads its input and writes its output: (buffer, channel stride, offset).
+struct View {
+    bf16 *p;
+    int s, o;
+};
+
+void layer_views(hr_cnn_net *n, View *in, View *out)
+{
+    // e1a: x(16) -> act0 ; e1b: act0 -> cat1[32:48] ; e2a: pool0 -> act2 ; e2b: act2 -> cat2[64:96]
+    // e3a: pool1 -> act4 ; e3b: act4 -> cat3[128:192] ; ba: pool2 -> act6 ; bb: act6 -> act7
+    // d3a: cat3 -> act8 ; d3b: act8 -> act9 ; d2a: cat2 -> act10 ; d2b -> act11 ; d1a: cat1 -> act12 ; d1b -> act13
+    in[0] = {n->x, 16, 0};
+    out[0] = {n->act[0], 16, 0};
+    in[1] = {n->act[0], 16, 0};
+    out[1] = {n->cat1, 48, 32};
+    in[2] = {n->pool[0], 16, 0};
+    out[2] = {n->act[2], 32, 0};
+    in[3] = {n->act[2], 32, 0};
+    out[3] = {n->cat2, 96, 64};
+    in[4] = {n->pool[1], 32, 0};
+    out[4] = {n->act[4], 64, 0};
+    in[5] = {n->act[4], 64, 0};
+    out[5] = {n->cat3, 192, 128};
+    in[6] = {n->pool[2], 64, 0};
+    out[6] = {n->act[6], 128, 0};
+    in[7] = {n->act[6], 128, 0};
+    out[7] = {n->act[7], 128, 0};
+    in[8] = {n->cat3, 192, 0};
+    out[8] = {n->act[8], 64, 0};
+    in[9] = {n->act[8], 64, 0};
+    out[9] = {n->act[9], 64, 0};
+    in[10] = {n->cat2, 96, 0};
+    out[10] = {n->act[10], 32, 0};
+    in[11] = {n->act[10], 32, 0};
+    out[11] = {n->act[11], 32, 0};
+    in[12] = {n->cat1, 48, 0};
+    out[12] = {n->act[12], 16, 0};
+    in[13] = {n->act[12], 16, 0};
+    out[13] = {n->act[13], 16, 0};
+}
+
+int forward(hrebsd_ctx *ctx, int B, cudaStream_t st)
+{
+    hr_cnn_net *n = ctx->cnn;
+    View in[NCONV], out[NCONV];
+    layer_views(n, in, out);
+    int e;
+    auto run = [&](int l) {
+        return conv(ctx, in[l].p, in[l].s, in[l].o, pad16(kLayers[l].cin), n->wf[l], n->W + n->b_off[l],
+                    kLayers[l].cout, out[l].p, out[l].s, out[l].o, 0, 1, B, kLayers[l].res, st);
+    };
+    auto pool = [&](int k, const View &v, int C, int res) {
+        maxpool_kernel<<<grid_for(ctx, (size_t)B * res * res / 4 * C), 256, 0, st>>>(v.p, v.s, v.o, C, B, res, res,
+                                                                                    n->pool[k], n->parg[k]);
+        return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
+    };
+    auto up = [&](const bf16 *src, int C, int res, bf16 *dst, int ds) {
+        up2_kernel<<<grid_for(ctx, (size_t)B * res * res * 4 * C), 256, 0, st>>>(src, C, B, res, res, dst, ds, 0);
+        return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
+    };
+    if ((e = run(0)) || (e = run(1)) || (e = pool(0, out[1], 16, 64))) return e;
+    if ((e = run(2)) || (e = run(3)) || (e = pool(1, out[3], 32, 32))) return e;
+    if ((e = run(4)) || (e = run(5)) || (e = pool(2, out[5], 64, 16))) return e;
+    if ((e = run(6)) || (e = run(7)) || (e = up(n->act[7], 128, 8, n->cat3, 192))) return e;
+    if ((e = run(8)) || (e = run(9)) || (e = up(n->act[9], 64, 16, n->cat2, 96))) return e;
+    if ((e = run(10)) || (e = run(11)) || (e = up(n->act[11], 32, 32, n->cat1, 48))) return e;
+    if ((e = run(12)) || (e = run(13))) return e;
+    hr_prof_begin(ctx, st);
+    head_fwd_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(n->act[13], n->wf[NCONV], n->W + n->b_off[NCONV], B,
+                                                                    n->out);
+    hr_prof_end(ctx, PROF_CNN, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// Backward of conv l given the FP32 gradient of its post-ReLU output (dpost,
+// stride ds, offset do): weight and bias gradients, and (if dx != null) the FP32
+// gradient of its input written dense with the input's channel count.
+int conv_bwd(hrebsd_ctx *ctx, int l, const float *dpost, int ds, int dof, float *dx, int B, cudaStream_t st)
+{
+    hr_cnn_net *n = ctx->cnn;
+    View in[NCONV], out[NCONV];
+    layer_views(n, in, out);
+    const LayerDef &L = kLayers[l];
+    const size_t P = (size_t)B * L.res * L.res;
+    relu_bwd_kernel<<<grid_for(ctx, P * L.cout), 256, 0, st>>>(dpost, ds, dof, out[l].p, out[l].s, out[l].o, L.cout, P,
+                                                              n->dpre);
+    HR_LAUNCHED(ctx);
+    int e;
+    if ((e = wgrad(ctx, n->dpre, L.cout, in[l].p, in[l].s, in[l].o, pad16(L.cin), n->G + n->w_off[l], B, L.res, st)))
+        return e;
+    bias_grad_kernel<<<grid_for(ctx, P), 256, 0, st>>>(n->dpre, L.cout, P, n->G + n->b_off[l]);
+    HR_LAUNCHED(ctx);
+    if (dx)
+        return conv(ctx, n->dpre, L.cout, 0, L.cout, n->wd[l], nullptr, L.cin, dx, L.cin, 0, 1, 0, B, L.res, st);
+    return HREBSD_OK;
+}
+
+int backward(hrebsd_ctx *ctx, int B, cudaStream_t st)
+{
+    hr_cnn_net *n = ctx->cnn;
+    int e;
+    float *dd = n->g_a;   // gradient of d1b's output [B*4096][16]
+    hr_prof_begin(ctx, st);
+    head_bwd_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(n->dout, n->act[13], n->wf[NCONV], B, dd,
+                                                                     n->G + n->w_off[NCONV], n->G + n->b_off[NCONV]);
+    hr_prof_end(ctx, PROF_CNN, st);
+    HR_LAUNCHED(ctx);
+    const size_t p64 = (size_t)B * 4096, p32 = p64 / 4, p16 = p64 / 16;
+    auto ub = [&](const float *src, int ss, int C, int res, float *dst) {   // res: coarse size
+        up2_bwd_kernel<<<grid_for(ctx, (size_t)B * res * res * C), 256, 0, st>>>(src, ss, 0, C, B, res, res, dst);
+        return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
+    };
+    auto pb = [&](int k, const float *dp, int C, int res, const float *skip, int ss, int so, float *dst) {
+        maxpool_bwd_kernel<<<grid_for(ctx, (size_t)B * res * res * C), 256, 0, st>>>(dp, n->parg[k], C, B, res, res,
+                                                                                    skip, ss, so, dst);
+        return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
+    };
+    // decoder level 1 (64x64)
+    if ((e = conv_bwd(ctx, 13, dd, 16, 0, n->g_b, B, st))) return e;               // -> d d1a.out
+    if ((e = conv_bwd(ctx, 12, n->g_b, 16, 0, n->g_cat, B, st))) return e;         // -> d cat1 [32|16]
+    if ((e = ub(n->g_cat, 48, 32, 32, n->g_a))) return e;                          // -> d d2b.out [p32][32]
+    // keep d e1 (skip part of cat1) in g_cat (channels 32..47, stride 48)
+    if ((e = conv_bwd(ctx, 11, n->g_a, 32, 0, n->g_b, B, st))) return e;           // -> d d2a.out
+    float *dcat2 = n->g_c;
+    if ((e = conv_bwd(ctx, 10, n->g_b, 32, 0, dcat2, B, st))) return e;            // -> d cat2 [64|32]
+    if ((e = ub(dcat2, 96, 64, 16, n->g_a))) return e;                             // -> d d3b.out [p16][64]
+    if ((e = conv_bwd(ctx, 9, n->g_a, 64, 0, n->g_b, B, st))) return e;            // -> d d3a.out
+    float *dcat3 = n->dout + 0;   // reuse? no: dout is needed only before; use a slice of g_a after
+    dcat3 = n->g_a + p16 * 64;    // g_a holds d d3b.out in its first p16*64 floats
+    if ((e = conv_bwd(ctx, 8, n->g_b, 64, 0, dcat3, B, st))) return e;             // -> d cat3 [128|64]
+    if ((e = ub(dcat3, 192, 128, 8, n->g_b))) return e;                            // -> d bb.out [p8][128]
+    float *t1 = n->g_b + p16 / 4 * 128;
+    if ((e = conv_bwd(ctx, 7, n->g_b, 128, 0, t1, B, st))) return e;              // -> d ba.out
+    float *t2 = t1 + p16 / 4 * 128;
+    if ((e = conv_bwd(ctx, 6, t1, 128, 0, t2, B, st))) return e;                   // -> d pool2 [p8][64]
+    float *de3 = t2 + p16 / 4 * 64;
+    if ((e = pb(2, t2, 64, 16, dcat3, 192, 128, de3))) return e;                   // d e3b.out = pool + skip
+    float *t3 = de3 + p16 * 64;
+    if ((e = conv_bwd(ctx, 5, de3, 64, 0, t3, B, st))) return e;                   // -> d e3a.out
+    float *t4 = t3 + p16 * 64;
+    if ((e = conv_bwd(ctx, 4, t3, 64, 0, t4, B, st))) return e;                    // -> d pool1 [p16][32]
+    float *de2 = n->g_c + p32 * 96;   // g_c holds dcat2 [p32][96] first
+    if ((e = pb(1, t4, 32, 32, dcat2, 96, 64, de2))) return e;                     // d e2b.out
+    float *t5 = de2 + p32 * 32;
+    if ((e = conv_bwd(ctx, 3, de2, 32, 0, t5, B, st))) return e;                   // -> d e2a.out
+    float *t6 = t5 + p32 * 32;
+    if ((e = conv_bwd(ctx, 2, t5, 32, 0, t6, B, st))) return e;                    // -> d pool0 [p32][16]
+    float *de1 = n->g_a;   // free now
+    if ((e = pb(0, t6, 16, 64, n->g_cat, 48, 32, de1))) return e;                  // d e1b.out
+    if ((e = conv_bwd(ctx, 1, de1, 16, 0, n->g_b, B, st))) return e;               // -> d e1a.out
+    if ((e = conv_bwd(ctx, 0, n->g_b, 16, 0, nullptr, B, st))) return e;
+    (void)p64;
+    return HREBSD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ABI
+extern "C" int hrebsd_cnn_init(hrebsd_ctx *ctx, const float *params_host, long long n_params)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_net(ctx))) return e;
+    hr_cnn_net *n = ctx->cnn;
+    if (params_host) {
+        if (n_params != (long long)n->n_params) return HREBSD_EINVAL;
+        HR_CHECK(cudaMemcpy(n->W, params_host, n->n_params * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    HR_CHECK(cudaMemset(n->M, 0, n->n_params * sizeof(float)));
+    HR_CHECK(cudaMemset(n->V, 0, n->n_params * sizeof(float)));
+    n->step = 0;
+    if ((e = refresh_bf16(ctx, 0))) return e;
+    HR_CHECK(cudaDeviceSynchronize());
+    return HREBSD_OK;
+}
+
+extern "C" long long hrebsd_cnn_num_params(hrebsd_ctx *ctx)
+{
+    if (!ctx) return -1;
+    if (hr_set_device(ctx) || ensure_net(ctx)) return -1;
+    return (long long)ctx->cnn->n_params;
+}
+
+extern "C" int hrebsd_cnn_get_params(hrebsd_ctx *ctx, float *params_host, float *grads_host)
+{
+    if (!ctx || !ctx->cnn) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    HR_CHECK(cudaDeviceSynchronize());
+    if (params_host) HR_CHECK(cudaMemcpy(params_host, ctx->cnn->W, ctx->cnn->n_params * 4, cudaMemcpyDeviceToHost));
+    if (grads_host) HR_CHECK(cudaMemcpy(grads_host, ctx->cnn->G, ctx->cnn->n_params * 4, cudaMemcpyDeviceToHost));
+    return HREBSD_OK;
+}
+
+static int infer_common(hrebsd_ctx *ctx, int B, float *field, cudaStream_t st)
+{
+    int e = forward(ctx, B, st);
+    if (e) return e;
+    HR_CHECK(cudaMemcpyAsync(field, ctx->cnn->out, (size_t)B * 8192 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_cnn_infer(hrebsd_ctx *ctx, const uint16_t *x_bf16, int B, float *field64, void *stream)
+{
+    if (!ctx || !ctx->cnn || B < 0) return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!x_bf16 || !field64) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_acts(ctx, B))) return e;
+    cudaStream_t st = hr_stream(stream);
+    pack_nchw_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B,
+                                                                     ctx->cnn->x);
+    HR_LAUNCHED(ctx);
+    return infer_common(ctx, B, field64, st);
+}
+
+extern "C" int hrebsd_cnn_infer_patterns(hrebsd_ctx *ctx, const float *ref, const float *test, const int32_t *ref_idx,
+                                         int B, int H, int W, float *field64, void *stream)
+{
+    if (!ctx || !ctx->cnn || B < 0) return HREBSD_EINVAL;
+    if (H != W || H < 64 || H % 64) return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!ref || !test || !ref_idx || !field64) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_acts(ctx, B))) return e;
+    cudaStream_t st = hr_stream(stream);
+    pack_patterns_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(ref, test, ref_idx, B, H, W, ctx->cnn->x);
+    HR_LAUNCHED(ctx);
+    return infer_common(ctx, B, field64, st);
+}
+
+extern "C" int hrebsd_cnn_train_step(hrebsd_ctx *ctx, const uint16_t *x_bf16, const float *target, int B, float lr,
+                                     float *loss_out, void *stream)
+{
+    if (!ctx || !ctx->cnn || B <= 0 || !x_bf16 || !target || !(lr >= 0.0f)) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_acts(ctx, B))) return e;
+    hr_cnn_net *n = ctx->cnn;
+    cudaStream_t st = hr_stream(stream);
+    pack_nchw_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B, n->x);
+    HR_LAUNCHED(ctx);
+    if ((e = forward(ctx, B, st))) return e;
+    HR_CHECK(cudaMemsetAsync(n->loss, 0, sizeof(float), st));
+    HR_CHECK(cudaMemsetAsync(n->G, 0, n->n_params * sizeof(float), st));
+    mse_kernel<<<grid_for(ctx, (size_t)B * 8192), 256, 0, st>>>(n->out, target, (size_t)B * 8192, n->dout, n->loss);
+    HR_LAUNCHED(ctx);
+    if ((e = backward(ctx, B, st))) return e;
+    if (lr > 0.0f) {
+        n->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const double bc1 = 1.0 - pow((double)b1, n->step), bc2 = 1.0 - pow((double)b2, n->step);
+        const float lr_t = (float)(lr * sqrt(bc2) / bc1);
+        // eps scaled so that the update equals lr m_hat / (sqrt(v_hat) + 1e-8)
+        const float eps = (float)(1e-8 * sqrt(bc2));
+        adam_kernel<<<grid_for(ctx, n->n_params), 256, 0, st>>>(n->W, n->G, n->M, n->V, n->n_params, lr_t, b1, b2, eps);
+        HR_LAUNCHED(ctx);
+        if ((e = refresh_bf16(ctx, st))) return e;
+    }
+    if (loss_out) HR_CHECK(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return HREBSD_OK;
+}
+
+void hr_cnn_destroy(hrebsd_ctx *ctx)
+{
+    if (!ctx->cnn) return;
+    for (void *p : ctx->cnn->allocs) cudaFree(p);
+    delete ctx->cnn;
+    ctx->cnn = nullptr;
+}

@@ -194,6 +194,7 @@ int hrebsd_destroy(hrebsd_ctx *ctx)
     cudaDeviceSynchronize();
     for (auto &b : ctx->ws)
         if (b.ptr) cudaFree(b.ptr);
+    hr_cnn_destroy(ctx);
     for (auto &p : ctx->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);

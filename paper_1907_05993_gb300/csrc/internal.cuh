@@ -30,7 +30,10 @@ struct hr_buf {
     size_t bytes = 0;
 };
 
-enum { PROF_ITER = 0, PROF_CTRL, PROF_DEMONS_AUX, PROF_PRE, PROF_FIT, PROF_REMAP, PROF_XCF, PROF_SOLVE };
+enum { PROF_ITER = 0, PROF_CTRL, PROF_DEMONS_AUX, PROF_PRE, PROF_FIT, PROF_REMAP, PROF_XCF, PROF_SOLVE, PROF_CNN };
+
+struct hr_cnn_net;
+void hr_cnn_destroy(hrebsd_ctx *ctx);
 
 struct hr_pending {
     int cls;
@@ -47,6 +50,7 @@ struct hrebsd_ctx {
     int no_events = 0;   // set while a call must not create CUDA events
     int no_tma = 0;      // force the non-TMA demons iteration (testing, unsupported shapes)
     int *d_err = nullptr;   // device flag: a bounded wait gave up (static device symbol)
+    hr_cnn_net *cnn = nullptr;   // learned initialiser (allocated on first use)
     double prof_ms[HREBSD_PROF_CLASSES] = {};
     long long prof_launches[HREBSD_PROF_CLASSES] = {};
     unsigned long long *d_pixiters = nullptr;
