@@ -135,6 +135,11 @@ typedef struct {
 int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int flat, float *out,
                             void *stream);
 
+/* Box mean of f x f blocks, [n][H][W] -> [n][H/f][W/f] FP32 (equal to the
+ * pyramid level log2(f) of the registration up to rounding order; used for the
+ * inputs and targets of the learned initialiser).  H, W divisible by f. */
+int hrebsd_downsample_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int f, float *out, void *stream);
+
 /* a2-a4, a9 -- multi-resolution demons registration of B pairs (Section 1,
  * Eq. 1).  ref [R][H][W] and test [B][H][W] must be preprocessed
  * (hrebsd_preprocess_batch).  Pair b registers ref[ref_idx[b]] (moving) onto

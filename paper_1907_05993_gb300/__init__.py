@@ -96,6 +96,7 @@ def load(build: bool = False):
         "hrebsd_remap": (i, [vp, vp, vp, vp, i, i, i, C.POINTER(hrebsd_geometry), vp, vp]),
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
         "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
+        "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
         "hrebsd_cnn_num_params": (ll, [vp]),
         "hrebsd_cnn_init": (i, [vp, vp, ll]),
         "hrebsd_cnn_get_params": (i, [vp, vp, vp]),
@@ -191,6 +192,12 @@ def hrebsd_preprocess_batch(ctx, inp, n, H, W, flat, out, stream=None):
     f32 = _t().float32
     _chk(load().hrebsd_preprocess_batch(ctx, _p(inp, f32), n, H, W, int(flat), _p(out, f32), _s(stream)),
          "hrebsd_preprocess_batch")
+
+
+def hrebsd_downsample_batch(ctx, inp, n, H, W, f, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_downsample_batch(ctx, _p(inp, f32), n, H, W, f, _p(out, f32), _s(stream)),
+         "hrebsd_downsample_batch")
 
 
 def hrebsd_demons_register_batch(ctx, ref, test, ref_idx, R, B, H, W, params, init_field, field, iters,

@@ -224,3 +224,42 @@ extern "C" int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, 
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
 }
+
+// Box mean of f x f blocks: [n][H][W] -> [n][H/f][W/f] (the pyramid level
+// log2(f) in one pass; used to build the inputs and targets of the learned
+// initialiser at the 64x64 level).
+namespace {
+__global__ void downsample_kernel(const float *__restrict__ in, float *__restrict__ out, int n, int H, int W, int f)
+{
+    const int h = H / f, w = W / f;
+    const size_t total = (size_t)n * h * w;
+    const float s = 1.0f / (float)(f * f);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t img = idx / ((size_t)h * w);
+        const int rem = (int)(idx - img * h * w), i = rem / w, j = rem - i * w;
+        const float *p = in + img * H * W + (size_t)(i * f) * W + j * f;
+        float acc = 0.0f;
+        for (int a = 0; a < f; ++a)
+            for (int b = 0; b < f; ++b) acc += p[(size_t)a * W + b];
+        out[idx] = acc * s;
+    }
+}
+}  // namespace
+
+extern "C" int hrebsd_downsample_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int f, float *out,
+                                       void *stream)
+{
+    if (!ctx || n < 0 || f < 1 || H % f || W % f) return HREBSD_EINVAL;
+    if (n == 0) return HREBSD_OK;
+    if (!in || !out) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    size_t total = (size_t)n * (H / f) * (W / f);
+    int grid = (int)((total + 255) / 256);
+    if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+    hr_prof_begin(ctx, hr_stream(stream));
+    downsample_kernel<<<grid, 256, 0, hr_stream(stream)>>>(in, out, n, H, W, f);
+    hr_prof_end(ctx, PROF_PRE, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}

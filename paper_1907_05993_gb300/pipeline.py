@@ -12,8 +12,9 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (demons_params, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy, hrebsd_fit_rotation,
-               hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F, hrebsd_xcf_roi_batch)
+from . import (demons_params, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
+               hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
+               hrebsd_xcf_roi_batch)
 
 
 @dataclass
@@ -73,8 +74,13 @@ class Pipeline:
         hrebsd_preprocess_batch(self.ctx, raw, n, H, W, self.cfg.flat, out, stream)
         return out
 
-    def run(self, refs_raw, tests_raw, ref_idx, stream=None, init_field=None, start_level=-1, out=None):
-        """refs_raw [R,H,W], tests_raw [B,H,W] float32 CUDA; ref_idx [B] int32 CUDA."""
+    def run(self, refs_raw, tests_raw, ref_idx, stream=None, init_field=None, start_level=-1, out=None,
+            learned_caps=None):
+        """refs_raw [R,H,W], tests_raw [B,H,W] float32 CUDA; ref_idx [B] int32 CUDA.
+
+        learned_caps (per level, finest first): start the registration at the 64x64 level
+        from the learned initialiser's field (hrebsd_cnn_infer_patterns; the network must be
+        loaded in this pipeline's context) with these iteration caps."""
         t = self.torch
         c = self.cfg
         R, B = refs_raw.shape[0], tests_raw.shape[0]
@@ -92,8 +98,14 @@ class Pipeline:
         field = get("field", (B, 2, H, W), t.float32)
         iters = get("iters", (B, L), t.int32)
         status = get("status", (B,), t.int32)
-        self.params.start_level = start_level
-        hrebsd_demons_register_batch(self.ctx, ref_p, test_p, ref_idx, R, B, H, W, self.params, init_field, field,
+        params = self.params
+        params.start_level = start_level
+        if learned_caps is not None:
+            lvl = int(round(np.log2(H / 64)))
+            init_field = get("field64", (B, 2, 64, 64), t.float32)
+            hrebsd_cnn_infer_patterns(self.ctx, ref_p, test_p, ref_idx, B, H, W, init_field, stream)
+            params = demons_params(c.levels, learned_caps, c.alpha, c.sigma, c.sigma, c.stop_tol, c.stop_window, lvl)
+        hrebsd_demons_register_batch(self.ctx, ref_p, test_p, ref_idx, R, B, H, W, params, init_field, field,
                                      iters, status, stream)
         F1 = get("F_first", (B, 9), t.float64)
         Rf = get("R_finite", (B, 9), t.float64)

@@ -241,7 +241,10 @@ def pair_truth(spec: ScanSpec, p: int) -> np.ndarray:
 
 
 def ref_index(spec: ScanSpec, p: int) -> int:
-    """Grain of scan point p: the scan is a square grid cut into n_refs vertical strips."""
+    """Grain of scan point p: the scan is a square grid cut into n_refs vertical strips
+    (with as many references as pairs, every pair has its own)."""
+    if spec.n_refs >= spec.n_pairs:
+        return p
     side = int(math.isqrt(spec.n_pairs))
     if side * side != spec.n_pairs or spec.n_refs == 1:
         return p % spec.n_refs
@@ -290,6 +293,13 @@ def config3(n_pairs: int = 20_000) -> ScanSpec:
     """Large-misorientation scan at 256x256, mis U(6,12) deg, 200 counts."""
     return ScanSpec(n_pairs=n_pairs, H=256, W=256, n_refs=4, mis_lo_deg=6.0, mis_hi_deg=12.0,
                     strain=5e-4, strain_mode="sigma", counts=200.0, seed=3)
+
+
+def config4(n_pairs: int = 200_000) -> ScanSpec:
+    """Training pairs of the learned initialiser: as the single pair (128x128, strain norm
+    1e-4, 500 counts) with misorientation U(0, 12) deg, one reference orientation per pair."""
+    return ScanSpec(n_pairs=n_pairs, H=128, W=128, n_refs=n_pairs, mis_lo_deg=0.0, mis_hi_deg=12.0, strain=1e-4,
+                    strain_mode="norm", counts=500.0, seed=4)
 
 
 def config5(n_pairs: int = 160_000) -> ScanSpec:
