@@ -341,6 +341,109 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ learned initialiser vs plain
+def _oracle_pair5(args):
+    p, n_pairs = args
+    import numpy as np
+    import oracle
+    from synth import kikuchi as K
+    spec = K.config5(n_pairs)
+    ref = K.render_ref(spec, K.ref_index(spec, p)).astype(np.float64)
+    test = K.render_test(spec, p).astype(np.float64)
+    res = oracle.pipeline(ref, test, K.roi_grid(256, 256, 64, False), 64, spec.geom, 4, [100] * 4, 1.0, 1.0, 5, 1e-4)
+    return oracle.polar(res["F"])
+
+
+def run_learned(args, rank, world, local_rank):
+    """Config-5 scan: plain registration vs registration started from the learned field."""
+    import numpy as np
+    cores = os.cpu_count() or 1
+    n_pairs = 160_000
+    # seeded subset of the timed points for the oracle comparison
+    sub = list(range(0, args.pairs, max(1, args.pairs // args.oracle_pairs)))[:args.oracle_pairs]
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        R_oracle = pool.map(_oracle_pair5, [(p, n_pairs) for p in sub], chunksize=1)
+    t_oracle = time.perf_counter() - t0
+    import torch
+    import paper_1907_05993_gb300 as P
+    from paper_1907_05993_gb300 import learned as LN
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    from synth import gpu as SG
+    from synth import kikuchi as K
+    torch.cuda.set_device(local_rank)
+    spec5 = K.config5(n_pairs)
+    pairs = sorted(set(range(args.pairs)) | set(sub))
+    refs, tests, ridx, _ = SG.make_scan_gpu(spec5, pairs)
+    pos = {p: i for i, p in enumerate(pairs)}
+    roi = K.roi_grid(256, 256, 64, False)
+    cfg = PipelineConfig(256, 256, roi, 64, 4, (100, 100, 100, 100), 1.0, 1.0, 1e-4, 5)
+    pipe = Pipeline(cfg, device=local_rank)
+    # train the initialiser (config-4 recipe) in the pipeline's context
+    t0 = time.perf_counter()
+    x, y = LN.build_training_set(pipe.ctx, K.config4(args.train_pairs))
+    hist = LN.train(pipe.ctx, x, y, epochs=args.epochs, batch=256, lr=2e-3, seed=0)
+    del x, y
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    caps_l = tuple(args.learned_caps)
+    B = len(pairs)
+    stream = torch.cuda.current_stream()
+
+    def timed(learned):
+        out = {}
+        kw = {"learned_caps": caps_l} if learned else {}
+        for _ in range(args.warmup):
+            pipe.run(refs, tests, ridx, out=out, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pipe.run(refs, tests, ridx, out=out, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        F = out["F"].cpu().numpy().reshape(-1, 3, 3)
+        its = out["iters"].cpu().numpy()
+        return B * args.steps / t, F, its
+
+    v_plain, F_plain, it_plain = timed(False)
+    v_learn, F_learn, it_learn = timed(True)
+    import oracle as O
+
+    def rot_deg(Ra, Rb):
+        c = np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1)
+        return float(np.degrees(np.arccos(c)))
+    e_plain = np.array([rot_deg(O.polar(F_plain[pos[p]]), R) for p, R in zip(sub, R_oracle)])
+    e_learn = np.array([rot_deg(O.polar(F_learn[pos[p]]), R) for p, R in zip(sub, R_oracle)])
+    line = {
+        "metric": METRIC + "; learned-init vs plain", "workload": "learned-init vs plain",
+        "value": v_learn, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic (seeded kinematic Kikuchi generator)",
+        "config": {"workload": f"config-5 scan 400x400 (first {args.pairs} points), 256x256, 8 grains, "
+                               f"mis U(0,12) deg; plain: 4 levels <=100 it; learned: start at 64x64 from the "
+                               f"network, caps {list(caps_l)}", "pairs": B,
+                   "training": f"{args.train_pairs} config-4 pairs, {args.epochs} epochs, batch 256, Adam 2e-3"},
+        "plain_pairs_per_s": v_plain, "learned_pairs_per_s": v_learn, "speedup": v_learn / v_plain,
+        "iters_mean_per_level_plain": [float(a) for a in it_plain.mean(axis=0)],
+        "iters_mean_per_level_learned": [float(a) for a in it_learn.mean(axis=0)],
+        "oracle_subset": len(sub), "oracle_seconds": t_oracle, "oracle_cores": cores,
+        "rot_err_vs_oracle_deg": {
+            "plain": {"median": float(np.median(e_plain)), "p95": float(np.percentile(e_plain, 95)),
+                      "frac_le_1e-4": float(np.mean(e_plain <= 1e-4))},
+            "learned": {"median": float(np.median(e_learn)), "p95": float(np.percentile(e_learn, 95)),
+                        "frac_le_1e-4": float(np.mean(e_learn <= 1e-4))}},
+        "training_loss_per_epoch": hist, "training_seconds": t_train,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pipe.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,12 +454,19 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("scan", "learned"), default="scan")
+    ap.add_argument("--train-pairs", type=int, default=200_000)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--oracle-pairs", type=int, default=500)
+    ap.add_argument("--learned-caps", type=int, nargs=4, default=(100, 100, 100, 0))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "learned":
+        return run_learned(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 
