@@ -229,8 +229,9 @@ def run_ours(args, rank, world, local_rank):
     B = args.pairs
     # this rank's shard of a world * B point scan (independent pairs)
     from synth import kikuchi as K
+    from paper_1907_05993_gb300.shard import max_over_ranks, shard_range
     spec = K.ScanSpec(**{**spec.__dict__, "n_pairs": B * world})
-    pairs = range(rank * B, (rank + 1) * B)
+    pairs = shard_range(B * world, rank, world)
     refs, tests, ridx, _ = synth_gpu.make_scan_gpu(spec, pairs)
     torch.cuda.synchronize()
     cfg = PipelineConfig(wl["H"], wl["W"], wl["roi"], wl["S"], wl["levels"], wl["caps"], 1.0, 1.0,
@@ -262,11 +263,7 @@ def run_ours(args, rank, world, local_rank):
     launches = P.hrebsd_launch_count(pipe.ctx) - l0
     prof = P.hrebsd_profile_read(pipe.ctx)
     P.hrebsd_profile_enable(pipe.ctx, False)
-    t = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt)
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, device="cuda")
     value = world * B * args.steps / t
     iters = out["iters"].cpu().numpy()
     status = out["status"].cpu().numpy()
@@ -295,11 +292,8 @@ def run_ours(args, rank, world, local_rank):
         h_st.copy_(out["status"], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    te = e0.elapsed_time(e1) / 1e3
+    te = max_over_ranks(e0.elapsed_time(e1) / 1e3, device="cuda")
     if dist:
-        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt)
         dist.barrier()
     h2d = tests.numel() * 4 + refs.numel() * 4 + ridx.numel() * 4
     d2h = B * 9 * 8 * 2 + B * 4
