@@ -226,6 +226,21 @@ int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N
                    const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
                    void *stream);
 
+/* f1 -- strain and stress of each pair (Eq. 13-16; Supplementary Part 2).
+ * F [B][9]: detector-frame deformation gradients (e.g. from hrebsd_solve_F).
+ * F_S = T F T^T with the tilt rotation T = [[c, s, 0], [-s, c, 0], [0, 0, 1]]
+ * of Eq. 13 (c, s of tilt_rad), Eq. 14.  With traction_free the scale of F_S
+ * (undetermined by Eq. 3) is set so that sigma_33 = 0.  Strain
+ * eps = 1/2 (F_S F_S^T - I) (Eq. 15, exact for the finite rotation of the
+ * remapping); stress sigma = C_S : eps (Eq. 16), C_S the cubic stiffness
+ * (c11, c12, c44 in Pa; nickel 276e9, 159e9, 132e9) rotated to the sample frame
+ * by the passive orientation matrix g[ref_idx[b]] (sample -> crystal, [R][9]).
+ * ref_idx may be NULL (all pairs use g[0]); an index outside [0, R) gives NaN
+ * outputs.  Outputs [B][9]: F_S (may be NULL), eps, sigma (Pa). */
+int hrebsd_strain_stress(hrebsd_ctx *ctx, const double *F, const int32_t *ref_idx, const double *g, int R, int B,
+                         double tilt_rad, double c11, double c12, double c44, int traction_free, double *F_S,
+                         double *eps, double *sigma, void *stream);
+
 /* a10 -- learned initialiser of the coarse field (project addition; the paper
  * has none: its future-work remark is to optimise the multi-resolution
  * demons).  A 4-level U-Net (3x3 convolutions 16-32-64-128, 2x2 max-pool,

@@ -20,7 +20,7 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -97,6 +97,8 @@ def load(build: bool = False):
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
         "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
         "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
+        "hrebsd_strain_stress": (i, [vp, vp, vp, vp, i, i, C.c_double, C.c_double, C.c_double, C.c_double, i, vp,
+                                     vp, vp, vp]),
         "hrebsd_cnn_num_params": (ll, [vp]),
         "hrebsd_cnn_init": (i, [vp, vp, ll]),
         "hrebsd_cnn_get_params": (i, [vp, vp, vp]),
@@ -247,6 +249,18 @@ def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, s
     _chk(load().hrebsd_solve_F(ctx, _p(q, t.float32), _p(roi_xy, t.int32), N, B, H, W, C.byref(geom),
                                _p(R_finite, t.float64), _p(F, t.float64), _p(pair_status, t.int32), _s(stream)),
          "hrebsd_solve_F")
+
+
+NI_STIFFNESS = (276e9, 159e9, 132e9)
+
+
+def hrebsd_strain_stress(ctx, F, ref_idx, g, R, B, tilt_rad, stiffness=NI_STIFFNESS, traction_free=True, F_S=None,
+                         eps=None, sigma=None, stream=None):
+    t = _t()
+    c11, c12, c44 = stiffness
+    _chk(load().hrebsd_strain_stress(ctx, _p(F, t.float64), _p(ref_idx, t.int32), _p(g, t.float64), R, B,
+                                     float(tilt_rad), c11, c12, c44, int(traction_free), _p(F_S, t.float64),
+                                     _p(eps, t.float64), _p(sigma, t.float64), _s(stream)), "hrebsd_strain_stress")
 
 
 # ------------------------------------------------------------------ learned initialiser

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import (demons_params, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
                hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
-               hrebsd_xcf_roi_batch)
+               hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
 
 
 @dataclass
@@ -120,3 +120,17 @@ class Pipeline:
         F = get("F", (B, 9), t.float64)
         hrebsd_solve_F(self.ctx, q, self.roi, N, B, H, W, self.geom, Rf, F, status, stream)
         return o
+
+    def strain_stress(self, out, g, ref_idx, tilt_rad, stiffness=NI_STIFFNESS, traction_free=True, stream=None):
+        """Post-processing of Eq. 13-16 on the F of ``run``: adds F_S, eps, sigma [B, 9] (FP64) to ``out``.
+
+        g: [R, 9] float64 CUDA passive orientation matrices of the references."""
+        t = self.torch
+        F = out["F"]
+        B = F.shape[0]
+        for name in ("F_S", "eps", "sigma"):
+            if name not in out:
+                out[name] = self._buf(name, (B, 9), t.float64)
+        hrebsd_strain_stress(self.ctx, F, ref_idx, g, g.shape[0], B, tilt_rad, stiffness, traction_free, out["F_S"],
+                             out["eps"], out["sigma"], stream)
+        return out

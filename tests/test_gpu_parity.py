@@ -353,6 +353,14 @@ def test_pipeline_single_pair_workload(torch, lib, oracle):
     assert np.abs(Fg - exp["F"]).max() <= F_TOL
     tie = out["near_tie"].cpu().numpy()[0].astype(bool) | exp["near_tie"]
     assert np.array_equal(out["peak"].cpu().numpy()[0][~tie], exp["peak"][~tie])
+    # strain / stress post-processing (Eq. 13-16) of the pipeline's F against the oracle's on the oracle's F
+    from oracle import strain as S
+    g = K.random_rotation(7, 0)
+    pipe.strain_stress(out, cuda(torch, g.reshape(1, 9)), cuda(torch, ridx), np.radians(20.0), traction_free=False)
+    torch.cuda.synchronize()
+    _, e_exp, s_exp = S.strain_stress(exp["F"], g, np.radians(20.0), traction_free=False)
+    assert np.abs(out["eps"].cpu().numpy().reshape(3, 3) - e_exp).max() <= 2 * F_TOL
+    assert np.abs(out["sigma"].cpu().numpy().reshape(3, 3) - s_exp).max() <= 2 * F_TOL * 1.2e12
     pipe.close()
 
 
@@ -382,3 +390,29 @@ def test_tma_and_plain_iteration_paths_agree(torch, lib, oracle, H, W, levels, c
     for b in range(3):
         exp, _ = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, 1.0, 1.0, 1.0)
         assert_field_parity(f0[b], exp, caps)
+
+
+# ------------------------------------------------------------------ strain / stress (Eq. 13-16)
+@pytest.mark.parametrize("traction_free", [True, False])
+def test_strain_stress_parity(torch, lib, ctx, traction_free):
+    from oracle import strain as S
+    rng = np.random.default_rng(13)
+    B, R = 9, 3
+    gs = np.stack([K.random_rotation(20 + r, 0) for r in range(R)])
+    Fs = []
+    for b in range(B):
+        e = rng.normal(0, 4e-4, (3, 3))
+        F = K.axis_angle(rng.normal(size=3), np.radians(rng.uniform(0, 10))) @ (np.eye(3) + (e + e.T) / 2)
+        Fs.append(F / np.cbrt(np.linalg.det(F)))
+    Fs = np.stack(Fs)
+    ridx = (np.arange(B) % R).astype(np.int32)
+    out = [torch.empty((B, 9), dtype=torch.float64, device="cuda") for _ in range(3)]
+    tilt = np.radians(20.0)
+    lib.hrebsd_strain_stress(ctx, cuda(torch, Fs.reshape(B, 9)), cuda(torch, ridx), cuda(torch, gs.reshape(R, 9)), R, B,
+                             tilt, traction_free=traction_free, F_S=out[0], eps=out[1], sigma=out[2])
+    FS, E, SG = [o.cpu().numpy().reshape(B, 3, 3) for o in out]
+    for b in range(B):
+        f_e, e_e, s_e = S.strain_stress(Fs[b], gs[ridx[b]], tilt, traction_free=traction_free)
+        assert np.abs(FS[b] - f_e).max() < 1e-12
+        assert np.abs(E[b] - e_e).max() < 1e-12
+        assert np.abs(SG[b] - s_e).max() < 1e-9 * max(1.0, np.abs(s_e).max())
