@@ -265,6 +265,13 @@ def run_ours(args, rank, world, local_rank):
     P.hrebsd_profile_enable(pipe.ctx, False)
     t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, device="cuda")
     value = world * B * args.steps / t
+    tune_ms = pipe._tuned.get((B, wl["H"], wl["W"]))
+    tile_choice = None if tune_ms is None else [
+        {"level": l, "shape": "x".join(map(str, P.TILE_SHAPES[P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l,
+                                                                                           wl["W"] >> l)])),
+         "ms_per_iteration_by_shape": {"x".join(map(str, P.TILE_SHAPES[v])): round(float(tune_ms[l, v]), 4)
+                                       for v in range(P.TILE_VARIANTS) if np.isfinite(tune_ms[l, v])}}
+        for l in range(wl["levels"])]
     iters = out["iters"].cpu().numpy()
     status = out["status"].cpu().numpy()
 
@@ -323,6 +330,7 @@ def run_ours(args, rank, world, local_rank):
                          "avg_launch_ms": it["ms"] / max(1, it["launches"]),
                          "share_of_step": it["ms"] / total_ms if total_ms else None},
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if k != "pixel_iters"},
+            "demons_tile_shape_per_level": tile_choice,
             "demons_iters_mean_per_level": [float(x) for x in iters.mean(axis=0)],
             "pairs_capped": int(np.sum(status & 1)),
             "clocks": clk,

@@ -79,6 +79,16 @@ int hrebsd_device_error(hrebsd_ctx *ctx);
  * without tensor-memory-accelerator tile loads (same results; used to test
  * both paths; the environment variable HREBSD_NO_TMA sets it at creation). */
 #define HREBSD_OPT_NO_TMA 1
+/* HREBSD_OPT_GRAPHS (value 0/1, default 1; the environment variable
+ * HREBSD_NO_GRAPHS clears it at creation): each pyramid level of a
+ * registration (its list reset, cap x (iteration, stop control), finalize and
+ * prolongation launches) is captured once into a CUDA graph on a private
+ * stream and replayed on the caller's stream; the cache (32 graphs, least
+ * recently used replaced) is keyed by every pointer, size and parameter of the
+ * launches.  Not used while tracing is on, inside the allocation-free entry
+ * point, or when the caller's stream is itself capturing (the launches then go
+ * into the caller's graph).  Same results either way. */
+#define HREBSD_OPT_GRAPHS 2
 int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value);
 
 /* Tracing: per kernel class, CUDA-event time of every launch (events are
@@ -184,6 +194,29 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
                                          const int32_t *ref_idx, int R, int B, int H, int W,
                                          const hrebsd_demons_params *params, const float *init_field, float *field,
                                          int32_t *iters, int32_t *pair_status, void *stream);
+
+/* Tile shapes of the TMA-fed demons iteration (batching; the paper has no
+ * counterpart): 0 = 64x32 outputs (2 CTAs per SM), 1 = 32x32 (3 per SM),
+ * 2 = 64x16 (3 per SM).  Shapes 1 and 2 exist for the Gaussian radius 3
+ * (sigma = 1); other radii always use shape 0.  Every shape computes each
+ * output pixel with the same operations in the same order, so the field is
+ * the same; only the grouping of the per-tile SSD partials changes. */
+#define HREBSD_TILE_VARIANTS 3
+
+/* Autotuner: for each pyramid level of an H x W registration with `params`,
+ * time every tile shape on synthetic striped patterns displaced by a small
+ * rotation field (min(B, 2048) pairs; 2 warm-up then 5 timed iterations,
+ * CUDA events on `stream`) and keep the fastest for later registrations of
+ * that level size in this context.  Synchronises `stream`; uses context
+ * workspace.  ms_out (host, nullable): [levels][HREBSD_TILE_VARIANTS]
+ * milliseconds per iteration, NaN where a shape is unavailable.  Returns
+ * HREBSD_EINVAL for invalid parameters (as hrebsd_demons_register_batch). */
+int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebsd_demons_params *params, float *ms_out,
+                    void *stream);
+/* Set (variant 0..HREBSD_TILE_VARIANTS-1) or clear (-1) the tile shape used
+ * for levels of size h x w; get returns the current choice (0 if none). */
+int hrebsd_set_tile_variant(hrebsd_ctx *ctx, int h, int w, int variant);
+int hrebsd_get_tile_variant(const hrebsd_ctx *ctx, int h, int w);
 
 /* a5 -- rotation fit (Section 2, Eq. 2-5).  The field [B][2][H][W] is
  * sampled bilinearly at the N ROI centres c (index coordinates c - 0.5);

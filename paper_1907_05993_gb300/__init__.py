@@ -20,7 +20,8 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
+    "hrebsd_autotune", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -97,6 +98,9 @@ def load(build: bool = False):
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
         "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
         "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
+        "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
+        "hrebsd_set_tile_variant": (i, [vp, i, i, i]),
+        "hrebsd_get_tile_variant": (i, [vp, i, i]),
         "hrebsd_strain_stress": (i, [vp, vp, vp, vp, i, i, C.c_double, C.c_double, C.c_double, C.c_double, i, vp,
                                      vp, vp, vp]),
         "hrebsd_cnn_num_params": (ll, [vp]),
@@ -166,6 +170,7 @@ def hrebsd_launch_count(ctx) -> int:
 
 
 OPT_NO_TMA = 1
+OPT_GRAPHS = 2
 
 
 def hrebsd_device_error(ctx):
@@ -249,6 +254,29 @@ def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, s
     _chk(load().hrebsd_solve_F(ctx, _p(q, t.float32), _p(roi_xy, t.int32), N, B, H, W, C.byref(geom),
                                _p(R_finite, t.float64), _p(F, t.float64), _p(pair_status, t.int32), _s(stream)),
          "hrebsd_solve_F")
+
+
+TILE_VARIANTS = 3
+TILE_SHAPES = ((64, 32), (32, 32), (64, 16))
+
+
+def hrebsd_autotune(ctx, B, H, W, params, stream=None):
+    """Time every tile shape per pyramid level and keep the fastest; returns ms [levels][TILE_VARIANTS]."""
+    import numpy as np
+    ms = (C.c_float * (params.levels * TILE_VARIANTS))()
+    _chk(load().hrebsd_autotune(ctx, B, H, W, C.byref(params), ms, _s(stream)), "hrebsd_autotune")
+    return np.array(ms[:], dtype=np.float32).reshape(params.levels, TILE_VARIANTS)
+
+
+def hrebsd_set_tile_variant(ctx, h, w, variant):
+    _chk(load().hrebsd_set_tile_variant(ctx, h, w, variant), "hrebsd_set_tile_variant")
+
+
+def hrebsd_get_tile_variant(ctx, h, w):
+    v = load().hrebsd_get_tile_variant(ctx, h, w)
+    if v < 0:
+        _chk(v, "hrebsd_get_tile_variant")
+    return v
 
 
 NI_STIFFNESS = (276e9, 159e9, 132e9)

@@ -183,6 +183,7 @@ int hrebsd_create(hrebsd_ctx **ctx, int device)
         return hr_cuda_error(e, "hrebsd_create", __FILE__, __LINE__);
     }
     if (getenv("HREBSD_NO_TMA")) c->no_tma = 1;
+    if (getenv("HREBSD_NO_GRAPHS")) c->graphs = 0;
     *ctx = c;
     return HREBSD_OK;
 }
@@ -195,6 +196,8 @@ int hrebsd_destroy(hrebsd_ctx *ctx)
     for (auto &b : ctx->ws)
         if (b.ptr) cudaFree(b.ptr);
     hr_cnn_destroy(ctx);
+    for (auto &g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto &p : ctx->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -237,6 +240,7 @@ int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value)
     if (!ctx) return HREBSD_EINVAL;
     switch (option) {
     case HREBSD_OPT_NO_TMA: ctx->no_tma = value ? 1 : 0; return HREBSD_OK;
+    case HREBSD_OPT_GRAPHS: ctx->graphs = value ? 1 : 0; return HREBSD_OK;
     default: return HREBSD_EINVAL;
     }
 }

@@ -108,17 +108,17 @@ __device__ __forceinline__ float2 bilinear2_clamped(const float2 *__restrict__ M
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-template <int RAD>
+template <int RAD, int TX_ = TX, int TY_ = TY>
 struct Geo {
-    static constexpr int BW = TX + 2 * RAD, BH = TY + 2 * RAD;       // u and du (T + r)
+    static constexpr int BW = TX_ + 2 * RAD, BH = TY_ + 2 * RAD;       // u and du (T + r)
     static constexpr int BWP = round_up(BW, RUN), BHP = round_up(BH, RUN);
-    static constexpr int AW = TX + 4 * RAD, AH = TY + 4 * RAD;       // s (T + 2r)
+    static constexpr int AW = TX_ + 4 * RAD, AH = TY_ + 4 * RAD;       // s (T + 2r)
     static constexpr int AHP = BHP + 2 * RAD;                        // rows read by padded y-pass runs
     static constexpr int AST = pad_stride(BWP + 2 * RAD);            // s tile row stride (>= AW)
     static constexpr int XST = pad_stride(BWP);                      // x-pass of s row stride
     static constexpr int UST = BWP;                                  // u row stride
     static constexpr int DST = pad_stride(BWP);                      // du row stride
-    static constexpr int XDST = pad_stride(TX);                      // x-pass of du row stride
+    static constexpr int XDST = pad_stride(TX_);                      // x-pass of du row stride
     static constexpr int FW = BW + 2, FH = BH + 2;                   // test image (T + r + 1)
     static constexpr int SA = (AHP * AST > BH * DST) ? AHP * AST : BH * DST;   // float2
     static constexpr int SX = (AHP * XST > BH * XDST) ? AHP * XST : BH * XDST; // float2
@@ -177,13 +177,14 @@ struct TileRef {
     int pair, tile, x0, y0;
 };
 
+template <int TX_ = TX, int TY_ = TY>
 __device__ __forceinline__ TileRef tile_of(const IterArgs &a, long long item)
 {
     TileRef t;
     t.pair = a.active[item / a.tiles];
     t.tile = (int)(item % a.tiles);
-    t.x0 = (t.tile % a.tiles_x) * TX;
-    t.y0 = (t.tile / a.tiles_x) * TY;
+    t.x0 = (t.tile % a.tiles_x) * TX_;
+    t.y0 = (t.tile / a.tiles_x) * TY_;
     return t;
 }
 
@@ -383,11 +384,11 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_kernel(IterArgs a
 // force stage works on runs of 4 pixels per thread with the gradient stencil
 // and field read once per run; runs that touch the image border take the
 // per-pixel clamped path.
-template <int RAD>
+template <int RAD, int TX_, int TY_>
 struct GeoT {
-    using L = Geo<RAD>;
+    using L = Geo<RAD, TX_, TY_>;
     static constexpr int FOFF = 4 * ((RAD + 1 + 3) / 4);   // test-image halo, rounded to 16 bytes
-    static constexpr int FWB = TX + 2 * FOFF;               // test-image tile columns
+    static constexpr int FWB = TX_ + 2 * FOFF;               // test-image tile columns
     static constexpr int FH = L::FH;
     static constexpr uint32_t S_BYTES = (uint32_t)L::AHP * L::AST * 8;
     static constexpr uint32_t F_BYTES = (uint32_t)FH * FWB * 4;
@@ -428,13 +429,13 @@ __device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, 
     }
 }
 
-template <int RAD>
-__global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
-                                                                          const __grid_constant__ CUtensorMap tmF,
-                                                                          IterArgs a)
+template <int RAD, int TX_, int TY_, int MINB>
+__global__ void __launch_bounds__(kIterThreads, MINB) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
+                                                                             const __grid_constant__ CUtensorMap tmF,
+                                                                             IterArgs a)
 {
-    using L = Geo<RAD>;
-    using G = GeoT<RAD>;
+    using L = Geo<RAD, TX_, TY_>;
+    using G = GeoT<RAD, TX_, TY_>;
     constexpr int NT = kIterThreads;
     extern __shared__ __align__(1024) unsigned char smraw[];
     float2 *sS = reinterpret_cast<float2 *>(smraw + G::S_OFF);   // [AHP][AST]
@@ -476,13 +477,13 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
     };
     long long item = blockIdx.x;
     if (tid == 0 && item < work) {
-        const TileRef t = tile_of(a, item);
+        const TileRef t = tile_of<TX_, TY_>(a, item);
         issue_S(t);
         issue_F(t);
     }
     uint32_t phase = 0;
     for (; item < work; item += gridDim.x) {
-        const TileRef cur = tile_of(a, item);
+        const TileRef cur = tile_of<TX_, TY_>(a, item);
         const long long next = item + gridDim.x;
         const int x0 = cur.x0, y0 = cur.y0;
         const float *M = a.Mref + (size_t)__ldg(a.ref_idx + cur.pair) * plane;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
         __syncthreads();
         if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
             hr_tma::fence_proxy_async();
-            issue_S(tile_of(a, next));
+            issue_S(tile_of<TX_, TY_>(a, next));
         }
         constexpr int NSY = L::BHP / RUN;
         for (int it = tid; it < NSY * L::BWP; it += NT) {
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
         for (int it = tid; it < NRUN * L::BH; it += NT) {
             const int r = it / NRUN, c0 = 4 * (it - r * NRUN);
             const int vy = y0 - RAD + r, vx0 = x0 - RAD + c0;
-            const bool rowT = r >= RAD && r < RAD + TY && vy < h;
+            const bool rowT = r >= RAD && r < RAD + TY_ && vy < h;
             const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
             const float4 *up = reinterpret_cast<const float4 *>(sU + r * L::UST + c0);
             const float4 ua = up[0], ub = up[1];
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
                 const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
                 du[i] = make_float2(t * gx, t * gy);
                 const int c = c0 + i;
-                if (rowT && c >= RAD && c < RAD + TX && vx < w) ssd = fmaf(d, d, ssd);
+                if (rowT && c >= RAD && c < RAD + TX_ && vx < w) ssd = fmaf(d, d, ssd);
             }
             float4 *dp = reinterpret_cast<float4 *>(sD + r * L::DST + c0);
             dp[0] = make_float4(du[0].x, du[0].y, du[1].x, du[1].y);
@@ -581,10 +582,10 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
         __syncthreads();
         if (tid == 0 && next < work) {   // the test-image tile is consumed: fetch the next one
             hr_tma::fence_proxy_async();
-            issue_F(tile_of(a, next));
+            issue_F(tile_of<TX_, TY_>(a, next));
         }
         // ---- G_u * du: x pass on rows of T + r, columns of T
-        constexpr int NSXD = TX / RUN;
+        constexpr int NSXD = TX_ / RUN;
         for (int it = tid; it < NSXD * L::BH; it += NT) {
             const int seg = it / L::BH, row = it - seg * L::BH;
             run_x<RAD>(sD + row * L::DST + seg * RUN, sX + row * L::XDST + seg * RUN, tu);
@@ -592,8 +593,8 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_tma_kernel(const 
         __syncthreads();
         // ---- y pass, s_{k+1} = u_k + G_u * du on T
         float2 *dst = a.out + (size_t)cur.pair * plane;
-        for (int it = tid; it < (TY / RUN) * TX; it += NT) {
-            const int seg = it / TX, col = it - seg * TX;
+        for (int it = tid; it < (TY_ / RUN) * TX_; it += NT) {
+            const int seg = it / TX_, col = it - seg * TX_;
             float2 acc[RUN];
             run_y<RAD>(sX + seg * RUN * L::XDST + col, L::XDST, tu, acc);
             const int gx = x0 + col;
@@ -777,17 +778,17 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
-template <int RAD>
+template <int RAD, int TX_, int TY_, int MINB>
 int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a, int max_items,
                     cudaStream_t st)
 {
-    constexpr size_t smem = GeoT<RAD>::BYTES;
+    constexpr size_t smem = GeoT<RAD, TX_, TY_>::BYTES;
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        HR_CHECK(cudaFuncSetAttribute(demons_iter_tma_kernel<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, demons_iter_tma_kernel<RAD>, kIterThreads, smem));
+        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB>;
+        HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kIterThreads, smem));
         if (occ < 1) occ = 1;
         configured_dev = ctx->device;
     }
@@ -795,7 +796,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    demons_iter_tma_kernel<RAD><<<grid, kIterThreads, smem, st>>>(tmS, tmF, a);
+    demons_iter_tma_kernel<RAD, TX_, TY_, MINB><<<grid, kIterThreads, smem, st>>>(tmS, tmF, a);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -803,12 +804,12 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
 
 // Tensor maps of one level for the TMA-fed iteration: the two s buffers
 // (float2 [B][h][w] seen as FP32 [B][h][2w]) and the test images.
-template <int RAD>
+template <int RAD, int TX_, int TY_>
 bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w, CUtensorMap *tmS,
                        CUtensorMap *tmF)
 {
-    using L = Geo<RAD>;
-    using G = GeoT<RAD>;
+    using L = Geo<RAD, TX_, TY_>;
+    using G = GeoT<RAD, TX_, TY_>;
     const uint64_t row2 = (uint64_t)w * 8, img2 = row2 * h, row1 = (uint64_t)w * 4, img1 = row1 * h;
     if (hr_encode_tmap_3d(&tmS[0], s0, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
     if (hr_encode_tmap_3d(&tmS[1], s1, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
@@ -816,32 +817,129 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, i
     return true;
 }
 
-bool encode_maps(int rad, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w, CUtensorMap *tmS,
-                 CUtensorMap *tmF)
+// Tile shapes of the TMA-fed iteration (autotuned per level).  Every shape
+// computes each output pixel with the same arithmetic in the same order, so
+// the field does not depend on the choice; only the per-tile SSD partials
+// (and hence the last bits of the level SSD) are grouped differently.  The
+// extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
+// use shape 0.
+constexpr int kTileVariants = 3;
+constexpr int kVarTX[kTileVariants] = {64, 32, 64};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16};
+constexpr int kMinTX = 32, kMinTY = 16;
+bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }   // smallest tile extents (sizes the SSD partials)
+static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
+
+int hr_tuned_variant(const hrebsd_ctx *ctx, int rad, int h, int w)
 {
-    switch (rad) {
-    case 1: return encode_level_maps<1>(s0, s1, ftest, B, h, w, tmS, tmF);
-    case 2: return encode_level_maps<2>(s0, s1, ftest, B, h, w, tmS, tmF);
-    case 3: return encode_level_maps<3>(s0, s1, ftest, B, h, w, tmS, tmF);
-    case 4: return encode_level_maps<4>(s0, s1, ftest, B, h, w, tmS, tmF);
-    case 5: return encode_level_maps<5>(s0, s1, ftest, B, h, w, tmS, tmF);
-    case 6: return encode_level_maps<6>(s0, s1, ftest, B, h, w, tmS, tmF);
-    default: return false;
-    }
+    for (const auto &t : ctx->tune)
+        if (t.h == h && t.w == w) return variant_ok(rad, t.var) ? t.var : 0;
+    return 0;
 }
 
-int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a,
-                      int max_items, cudaStream_t st)
+// ---------------------------------------------------------------------------
+// CUDA graph per pyramid level.  The launches of a level are captured once on
+// a private stream and replayed on the caller's stream; the cache is keyed by
+// every pointer, size and parameter the launches depend on.
+bool hr_graph_usable(hrebsd_ctx *ctx, cudaStream_t st)
 {
-    switch (rad) {
-    case 1: return launch_iter_tma<1>(ctx, tmS, tmF, a, max_items, st);
-    case 2: return launch_iter_tma<2>(ctx, tmS, tmF, a, max_items, st);
-    case 3: return launch_iter_tma<3>(ctx, tmS, tmF, a, max_items, st);
-    case 4: return launch_iter_tma<4>(ctx, tmS, tmF, a, max_items, st);
-    case 5: return launch_iter_tma<5>(ctx, tmS, tmF, a, max_items, st);
-    case 6: return launch_iter_tma<6>(ctx, tmS, tmF, a, max_items, st);
-    default: return HREBSD_EINVAL;
+    if (!ctx->graphs || ctx->prof_on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;   // the caller is capturing: launch into its graph
     }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cap_stream = nullptr;
+        return false;
+    }
+    return true;
+}
+
+template <typename Emit>
+int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit &&emit)
+{
+    constexpr size_t kMaxGraphs = 32;
+    hr_graph_entry *hit = nullptr;
+    for (auto &g : ctx->graph_cache)
+        if (!memcmp(&g.key, &key, sizeof key)) {
+            hit = &g;
+            break;
+        }
+    if (!hit) {
+        const long long n0 = ctx->launches;
+        HR_CHECK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int e = emit(ctx->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &g);
+        const long long nodes = ctx->launches - n0;
+        ctx->launches = n0;
+        if (e || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e ? e : hr_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return hr_cuda_error(ie, "cudaGraphInstantiate", __FILE__, __LINE__);
+        if (ctx->graph_cache.size() >= kMaxGraphs) {
+            size_t lru = 0;
+            for (size_t i = 1; i < ctx->graph_cache.size(); ++i)
+                if (ctx->graph_cache[i].last < ctx->graph_cache[lru].last) lru = i;
+            cudaGraphExecDestroy(ctx->graph_cache[lru].exec);
+            ctx->graph_cache.erase(ctx->graph_cache.begin() + lru);
+        }
+        ctx->graph_cache.push_back(hr_graph_entry{key, ex, nodes, 0});
+        hit = &ctx->graph_cache.back();
+    }
+    hit->last = ++ctx->graph_clock;
+    HR_CHECK(cudaGraphLaunch(hit->exec, st));
+    ctx->launches += hit->nodes;
+    return HREBSD_OK;
+}
+
+
+#define HR_TMA_VARIANTS(RAD, CALL)                                                                                 \
+    case 0: return CALL(RAD, 64, 32, 2);                                                                           \
+    case 1: if (RAD == 3) return CALL(3, 32, 32, 3); break;                                                        \
+    case 2: if (RAD == 3) return CALL(3, 64, 16, 3); break;
+
+bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w,
+                 CUtensorMap *tmS, CUtensorMap *tmF)
+{
+#define HR_ENC(R, X, Y, MB) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
+    switch (rad) {
+    case 1: return var == 0 && HR_ENC(1, 64, 32, 2);
+    case 2: return var == 0 && HR_ENC(2, 64, 32, 2);
+    case 3:
+        switch (var) { HR_TMA_VARIANTS(3, HR_ENC) default: break; }
+        return false;
+    case 4: return var == 0 && HR_ENC(4, 64, 32, 2);
+    case 5: return var == 0 && HR_ENC(5, 64, 32, 2);
+    case 6: return var == 0 && HR_ENC(6, 64, 32, 2);
+    default: return false;
+    }
+#undef HR_ENC
+}
+
+int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, int var, const CUtensorMap &tmS, const CUtensorMap &tmF,
+                      const IterArgs &a, int max_items, cudaStream_t st)
+{
+#define HR_LT(R, X, Y, MB) launch_iter_tma<R, X, Y, MB>(ctx, tmS, tmF, a, max_items, st)
+    switch (rad) {
+    case 1: if (var == 0) return HR_LT(1, 64, 32, 2); break;
+    case 2: if (var == 0) return HR_LT(2, 64, 32, 2); break;
+    case 3:
+        switch (var) { HR_TMA_VARIANTS(3, HR_LT) default: break; }
+        break;
+    case 4: if (var == 0) return HR_LT(4, 64, 32, 2); break;
+    case 5: if (var == 0) return HR_LT(5, 64, 32, 2); break;
+    case 6: if (var == 0) return HR_LT(6, 64, 32, 2); break;
+    default: break;
+    }
+#undef HR_LT
+    return HREBSD_EINVAL;
 }
 
 int dispatch_iter(hrebsd_ctx *ctx, int rad, const IterArgs &a, int max_items, cudaStream_t st)
@@ -906,7 +1004,7 @@ void slot_bytes(int R, int B, int H, int W, const hrebsd_demons_params *p, size_
         rpyr_px += (size_t)R * (H >> l) * (W >> l);
     }
     const size_t field_elems = (size_t)B * 2 * H * W;
-    const int tiles0 = ((W + TX - 1) / TX) * ((H + TY - 1) / TY);
+    const int tiles0 = ((W + kMinTX - 1) / kMinTX) * ((H + kMinTY - 1) / kMinTY);
     bytes[WS_TPYR] = pyr_px * 4 + 16;
     bytes[WS_RPYR] = rpyr_px * 4 + 16;
     bytes[WS_U0] = field_elems * 4;
@@ -989,76 +1087,103 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
 
     for (int l = start; l >= 0; --l) {
         const int h = H >> l, w = W >> l;
-        const int tiles_x = (w + TX - 1) / TX, tiles = tiles_x * ((h + TY - 1) / TY);
         const int cap = p->max_iters[l];
+        const int var = hr_tuned_variant(ctx, rad, h, w);
         CUtensorMap tmS[2], tmF;
-        const bool use_tma = rad > 0 && !ctx->no_tma &&
-                             encode_maps(rad, (const float2 *)s0, (const float2 *)s1, tl[l], B, h, w, tmS, &tmF);
-        hr_prof_begin(ctx, st);
-        iota_kernel<<<(B + 255) / 256, 256, 0, st>>>(list0, B, cnt);
-        hr_prof_end(ctx, PROF_DEMONS_AUX, st);
-        HR_LAUNCHED(ctx);
-        for (int k = 0; k < cap; ++k) {
-            int *cur = (k & 1) ? list1 : list0, *nxt = (k & 1) ? list0 : list1;
-            IterArgs a;
-            a.Ftest = tl[l];
-            a.Mref = rl[l];
-            a.ref_idx = ref_idx;
-            a.in = k == 0 ? (const float2 *)u0 : ((k & 1) ? (const float2 *)s1 : (const float2 *)s0);
-            a.out = ((k + 1) & 1) ? (float2 *)s1 : (float2 *)s0;
-            a.part = (float *)part;
-            a.active = cur;
-            a.n_active = cnt + (k & 1);
-            a.n_next_reset = cnt + ((k + 1) & 1);
-            a.h = h;
-            a.w = w;
-            a.tiles_x = tiles_x;
-            a.tiles = tiles;
-            a.in_is_s = k > 0;
-            a.alpha2 = p->alpha * p->alpha;
-            a.taps = taps;
-            a.px_count = hr_prof_pixiters(ctx);
-            a.err = ctx->d_err;
-            if (k > 0 && use_tma) e = dispatch_iter_tma(ctx, rad, tmS[k & 1], tmF, a, B * tiles, st);
-            else e = dispatch_iter(ctx, rad, a, B * tiles, st);
-            if (e) return e;
-            CtrlArgs c;
-            c.part = (const float *)part;
-            c.hist = (double *)hist;
-            c.active = cur;
-            c.n_active = cnt + (k & 1);
-            c.next = nxt;
-            c.n_next = cnt + ((k + 1) & 1);
-            c.iters = iters;
-            c.status = status;
-            c.tiles = tiles;
-            c.hist_stride = cap_max + 1;
-            c.k = k;
-            c.cap = cap;
-            c.window = p->stop_window;
-            c.level = l;
-            c.levels = L;
-            c.tol = p->stop_tol;
-            int cgrid = (B + 255) / 256;
-            if (cgrid > ctx->num_sms * 4) cgrid = ctx->num_sms * 4;
+        const bool use_tma = rad > 0 && !ctx->no_tma && cap > 1 &&
+                             encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, tl[l], B, h, w, tmS, &tmF);
+        // The launches of one level: list reset, cap x (iteration, control),
+        // finalize, prolongation.  Replayed from a cached CUDA graph when possible.
+        auto emit = [&](cudaStream_t st) -> int {
+            int e2;
             hr_prof_begin(ctx, st);
-            demons_control_kernel<<<cgrid, 256, 0, st>>>(c);
-            hr_prof_end(ctx, PROF_CTRL, st);
-            HR_LAUNCHED(ctx);
-        }
-        float *dst = l == 0 ? field : (float *)uout;
-        if ((e = dispatch_finalize(ctx, rad, l == 0, (const float2 *)u0, (const float2 *)s0, (const float2 *)s1,
-                                   iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
-            return e;
-        if (l > 0) {
-            size_t total = (size_t)B * (2 * h) * (2 * w);
-            int grid = (int)((total + 255) / 256);
-            if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
-            hr_prof_begin(ctx, st);
-            prolong_kernel<<<grid, 256, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
+            iota_kernel<<<(B + 255) / 256, 256, 0, st>>>(list0, B, cnt);
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
             HR_LAUNCHED(ctx);
+            for (int k = 0; k < cap; ++k) {
+                const bool tma_k = k > 0 && use_tma;
+                const int tx = tma_k ? kVarTX[var] : TX, ty = tma_k ? kVarTY[var] : TY;
+                const int tiles_x = (w + tx - 1) / tx, tiles = tiles_x * ((h + ty - 1) / ty);
+                int *cur = (k & 1) ? list1 : list0, *nxt = (k & 1) ? list0 : list1;
+                IterArgs a;
+                a.Ftest = tl[l];
+                a.Mref = rl[l];
+                a.ref_idx = ref_idx;
+                a.in = k == 0 ? (const float2 *)u0 : ((k & 1) ? (const float2 *)s1 : (const float2 *)s0);
+                a.out = ((k + 1) & 1) ? (float2 *)s1 : (float2 *)s0;
+                a.part = (float *)part;
+                a.active = cur;
+                a.n_active = cnt + (k & 1);
+                a.n_next_reset = cnt + ((k + 1) & 1);
+                a.h = h;
+                a.w = w;
+                a.tiles_x = tiles_x;
+                a.tiles = tiles;
+                a.in_is_s = k > 0;
+                a.alpha2 = p->alpha * p->alpha;
+                a.taps = taps;
+                a.px_count = hr_prof_pixiters(ctx);
+                a.err = ctx->d_err;
+                if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, tmS[k & 1], tmF, a, B * tiles, st);
+                else e2 = dispatch_iter(ctx, rad, a, B * tiles, st);
+                if (e2) return e2;
+                CtrlArgs c;
+                c.part = (const float *)part;
+                c.hist = (double *)hist;
+                c.active = cur;
+                c.n_active = cnt + (k & 1);
+                c.next = nxt;
+                c.n_next = cnt + ((k + 1) & 1);
+                c.iters = iters;
+                c.status = status;
+                c.tiles = tiles;
+                c.hist_stride = cap_max + 1;
+                c.k = k;
+                c.cap = cap;
+                c.window = p->stop_window;
+                c.level = l;
+                c.levels = L;
+                c.tol = p->stop_tol;
+                int cgrid = (B + 255) / 256;
+                if (cgrid > ctx->num_sms * 4) cgrid = ctx->num_sms * 4;
+                hr_prof_begin(ctx, st);
+                demons_control_kernel<<<cgrid, 256, 0, st>>>(c);
+                hr_prof_end(ctx, PROF_CTRL, st);
+                HR_LAUNCHED(ctx);
+            }
+            const int tiles_x = (w + TX - 1) / TX, tiles = tiles_x * ((h + TY - 1) / TY);
+            float *dst = l == 0 ? field : (float *)uout;
+            if ((e2 = dispatch_finalize(ctx, rad, l == 0, (const float2 *)u0, (const float2 *)s0, (const float2 *)s1,
+                                        iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
+                return e2;
+            if (l > 0) {
+                size_t total = (size_t)B * (2 * h) * (2 * w);
+                int grid = (int)((total + 255) / 256);
+                if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+                hr_prof_begin(ctx, st);
+                prolong_kernel<<<grid, 256, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
+                hr_prof_end(ctx, PROF_DEMONS_AUX, st);
+                HR_LAUNCHED(ctx);
+            }
+            return HREBSD_OK;
+        };
+        if (given || !hr_graph_usable(ctx, st)) {
+            if ((e = emit(st))) return e;
+            continue;
         }
+        // graph key: everything the launches of this level depend on
+        hr_graph_key key{};
+        const void *kp[] = {ref_idx, tl[l], rl[l], u0, s0, s1, uout, part, hist, lists, iters, status, field,
+                            ctx->d_err};
+        static_assert(sizeof(kp) / sizeof(kp[0]) <= sizeof(key.p) / sizeof(key.p[0]), "graph key");
+        for (size_t i = 0; i < sizeof(kp) / sizeof(kp[0]); ++i) key.p[i] = kp[i];
+        const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window};
+        for (size_t i = 0; i < sizeof(ki) / sizeof(ki[0]); ++i) key.i[i] = ki[i];
+        key.f[0] = p->alpha;
+        key.f[1] = p->stop_tol;
+        memcpy(&key.f[2], taps.up, sizeof(taps.up));
+        memcpy(&key.f[2 + 2 * kMaxRad + 1], taps.f, sizeof(taps.f));
+        if ((e = hr_graph_run(ctx, key, st, emit))) return e;
     }
     return HREBSD_OK;
 }
@@ -1082,6 +1207,160 @@ int check_register_args(hrebsd_ctx *ctx, const float *ref, const float *test, co
 }
 
 }  // namespace
+
+namespace {
+
+// Synthetic inputs of the autotuner: striped images (a few plane waves, like
+// Kikuchi bands) and a field of a small rotation about the image centre, so
+// that the moving-image gathers have realistic offsets.
+__global__ void tune_fill_kernel(float *img, int n_img, float2 *s0, float2 *s1, int n_field, int h, int w)
+{
+    const size_t plane = (size_t)h * w, total = (size_t)n_img * plane;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / plane), y = (int)((idx % plane) / w), x = (int)(idx % w);
+        const float xf = (float)x / (float)w, yf = (float)y / (float)h;
+        float v = 0.0f;
+        for (int k = 0; k < 6; ++k) {
+            const float ang = 0.52f * (float)k + 0.11f * (float)(b % 7);
+            v += cosf(37.0f * (cosf(ang) * xf + sinf(ang) * yf) + (float)k);
+        }
+        img[idx] = v;
+        if (b < n_field) {
+            const float cx = (float)x - 0.5f * (float)(w - 1), cy = (float)y - 0.5f * (float)(h - 1);
+            const float2 u = make_float2(-0.03f * cy + 0.4f, 0.03f * cx - 0.3f);
+            s0[idx] = u;
+            s1[idx] = u;
+        }
+    }
+}
+
+enum { WS_TUNE_IMG = 9, WS_TUNE_S0, WS_TUNE_S1, WS_TUNE_PART, WS_TUNE_IDX };
+
+}  // namespace
+
+extern "C" int hrebsd_set_tile_variant(hrebsd_ctx *ctx, int h, int w, int variant)
+{
+    if (!ctx || h < 1 || w < 1 || variant < -1 || variant >= kTileVariants) return HREBSD_EINVAL;
+    for (size_t i = 0; i < ctx->tune.size(); ++i)
+        if (ctx->tune[i].h == h && ctx->tune[i].w == w) {
+            if (variant < 0) ctx->tune.erase(ctx->tune.begin() + i);
+            else ctx->tune[i].var = variant;
+            return HREBSD_OK;
+        }
+    if (variant >= 0) ctx->tune.push_back(hr_tune_entry{h, w, variant});
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_get_tile_variant(const hrebsd_ctx *ctx, int h, int w)
+{
+    if (!ctx) return HREBSD_EINVAL;
+    for (const auto &t : ctx->tune)
+        if (t.h == h && t.w == w) return t.var;
+    return 0;
+}
+
+extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebsd_demons_params *p, float *ms_out,
+                               void *stream)
+{
+    if (!ctx || !p || B < 1) return HREBSD_EINVAL;
+    int e = check_register_args(ctx, (const float *)1, (const float *)1, (const int32_t *)1, 1, B, H, W, p,
+                                (float *)1, (int32_t *)1, (int32_t *)1);
+    if (e) return e;
+    if ((e = hr_set_device(ctx))) return e;
+    const int L = p->levels;
+    const int rad = max(hr_gauss_radius(p->sigma_update), hr_gauss_radius(p->sigma_field));
+    Taps taps;
+    if (hr_gauss_taps(p->sigma_update, rad, taps.up) < 0 || hr_gauss_taps(p->sigma_field, rad, taps.f) < 0)
+        return HREBSD_EINVAL;
+    if (ms_out)
+        for (int i = 0; i < L * kTileVariants; ++i) ms_out[i] = nanf("");
+    if (rad == 0) return HREBSD_OK;   // no TMA-fed iteration at r = 0
+    const int Bt = B < 2048 ? B : 2048;
+    const size_t px0 = (size_t)H * W;
+    const int tiles0 = ((W + kMinTX - 1) / kMinTX) * ((H + kMinTY - 1) / kMinTY);
+    void *img, *s0, *s1, *part, *idx;
+    if ((e = hr_ws(ctx, WS_TUNE_IMG, (Bt + 1) * px0 * 4, &img))) return e;
+    if ((e = hr_ws(ctx, WS_TUNE_S0, Bt * px0 * 8, &s0))) return e;
+    if ((e = hr_ws(ctx, WS_TUNE_S1, Bt * px0 * 8, &s1))) return e;
+    if ((e = hr_ws(ctx, WS_TUNE_PART, (size_t)Bt * tiles0 * 4, &part))) return e;
+    if ((e = hr_ws(ctx, WS_TUNE_IDX, ((size_t)2 * Bt + 4) * 4, &idx))) return e;
+    int32_t *ridx = (int32_t *)idx, *list = ridx + Bt, *cnt = list + Bt;
+    cudaStream_t st = hr_stream(stream);
+    const int prof = ctx->prof_on;
+    ctx->prof_on = 0;   // tuning launches stay out of the trace
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) {
+        ctx->prof_on = prof;
+        return hr_cuda_error(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__);
+    }
+    auto run = [&]() -> int {
+        HR_CHECK(cudaMemsetAsync(ridx, 0, (size_t)Bt * 4, st));
+        iota_kernel<<<(Bt + 255) / 256, 256, 0, st>>>(list, Bt, cnt);
+        HR_LAUNCHED(ctx);
+        for (int l = 0; l < L; ++l) {
+            const int h = H >> l, w = W >> l;
+            float *ref = (float *)img, *test = ref + (size_t)h * w;   // image 0 is the reference
+            tune_fill_kernel<<<ctx->num_sms * 8, 256, 0, st>>>((float *)img, Bt + 1, (float2 *)s0, (float2 *)s1,
+                                                               Bt, h, w);
+            HR_LAUNCHED(ctx);
+            float best = 0.0f;
+            int best_v = 0;
+            for (int v = 0; v < kTileVariants; ++v) {
+                if (!variant_ok(rad, v) || ctx->no_tma) continue;
+                CUtensorMap tmS[2], tmF;
+                if (!encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, test, Bt, h, w, tmS, &tmF)) continue;
+                const int tiles_x = (w + kVarTX[v] - 1) / kVarTX[v], tiles = tiles_x * ((h + kVarTY[v] - 1) / kVarTY[v]);
+                IterArgs a;
+                a.Ftest = test;
+                a.Mref = ref;
+                a.ref_idx = ridx;
+                a.part = (float *)part;
+                a.active = list;
+                a.n_active = cnt;
+                a.n_next_reset = cnt + 1;
+                a.px_count = nullptr;
+                a.err = ctx->d_err;
+                a.h = h;
+                a.w = w;
+                a.tiles_x = tiles_x;
+                a.tiles = tiles;
+                a.in_is_s = 1;
+                a.alpha2 = p->alpha * p->alpha;
+                a.taps = taps;
+                constexpr int kWarm = 2, kTimed = 5;
+                for (int k = 0; k < kWarm + kTimed; ++k) {
+                    if (k == kWarm) HR_CHECK(cudaEventRecord(ev[0], st));
+                    a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
+                    a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
+                    int e2 = dispatch_iter_tma(ctx, rad, v, tmS[k & 1], tmF, a, Bt * tiles, st);
+                    if (e2) return e2;
+                }
+                HR_CHECK(cudaEventRecord(ev[1], st));
+                HR_CHECK(cudaEventSynchronize(ev[1]));
+                float ms = 0.0f;
+                HR_CHECK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                ms /= (float)kTimed;
+                if (ms_out) ms_out[l * kTileVariants + v] = ms;
+                if (best_v == 0 && best == 0.0f) {
+                    best = ms;
+                    best_v = v;
+                } else if (ms < best) {
+                    best = ms;
+                    best_v = v;
+                }
+            }
+            int e3 = hrebsd_set_tile_variant(ctx, h, w, best_v);
+            if (e3) return e3;
+        }
+        return HREBSD_OK;
+    };
+    e = run();
+    ctx->prof_on = prof;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e) return e;
+    return hrebsd_device_error(ctx);
+}
 
 extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float *test,
                                             const int32_t *ref_idx, int R, int B, int H, int W,

@@ -40,6 +40,23 @@ struct hr_pending {
     cudaEvent_t a, b;
 };
 
+// Cached CUDA graph of one pyramid level of a registration (demons.cu).
+struct hr_graph_key {
+    const void *p[16];
+    int i[16];
+    float f[32];
+};
+struct hr_graph_entry {
+    hr_graph_key key;
+    cudaGraphExec_t exec;
+    long long nodes;          // kernel launches in the graph
+    unsigned long long last;  // LRU clock
+};
+// Tile shape chosen for a level size (autotuner or caller).
+struct hr_tune_entry {
+    int h, w, var;
+};
+
 struct hrebsd_ctx {
     int device = 0;
     int num_sms = 0;
@@ -49,6 +66,11 @@ struct hrebsd_ctx {
     int prof_on = 0;
     int no_events = 0;   // set while a call must not create CUDA events
     int no_tma = 0;      // force the non-TMA demons iteration (testing, unsupported shapes)
+    int graphs = 1;      // replay each registration level from a cached CUDA graph
+    cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
+    std::vector<hr_graph_entry> graph_cache;
+    unsigned long long graph_clock = 0;
+    std::vector<hr_tune_entry> tune;
     int *d_err = nullptr;   // device flag: a bounded wait gave up (static device symbol)
     hr_cnn_net *cnn = nullptr;   // learned initialiser (allocated on first use)
     double prof_ms[HREBSD_PROF_CLASSES] = {};

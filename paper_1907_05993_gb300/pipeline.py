@@ -1,7 +1,7 @@
 """The whole hot path for a batch of pattern pairs, chained through the C ABI.
 
-``Pipeline.run`` calls, in order: hrebsd_preprocess_batch (references and
-tests), hrebsd_demons_register_batch, hrebsd_fit_rotation, hrebsd_remap,
+``Pipeline.run`` calls, in order: hrebsd_autotune (first batch of a size
+only), hrebsd_preprocess_batch (references and tests), hrebsd_demons_register_batch, hrebsd_fit_rotation, hrebsd_remap,
 hrebsd_xcf_roi_batch and hrebsd_solve_F, all on one stream.  This module
 only allocates the output tensors and passes pointers; every step runs in
 the CUDA library.
@@ -12,7 +12,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (demons_params, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
+from . import (demons_params, hrebsd_autotune, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
                hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
                hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
 
@@ -34,6 +34,7 @@ class PipelineConfig:
     zstar: float = 0.6
     flat: bool = True
     window: bool = True
+    autotune: bool = True       # pick the demons tile shape per level on the first batch of a size
 
 
 class Pipeline:
@@ -49,6 +50,7 @@ class Pipeline:
         self.roi = torch.as_tensor(np.ascontiguousarray(cfg.roi_xy, dtype=np.int32), device=self.dev)
         self.N = int(cfg.roi_xy.shape[0])
         self._bufs = {}
+        self._tuned = {}
 
     def close(self):
         if self.ctx is not None:
@@ -93,6 +95,8 @@ class Pipeline:
             return o[name]
         ref_p = get("ref_pre", (R, H, W), t.float32)
         test_p = get("test_pre", (B, H, W), t.float32)
+        if c.autotune and (B, H, W) not in self._tuned:
+            self._tuned[(B, H, W)] = hrebsd_autotune(self.ctx, B, H, W, self.params, stream)
         hrebsd_preprocess_batch(self.ctx, refs_raw, R, H, W, c.flat, ref_p, stream)
         hrebsd_preprocess_batch(self.ctx, tests_raw, B, H, W, c.flat, test_p, stream)
         field = get("field", (B, 2, H, W), t.float32)

@@ -1,0 +1,120 @@
+"""Batching machinery (project addition): tile-shape variants, the autotuner and the
+per-level CUDA graphs.  None of them may change the registration's result."""
+import numpy as np
+import pytest
+
+from synth import kikuchi as K
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def lib(torch):
+    import paper_1907_05993_gb300 as P
+    P.load()
+    return P
+
+
+@pytest.fixture(scope="module")
+def pairs(oracle):
+    """Four noisy pairs of the batched-scan kind at 256x256, two references."""
+    spec = K.ScanSpec(n_pairs=4, H=256, W=256, n_refs=2, mis_lo_deg=0.5, mis_hi_deg=5.0, seed=71)
+    refs = np.stack([oracle.preprocess(K.render_ref(spec, r).astype(np.float64), True) for r in range(2)])
+    tests = np.stack([oracle.preprocess(K.render_test(spec, p).astype(np.float64), True) for p in range(4)])
+    ridx = np.array([K.ref_index(spec, p) for p in range(4)], dtype=np.int32)
+    return refs.astype(np.float32), tests.astype(np.float32), ridx
+
+
+def _register(torch, lib, ctx, pairs, params):
+    refs, tests, ridx = pairs
+    R, H, W = refs.shape
+    B = tests.shape[0]
+    field = torch.empty((B, 2, H, W), dtype=torch.float32, device="cuda")
+    iters = torch.empty((B, params.levels), dtype=torch.int32, device="cuda")
+    status = torch.empty((B,), dtype=torch.int32, device="cuda")
+    lib.hrebsd_demons_register_batch(ctx, torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(),
+                                     torch.from_numpy(ridx).cuda(), R, B, H, W, params, None, field, iters, status)
+    lib.hrebsd_device_error(ctx)   # raises if a bounded wait gave up
+    return field.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy()
+
+
+def test_tile_shapes_give_the_same_field(torch, lib, pairs):
+    """Fixed iteration counts: every tile shape yields a bit-identical field."""
+    params = lib.demons_params(4, [12] * 4, 1.0, 1.0, 1.0)
+    out = []
+    for v in range(lib.TILE_VARIANTS):
+        ctx = lib.hrebsd_create(0)
+        for l in range(4):
+            lib.hrebsd_set_tile_variant(ctx, 256 >> l, 256 >> l, v)
+            assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == v
+        out.append(_register(torch, lib, ctx, pairs, params))
+        lib.hrebsd_destroy(ctx)
+    for f, it, st in out[1:]:
+        assert np.array_equal(f, out[0][0])
+        assert np.array_equal(it, out[0][1]) and np.array_equal(st, out[0][2])
+
+
+def test_autotune_records_the_fastest_shape(torch, lib):
+    ctx = lib.hrebsd_create(0)
+    params = lib.demons_params(4, [100] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
+    ms = lib.hrebsd_autotune(ctx, 64, 256, 256, params)
+    assert ms.shape == (4, lib.TILE_VARIANTS)
+    assert np.isfinite(ms).all() and (ms > 0).all()
+    for l in range(4):
+        assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == int(np.argmin(ms[l]))
+    # radius 0 (no smoothing): nothing to tune
+    ms0 = lib.hrebsd_autotune(ctx, 8, 64, 64, lib.demons_params(2, [5, 5], 1.0, 0.0, 0.0))
+    assert np.isnan(ms0).all()
+    with pytest.raises(lib.HrebsdError):
+        lib.hrebsd_autotune(ctx, 8, 100, 64, lib.demons_params(4, [5] * 4))   # 100 not divisible by 8
+    lib.hrebsd_destroy(ctx)
+
+
+def test_graph_replay_matches_direct_launches(torch, lib, pairs):
+    """Stop rule on: the graph path (captured, then replayed from the cache) equals direct launches."""
+    params = lib.demons_params(4, [60] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
+    res = {}
+    for graphs in (0, 1):
+        ctx = lib.hrebsd_create(0)
+        lib.hrebsd_set_option(ctx, lib.OPT_GRAPHS, graphs)
+        first = _register(torch, lib, ctx, pairs, params)
+        n1 = lib.hrebsd_launch_count(ctx)
+        second = _register(torch, lib, ctx, pairs, params)
+        n2 = lib.hrebsd_launch_count(ctx)
+        for a, b in zip(first, second):
+            assert np.array_equal(a, b)
+        res[graphs] = (first, n1, n2 - n1)
+        lib.hrebsd_destroy(ctx)
+    for a, b in zip(res[0][0], res[1][0]):
+        assert np.array_equal(a, b)
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]   # same kernel launches counted
+
+
+def test_graphs_on_a_side_stream(torch, lib, pairs):
+    params = lib.demons_params(2, [8, 8], 1.0, 1.0, 1.0)
+    refs, tests, ridx = pairs
+    ctx = lib.hrebsd_create(0)
+    ref_ = lib.demons_params(2, [8, 8], 1.0, 1.0, 1.0)
+    base = _register(torch, lib, ctx, pairs, ref_)
+    s = torch.cuda.Stream()
+    R, H, W = refs.shape
+    B = tests.shape[0]
+    with torch.cuda.stream(s):
+        field = torch.empty((B, 2, H, W), dtype=torch.float32, device="cuda")
+        iters = torch.empty((B, 2), dtype=torch.int32, device="cuda")
+        status = torch.empty((B,), dtype=torch.int32, device="cuda")
+        r_d, t_d, i_d = (torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(),
+                         torch.from_numpy(ridx).cuda())
+        for _ in range(2):
+            lib.hrebsd_demons_register_batch(ctx, r_d, t_d, i_d, R, B, H, W, params, None, field, iters, status,
+                                             stream=s)
+    s.synchronize()
+    assert np.array_equal(field.cpu().numpy(), base[0])
+    lib.hrebsd_destroy(ctx)
