@@ -378,7 +378,7 @@ def run_learned(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     spec5 = K.config5(n_pairs)
     pairs = sorted(set(range(args.pairs)) | set(sub))
-    refs, tests, ridx, _ = SG.make_scan_gpu(spec5, pairs)
+    refs, tests, ridx, F_true = SG.make_scan_gpu(spec5, pairs)
     pos = {p: i for i, p in enumerate(pairs)}
     roi = K.roi_grid(256, 256, 64, False)
     cfg = PipelineConfig(256, 256, roi, 64, 4, (100, 100, 100, 100), 1.0, 1.0, 1e-4, 5)
@@ -386,7 +386,10 @@ def run_learned(args, rank, world, local_rank):
     # train the initialiser (config-4 recipe) in the pipeline's context
     t0 = time.perf_counter()
     x, y = LN.build_training_set(pipe.ctx, K.config4(args.train_pairs))
-    hist = LN.train(pipe.ctx, x, y, epochs=args.epochs, batch=256, lr=2e-3, seed=0)
+    torch.cuda.synchronize()
+    t_set = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = LN.train(pipe.ctx, x, y, epochs=args.epochs, batch=256, lr=args.lr, seed=0, lr_final=args.lr_final)
     del x, y
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -396,7 +399,7 @@ def run_learned(args, rank, world, local_rank):
 
     def timed(learned):
         out = {}
-        kw = {"learned_caps": caps_l} if learned else {}
+        kw = {"learned_caps": caps_l, "learned_start_res": args.learned_start} if learned else {}
         for _ in range(args.warmup):
             pipe.run(refs, tests, ridx, out=out, **kw)
         torch.cuda.synchronize()
@@ -418,27 +421,39 @@ def run_learned(args, rank, world, local_rank):
     def rot_deg(Ra, Rb):
         c = np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1)
         return float(np.degrees(np.arccos(c)))
-    e_plain = np.array([rot_deg(O.polar(F_plain[pos[p]]), R) for p, R in zip(sub, R_oracle)])
-    e_learn = np.array([rot_deg(O.polar(F_learn[pos[p]]), R) for p, R in zip(sub, R_oracle)])
+
+    def stats(e):
+        e = np.asarray(e)
+        return {"median": float(np.median(e)), "p95": float(np.percentile(e, 95)),
+                "frac_le_1e-4": float(np.mean(e <= 1e-4))}
+    R_plain = [O.polar(f) for f in F_plain]
+    R_learn = [O.polar(f) for f in F_learn]
+    R_true = [O.polar(f) for f in F_true]
+    e_plain = [rot_deg(R_plain[pos[p]], R) for p, R in zip(sub, R_oracle)]
+    e_learn = [rot_deg(R_learn[pos[p]], R) for p, R in zip(sub, R_oracle)]
+    t_plain = [rot_deg(a, b) for a, b in zip(R_plain, R_true)]
+    t_learn = [rot_deg(a, b) for a, b in zip(R_learn, R_true)]
+    d_pl = [rot_deg(a, b) for a, b in zip(R_plain, R_learn)]
     line = {
         "metric": METRIC + "; learned-init vs plain", "workload": "learned-init vs plain",
         "value": v_learn, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
         "data": "synthetic (seeded kinematic Kikuchi generator)",
         "config": {"workload": f"config-5 scan 400x400 (first {args.pairs} points), 256x256, 8 grains, "
-                               f"mis U(0,12) deg; plain: 4 levels <=100 it; learned: start at 64x64 from the "
-                               f"network, caps {list(caps_l)}", "pairs": B,
-                   "training": f"{args.train_pairs} config-4 pairs, {args.epochs} epochs, batch 256, Adam 2e-3"},
+                               f"mis U(0,12) deg; plain: 4 levels <=100 it; learned: network field resampled "
+                               f"to {args.learned_start}x{args.learned_start}, registration from that level, "
+                               f"caps {list(caps_l)}", "pairs": B,
+                   "training": f"{args.train_pairs} config-4 pairs (128x128, mis U(0,12) deg), target = final "
+                               f"field of the full registration at 64x64; {args.epochs} epochs, batch 256, "
+                               f"Adam {args.lr} -> {args.lr_final} (cosine)"},
         "plain_pairs_per_s": v_plain, "learned_pairs_per_s": v_learn, "speedup": v_learn / v_plain,
         "iters_mean_per_level_plain": [float(a) for a in it_plain.mean(axis=0)],
         "iters_mean_per_level_learned": [float(a) for a in it_learn.mean(axis=0)],
         "oracle_subset": len(sub), "oracle_seconds": t_oracle, "oracle_cores": cores,
-        "rot_err_vs_oracle_deg": {
-            "plain": {"median": float(np.median(e_plain)), "p95": float(np.percentile(e_plain, 95)),
-                      "frac_le_1e-4": float(np.mean(e_plain <= 1e-4))},
-            "learned": {"median": float(np.median(e_learn)), "p95": float(np.percentile(e_learn, 95)),
-                        "frac_le_1e-4": float(np.mean(e_learn <= 1e-4))}},
-        "training_loss_per_epoch": hist, "training_seconds": t_train,
+        "rot_err_vs_oracle_deg": {"plain": stats(e_plain), "learned": stats(e_learn)},
+        "rot_err_vs_ground_truth_deg": {"plain": stats(t_plain), "learned": stats(t_learn)},
+        "rot_dev_learned_vs_plain_deg": stats(d_pl),
+        "training_loss_per_epoch": hist, "training_seconds": t_train, "training_set_seconds": t_set,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -458,9 +473,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("scan", "learned"), default="scan")
     ap.add_argument("--train-pairs", type=int, default=200_000)
-    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr-final", type=float, default=5e-5)
+    ap.add_argument("--learned-start", type=int, default=64, choices=(64, 128))
     ap.add_argument("--oracle-pairs", type=int, default=500)
-    ap.add_argument("--learned-caps", type=int, nargs=4, default=(100, 100, 100, 0))
+    ap.add_argument("--learned-caps", type=int, nargs=4, default=(100, 100, 25, 0))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -150,6 +150,15 @@ int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int 
  * inputs and targets of the learned initialiser).  H, W divisible by f. */
 int hrebsd_downsample_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int f, float *out, void *stream);
 
+/* Displacement field between pyramid resolutions (learned initialiser):
+ * planar [B][2][h][w] FP32 -> [B][2][h2][w2], values converted to the new pixel
+ * unit.  h2 = h / f (box mean of f x f blocks, divided by f) or h2 = h * f
+ * (bilinear sample at x_c = (x_f + 0.5) / f - 0.5, clamped, times f; for f = 2
+ * the prolongation between registration levels, Section 1), f a power of two,
+ * the same for both axes.  EINVAL for other ratios or null pointers. */
+int hrebsd_field_resample(hrebsd_ctx *ctx, const float *in, int B, int h, int w, float *out, int h2, int w2,
+                          void *stream);
+
 /* a2-a4, a9 -- multi-resolution demons registration of B pairs (Section 1,
  * Eq. 1).  ref [R][H][W] and test [B][H][W] must be preprocessed
  * (hrebsd_preprocess_batch).  Pair b registers ref[ref_idx[b]] (moving) onto

@@ -21,7 +21,7 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_autotune", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -98,6 +98,7 @@ def load(build: bool = False):
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
         "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
         "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
+        "hrebsd_field_resample": (i, [vp, vp, i, i, i, vp, i, i, vp]),
         "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
         "hrebsd_set_tile_variant": (i, [vp, i, i, i]),
         "hrebsd_get_tile_variant": (i, [vp, i, i]),
@@ -277,6 +278,12 @@ def hrebsd_get_tile_variant(ctx, h, w):
     if v < 0:
         _chk(v, "hrebsd_get_tile_variant")
     return v
+
+
+def hrebsd_field_resample(ctx, field, B, h, w, out, h2, w2, stream=None):
+    t = _t()
+    _chk(load().hrebsd_field_resample(ctx, _p(field, t.float32), B, h, w, _p(out, t.float32), h2, w2, _s(stream)),
+         "hrebsd_field_resample")
 
 
 NI_STIFFNESS = (276e9, 159e9, 132e9)

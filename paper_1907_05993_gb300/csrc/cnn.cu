@@ -30,68 +30,94 @@ constexpr int HEAD_CIN = 16, HEAD_COUT = 2;
 
 __host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
 
+// Grid of the per-image element-wise kernels: x covers `per` items of one
+// image in blocks of 256, y walks the images.
+dim3 grid2(int per, int N)
+{
+    return dim3((unsigned)((per + 255) / 256), (unsigned)(N < 65535 ? (N > 0 ? N : 1) : 65535));
+}
+
 // ------------------------------------------------------------------ element-wise kernels
 // Input of the network from preprocessed patterns: box mean of f x f blocks
 // (f = H / 64) of ref[ref_idx[b]] and test[b] -> NHWC BF16, channels (ref, test, 0...).
+__device__ __forceinline__ void store_input_pixel(bf16 *o, float r, float t)
+{
+    __nv_bfloat162 v[8];
+    v[0] = __floats2bfloat162_rn(r, t);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) v[k] = __floats2bfloat162_rn(0.0f, 0.0f);
+    uint4 *dst = reinterpret_cast<uint4 *>(o);
+    dst[0] = *reinterpret_cast<const uint4 *>(&v[0]);
+    dst[1] = *reinterpret_cast<const uint4 *>(&v[4]);
+}
+
 __global__ void pack_patterns_kernel(const float *ref, const float *test, const int32_t *ref_idx, int B, int H, int W,
                                      bf16 *x)
 {
     const int f = H / 64;
-    const size_t total = (size_t)B * 64 * 64;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / 4096), rem = (int)(i % 4096), yy = rem / 64, xx = rem % 64;
-        const float *r = ref + (size_t)ref_idx[b] * H * W, *t = test + (size_t)b * H * W;
-        float sr = 0.0f, st = 0.0f;
-        for (int dy = 0; dy < f; ++dy)
-            for (int dx = 0; dx < f; ++dx) {
-                const size_t o = (size_t)(yy * f + dy) * W + xx * f + dx;
-                sr += r[o];
-                st += t[o];
-            }
-        const float s = 1.0f / (f * f);
-        bf16 *o = x + i * 16;
-        o[0] = __float2bfloat16_rn(sr * s);
-        o[1] = __float2bfloat16_rn(st * s);
-        for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
-    }
+    const float s = 1.0f / (float)(f * f);
+    for (int b = blockIdx.y; b < B; b += gridDim.y)
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < 4096; p += gridDim.x * blockDim.x) {
+            const int yy = p / 64, xx = p % 64;
+            const float *r = ref + (size_t)ref_idx[b] * H * W, *t = test + (size_t)b * H * W;
+            float sr = 0.0f, st = 0.0f;
+            for (int dy = 0; dy < f; ++dy)
+                for (int dx = 0; dx < f; ++dx) {
+                    const size_t o = (size_t)(yy * f + dy) * W + xx * f + dx;
+                    sr += r[o];
+                    st += t[o];
+                }
+            store_input_pixel(x + ((size_t)b * 4096 + p) * 16, sr * s, st * s);
+        }
 }
 
 // NCHW BF16 [B][2][64][64] -> NHWC BF16 padded to 16 channels.
 __global__ void pack_nchw_kernel(const bf16 *in, int B, bf16 *x)
 {
-    const size_t total = (size_t)B * 4096;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / 4096, p = i % 4096;
-        bf16 *o = x + i * 16;
-        o[0] = in[b * 8192 + p];
-        o[1] = in[b * 8192 + 4096 + p];
-        for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
-    }
+    for (int b = blockIdx.y; b < B; b += gridDim.y)
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < 4096; p += gridDim.x * blockDim.x) {
+            const size_t i = (size_t)b * 8192 + p;
+            store_input_pixel(x + ((size_t)b * 4096 + p) * 16, __bfloat162float(in[i]), __bfloat162float(in[i + 4096]));
+        }
 }
 
-// 2x2 max-pool of NHWC BF16 (stride xs, offset xo, C channels) -> dense [N][h/2][w/2][C]
-// plus the argmax (0..3, first maximum in row-major order of the 2x2 window).
+// 2x2 max-pool of NHWC BF16 (stride xs, offset xo, C channels, C and xs, xo
+// multiples of 8) -> dense [N][h/2][w/2][C] plus the argmax (0..3, first
+// maximum in row-major order of the 2x2 window).  One thread per 8 channels.
 __global__ void maxpool_kernel(const bf16 *x, int xs, int xo, int C, int N, int H, int W, bf16 *y, uint8_t *arg)
 {
-    const int h = H / 2, w = W / 2;
-    const size_t total = (size_t)N * h * w * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t q = i / C;
-        const int xx = (int)(q % w), yy = (int)((q / w) % h), n = (int)(q / ((size_t)w * h));
-        float best = -INFINITY;
-        int bi = 0;
-        for (int k = 0; k < 4; ++k) {
-            const size_t src = ((size_t)(n * H + 2 * yy + k / 2) * W + 2 * xx + k % 2) * xs + xo + c;
-            const float v = __bfloat162float(x[src]);
-            if (v > best) {
-                best = v;
-                bi = k;
+    const int h = H / 2, w = W / 2, C8 = C / 8, per = h * w * C8;
+    for (int n = blockIdx.y; n < N; n += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int c8 = i % C8, q = i / C8, xx = q % w, yy = q / w;
+            uint4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                v[k] = *reinterpret_cast<const uint4 *>(
+                    x + ((size_t)(n * H + 2 * yy + k / 2) * W + 2 * xx + k % 2) * xs + xo + c8 * 8);
+            uint4 out;
+            uint8_t am[8];
+            const bf16 *e0 = reinterpret_cast<const bf16 *>(&v[0]);
+            bf16 *eo = reinterpret_cast<bf16 *>(&out);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float best = -INFINITY;
+                int bi = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float t = __bfloat162float(e0[k * 8 + e]);
+                    if (t > best) {
+                        best = t;
+                        bi = k;
+                    }
+                }
+                eo[e] = __float2bfloat16_rn(best);
+                am[e] = (uint8_t)bi;
             }
+            const size_t o = ((size_t)n * h * w + q) * C + c8 * 8;
+            *reinterpret_cast<uint4 *>(y + o) = out;
+            *reinterpret_cast<uint2 *>(arg + o) = *reinterpret_cast<const uint2 *>(am);
         }
-        y[i] = __float2bfloat16_rn(best);
-        arg[i] = (uint8_t)bi;
-    }
 }
 
 // d_in[p][c] (FP32, dense [N][H][W][C]) = routed dy from the pool + skip gradient (stride ss, offset so).
@@ -111,17 +137,17 @@ __global__ void maxpool_bwd_kernel(const float *dy, const uint8_t *arg, int C, i
     }
 }
 
-// Nearest up-sampling x2 of dense [N][h][w][C] BF16 into y (stride ys, offset yo).
+// Nearest up-sampling x2 of dense [N][h][w][C] BF16 into y (stride ys, offset
+// yo; C, ys, yo multiples of 8).  One thread per 8 channels.
 __global__ void up2_kernel(const bf16 *x, int C, int N, int h, int w, bf16 *y, int ys, int yo)
 {
-    const int H = 2 * h, W = 2 * w;
-    const size_t total = (size_t)N * H * W * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t q = i / C;
-        const int xx = (int)(q % W), yy = (int)((q / W) % H), n = (int)(q / ((size_t)W * H));
-        y[q * ys + yo + c] = x[((size_t)(n * h + yy / 2) * w + xx / 2) * C + c];
-    }
+    const int H = 2 * h, W = 2 * w, C8 = C / 8, per = H * W * C8;
+    for (int n = blockIdx.y; n < N; n += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int c8 = i % C8, q = i / C8, xx = q % W, yy = q / W;
+            const uint4 v = *reinterpret_cast<const uint4 *>(x + ((size_t)(n * h + yy / 2) * w + xx / 2) * C + c8 * 8);
+            *reinterpret_cast<uint4 *>(y + ((size_t)n * H * W + q) * ys + yo + c8 * 8) = v;
+        }
 }
 
 // Adjoint of up2: dx[N][h][w][C] = sum of the 4 children of dy (stride ys, offset yo).
@@ -173,18 +199,22 @@ __global__ void bias_grad_kernel(const bf16 *dpre, int C, size_t P, float *db)
 // 1x1 head: out[b][o][y][x] (FP32 planar) = bias[o] + sum_c w[o][c] d1[p][c]
 __global__ void head_fwd_kernel(const bf16 *d1, const bf16 *w, const float *bias, int N, float *out)
 {
-    const size_t total = (size_t)N * 4096;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t b = i / 4096, p = i % 4096;
-        float a0 = bias[0], a1 = bias[1];
-        for (int c = 0; c < HEAD_CIN; ++c) {
-            const float v = __bfloat162float(d1[i * HEAD_CIN + c]);
-            a0 = fmaf(__bfloat162float(w[c]), v, a0);
-            a1 = fmaf(__bfloat162float(w[HEAD_CIN + c]), v, a1);
+    static_assert(HEAD_CIN == 16, "two 16-byte loads per pixel");
+    for (int n = blockIdx.y; n < N; n += gridDim.y)
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < 4096; p += gridDim.x * blockDim.x) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(d1 + ((size_t)n * 4096 + p) * HEAD_CIN);
+            uint4 v[2] = {src[0], src[1]};
+            const bf16 *e = reinterpret_cast<const bf16 *>(v);
+            float a0 = bias[0], a1 = bias[1];
+#pragma unroll
+            for (int c = 0; c < HEAD_CIN; ++c) {
+                const float t = __bfloat162float(e[c]);
+                a0 = fmaf(__bfloat162float(w[c]), t, a0);
+                a1 = fmaf(__bfloat162float(w[HEAD_CIN + c]), t, a1);
+            }
+            out[(size_t)n * 8192 + p] = a0;
+            out[(size_t)n * 8192 + 4096 + p] = a1;
         }
-        out[b * 8192 + p] = a0;
-        out[b * 8192 + 4096 + p] = a1;
-    }
 }
 
 // MSE gradient and loss: dout = 2 (pred - target) / count; loss += sum d^2 / count.
@@ -271,6 +301,7 @@ __global__ void cast_bf16_kernel(const float *w, int n, bf16 *out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = __float2bfloat16_rn(w[i]);
 }
+
 
 int grid_for(hrebsd_ctx *ctx, size_t n)
 {
@@ -417,6 +448,52 @@ int refresh_bf16(hrebsd_ctx *ctx, cudaStream_t st)
 }
 
 // One convolution launch.
+// Persistent halo-tiled convolution when the shape has a variant (images of
+// at least 16 x 16, cin <= 96 and the weights + two halos within 113 KB):
+// returns 1 when there is none.
+template <int CIN, int BN>
+int launch_halo_t(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
+{
+    using G = HaloConv<CIN, BN>;
+    static_assert(G::SMEM <= 113 * 1024, "halo variant too large");
+    static int configured = -1, occ = 1;
+    if (configured != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(conv3x3_halo_kernel<CIN, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)G::SMEM));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_halo_kernel<CIN, BN>, 256, G::SMEM));
+        if (occ < 1) occ = 1;
+        configured = ctx->device;
+    }
+    const long long tiles = (long long)a.N * (a.H / G::TH) * (a.W / G::TW);
+    const int cb = (a.cout + BN - 1) / BN;
+    long long gx = (long long)ctx->num_sms * occ / cb;
+    if (gx < 1) gx = 1;
+    if (gx > tiles) gx = tiles;
+    conv3x3_halo_kernel<CIN, BN><<<dim3((unsigned)gx, cb), 256, G::SMEM, st>>>(a);
+    return HREBSD_OK;
+}
+
+int launch_halo_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
+{
+    if (a.H != a.W || a.H < 16 || a.H % 16 || a.N < 1) return 1;
+    const int co = a.cout;
+    const int bn = co % 64 == 0 ? 64 : (co % 32 == 0 ? 32 : (co % 16 == 0 ? 16 : 0));
+    if (!bn) return 1;
+#define HR_H(C, B) \
+    if (a.cin == C && bn >= B) return launch_halo_t<C, B>(ctx, a, st)
+    HR_H(16, 32);
+    HR_H(16, 16);
+    HR_H(32, 64);
+    HR_H(32, 32);
+    HR_H(32, 16);
+    HR_H(48, 16);
+    HR_H(64, 32);
+    HR_H(64, 16);
+    HR_H(96, 16);
+#undef HR_H
+    return 1;
+}
+
 int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w, const float *bias, int cout, void *y,
          int ys, int yo, int y_fp32, int relu, int N, int res, cudaStream_t st)
 {
@@ -437,9 +514,30 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
     a.H = res;
     a.W = res;
     const int P = N * res * res;
-    dim3 grid((P + 63) / 64, (cout + 63) / 64);
     hr_prof_begin(ctx, st);
-    conv3x3_kernel<<<grid, 128, 0, st>>>(a);
+    int e = launch_halo_conv(ctx, a, st);
+    if (e == 1) {   // no halo variant for this shape: pipelined implicit GEMM
+        // output-channel tile: the largest of 64, 32, 16 that divides cout
+        const int bn = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);
+        dim3 grid((P + 127) / 128, (cout + bn - 1) / bn);
+#define HR_CONV(BN, KS)                                                                                           \
+    do {                                                                                                          \
+        constexpr size_t sm = conv_smem_bytes(BN, KS, 3);                                                         \
+        static int configured = -1;                                                                              \
+        if (configured != ctx->device) {                                                                          \
+            HR_CHECK(cudaFuncSetAttribute(conv3x3_kernel<BN, KS, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          (int)sm));                                                              \
+            configured = ctx->device;                                                                             \
+        }                                                                                                         \
+        conv3x3_kernel<BN, KS, 3><<<grid, 256, sm, st>>>(a);                                                     \
+    } while (0)
+        if (bn == 64) HR_CONV(64, 2);
+        else if (bn == 32) HR_CONV(32, 2);
+        else HR_CONV(16, 4);
+#undef HR_CONV
+    } else if (e) {
+        return e;
+    }
     hr_prof_end(ctx, PROF_CNN, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -521,12 +619,12 @@ int forward(hrebsd_ctx *ctx, int B, cudaStream_t st)
                     kLayers[l].cout, out[l].p, out[l].s, out[l].o, 0, 1, B, kLayers[l].res, st);
     };
     auto pool = [&](int k, const View &v, int C, int res) {
-        maxpool_kernel<<<grid_for(ctx, (size_t)B * res * res / 4 * C), 256, 0, st>>>(v.p, v.s, v.o, C, B, res, res,
-                                                                                    n->pool[k], n->parg[k]);
+        maxpool_kernel<<<grid2(res * res / 4 * C / 8, B), 256, 0, st>>>(v.p, v.s, v.o, C, B, res, res, n->pool[k],
+                                                                       n->parg[k]);
         return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
     };
     auto up = [&](const bf16 *src, int C, int res, bf16 *dst, int ds) {
-        up2_kernel<<<grid_for(ctx, (size_t)B * res * res * 4 * C), 256, 0, st>>>(src, C, B, res, res, dst, ds, 0);
+        up2_kernel<<<grid2(res * res * 4 * C / 8, B), 256, 0, st>>>(src, C, B, res, res, dst, ds, 0);
         return cudaGetLastError() == cudaSuccess ? (ctx->launches++, HREBSD_OK) : HREBSD_ECUDA;
     };
     if ((e = run(0)) || (e = run(1)) || (e = pool(0, out[1], 16, 64))) return e;
@@ -537,8 +635,7 @@ int forward(hrebsd_ctx *ctx, int B, cudaStream_t st)
     if ((e = run(10)) || (e = run(11)) || (e = up(n->act[11], 32, 32, n->cat1, 48))) return e;
     if ((e = run(12)) || (e = run(13))) return e;
     hr_prof_begin(ctx, st);
-    head_fwd_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(n->act[13], n->wf[NCONV], n->W + n->b_off[NCONV], B,
-                                                                    n->out);
+    head_fwd_kernel<<<grid2(4096, B), 256, 0, st>>>(n->act[13], n->wf[NCONV], n->W + n->b_off[NCONV], B, n->out);
     hr_prof_end(ctx, PROF_CNN, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -680,7 +777,7 @@ extern "C" int hrebsd_cnn_infer(hrebsd_ctx *ctx, const uint16_t *x_bf16, int B, 
     int e = hr_set_device(ctx);
     if (e || (e = ensure_acts(ctx, B))) return e;
     cudaStream_t st = hr_stream(stream);
-    pack_nchw_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B,
+    pack_nchw_kernel<<<grid2(4096, B), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B,
                                                                      ctx->cnn->x);
     HR_LAUNCHED(ctx);
     return infer_common(ctx, B, field64, st);
@@ -696,7 +793,7 @@ extern "C" int hrebsd_cnn_infer_patterns(hrebsd_ctx *ctx, const float *ref, cons
     int e = hr_set_device(ctx);
     if (e || (e = ensure_acts(ctx, B))) return e;
     cudaStream_t st = hr_stream(stream);
-    pack_patterns_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(ref, test, ref_idx, B, H, W, ctx->cnn->x);
+    pack_patterns_kernel<<<grid2(4096, B), 256, 0, st>>>(ref, test, ref_idx, B, H, W, ctx->cnn->x);
     HR_LAUNCHED(ctx);
     return infer_common(ctx, B, field64, st);
 }
@@ -709,7 +806,7 @@ extern "C" int hrebsd_cnn_train_step(hrebsd_ctx *ctx, const uint16_t *x_bf16, co
     if (e || (e = ensure_acts(ctx, B))) return e;
     hr_cnn_net *n = ctx->cnn;
     cudaStream_t st = hr_stream(stream);
-    pack_nchw_kernel<<<grid_for(ctx, (size_t)B * 4096), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B, n->x);
+    pack_nchw_kernel<<<grid2(4096, B), 256, 0, st>>>(reinterpret_cast<const bf16 *>(x_bf16), B, n->x);
     HR_LAUNCHED(ctx);
     if ((e = forward(ctx, B, st))) return e;
     HR_CHECK(cudaMemsetAsync(n->loss, 0, sizeof(float), st));

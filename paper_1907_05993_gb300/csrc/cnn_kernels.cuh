@@ -63,21 +63,38 @@ struct ConvArgs {
     int N, H, W;
 };
 
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros (the
+// source address is then not read).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Implicit-GEMM 3x3 convolution, stride 1, zero padding:
 // y[p][o] = bias[o] + sum_{tap, c} x[p + off(tap)][c] w[o][tap][c], off = (ky-1, kx-1).
-// CTA tile 64 pixels x 64 output channels, 4 warps of 16 pixels x 64 channels.
-__global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a)
+// CTA tile: 128 output pixels (8 warps x 16) x BN output channels.  The K
+// dimension (9 taps x cin) is walked in k-steps of 16 channels of one tap;
+// KS k-steps form a pipeline stage whose A rows (the shifted input pixels,
+// zero-filled outside the image) and B rows (weights) arrive by cp.async,
+// STAGES stages in flight.
+template <int BN, int KS, int STAGES>
+__global__ void __launch_bounds__(256) conv3x3_kernel(ConvArgs a)
 {
-    constexpr int LDA = 24;   // bf16 per shared row (16 + 8 padding: conflict-free ldmatrix)
-    __shared__ __align__(16) bf16 sa[64 * LDA];
-    __shared__ __align__(16) bf16 sb[64 * LDA];
+    constexpr int BM = 128, LD = 24;   // bf16 per shared row (16 + 8 padding: conflict-free ldmatrix)
+    constexpr int A_EL = BM * LD, B_EL = BN * LD, STEP_EL = A_EL + B_EL, STAGE_EL = KS * STEP_EL;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    bf16 *sm = reinterpret_cast<bf16 *>(conv_smem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = a.N * a.H * a.W;
-    const int p0 = blockIdx.x * 64, o0 = blockIdx.y * 64;
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-    // this thread's load slots: pixel / output channel tid/2, half (8 channels) tid%2
+    const int p0 = blockIdx.x * BM, o0 = blockIdx.y * BN;
+    // loader slots: A row tid/2 (a pixel), half tid%2 (8 channels); B row tid/2 for tid < 2 BN
     const int lp = p0 + (tid >> 1), half = tid & 1;
     int pn = 0, py = 0, px = 0;
     if (lp < P) {
@@ -87,37 +104,59 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a)
         px = rem - py * a.W;
     }
     const int lo = o0 + (tid >> 1);
-    const int ncb = a.cin / 16;
-    for (int tap = 0; tap < 9; ++tap) {
-        const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-        const bool inside = lp < P && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        const bf16 *xrow = a.x + ((size_t)(pn * a.H + yy) * a.W + xx) * a.xs + a.xo + half * 8;
-        const bf16 *wrow = a.w + ((size_t)lo * 9 + tap) * a.cin + half * 8;
-        for (int cb = 0; cb < ncb; ++cb) {
-            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-            if (inside) va = *reinterpret_cast<const uint4 *>(xrow + cb * 16);
-            if (lo < a.cout) vb = *reinterpret_cast<const uint4 *>(wrow + cb * 16);
-            *reinterpret_cast<uint4 *>(sa + (tid >> 1) * LDA + half * 8) = va;
-            *reinterpret_cast<uint4 *>(sb + (tid >> 1) * LDA + half * 8) = vb;
-            __syncthreads();
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3, sa + (warp * 16 + (lane & 15)) * LDA + (lane >> 4) * 8);
+    const int ncb = a.cin / 16, KT = 9 * ncb, nstage = (KT + KS - 1) / KS;
+    auto load_stage = [&](int s) {
+        bf16 *base = sm + (s % STAGES) * STAGE_EL;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t b0, b1;
-                ldsm_x2(b0, b1, sb + (j * 8 + (lane & 7)) * LDA + ((lane >> 3) & 1) * 8);
-                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+        for (int j = 0; j < KS; ++j) {
+            const int kt = s * KS + j;
+            const int tap = kt / ncb, cb = kt - tap * ncb;
+            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+            const bool oka = kt < KT && lp < P && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *srca = oka ? a.x + ((size_t)(pn * a.H + yy) * a.W + xx) * a.xs + a.xo + cb * 16 + half * 8 : a.x;
+            cp_async16(base + j * STEP_EL + (tid >> 1) * LD + half * 8, srca, oka ? 16 : 0);
+            if (tid < 2 * BN) {
+                const bool okb = kt < KT && lo < a.cout;
+                const bf16 *srcb = okb ? a.w + ((size_t)lo * 9 + tap) * a.cin + cb * 16 + half * 8 : a.w;
+                cp_async16(base + j * STEP_EL + A_EL + (tid >> 1) * LD + half * 8, srcb, okb ? 16 : 0);
             }
-            __syncthreads();
+        }
+    };
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < nstage) load_stage(s);
+        cp_async_commit();
+    }
+    for (int s = 0; s < nstage; ++s) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();   // stage s is in shared memory; stage s - 1 is consumed by every warp
+        if (s + STAGES - 1 < nstage) load_stage(s + STAGES - 1);
+        cp_async_commit();
+        const bf16 *base = sm + (s % STAGES) * STAGE_EL;
+#pragma unroll
+        for (int j = 0; j < KS; ++j) {
+            const bf16 *sa = base + j * STEP_EL, *sb = sa + A_EL;
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(a0, a1, a2, a3, sa + (warp * 16 + (lane & 15)) * LD + (lane >> 4) * 8);
+#pragma unroll
+            for (int jn = 0; jn < BN / 8; ++jn) {
+                uint32_t b0, b1;
+                ldsm_x2(b0, b1, sb + (jn * 8 + (lane & 7)) * LD + ((lane >> 3) & 1) * 8);
+                mma_bf16(acc[jn], a0, a1, a2, a3, b0, b1);
+            }
         }
     }
-    // epilogue: rows (pixels) warp*16 + lane/4 (+8), columns j*8 + (lane%4)*2 (+1)
+    cp_async_wait<0>();
+    // epilogue: rows (pixels) warp*16 + lane/4 (+8), columns jn*8 + (lane%4)*2 (+1)
 #pragma unroll
     for (int hrow = 0; hrow < 2; ++hrow) {
         const int p = p0 + warp * 16 + (lane >> 2) + hrow * 8;
         if (p >= P) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < BN / 8; ++j) {
             const int o = o0 + j * 8 + (lane & 3) * 2;
             if (o >= a.cout) continue;
             float v0 = acc[j][hrow * 2], v1 = acc[j][hrow * 2 + 1];
@@ -139,6 +178,124 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(ConvArgs a)
             }
         }
     }
+}
+
+// Shared-memory bytes of conv3x3_kernel<BN, KS, STAGES>.
+constexpr size_t conv_smem_bytes(int bn, int ks, int stages) { return (size_t)stages * ks * (128 + bn) * 24 * 2; }
+
+// Same convolution for images of at least 16 x 16 pixels, as a persistent
+// kernel over spatial tiles of 8 rows x 16 columns of one image.  The CTA keeps
+// all 9 taps of its BN weight rows in shared memory and double-buffers the
+// (8 + 2) x (16 + 2)-pixel input halo of its tiles (zeros outside the image),
+// so that every tap is an offset into the halo: the A fragments come from
+// ldmatrix row addresses of the shifted pixels, with no per-tap copy.  Warp w
+// computes image row w of the tile (16 pixels) x BN output channels.  Shared
+// rows are padded by 16 bytes to an odd number of 16-byte units (conflict-free
+// ldmatrix).
+template <int CIN, int BN>
+struct HaloConv {
+    static constexpr int TH = 8, TW = 16, HH = TH + 2, HW = TW + 2, HPX = HH * HW;
+    static constexpr int RB = 2 * CIN + 16;       // bytes per halo pixel
+    static constexpr int WRB = 18 * CIN + 16;     // bytes per output channel (9 taps x CIN)
+    static constexpr size_t W_BYTES = (size_t)BN * WRB;
+    static constexpr size_t H_BYTES = (size_t)HPX * RB;
+    static constexpr size_t SMEM = W_BYTES + 2 * H_BYTES;
+};
+
+template <int CIN, int BN>
+__global__ void __launch_bounds__(256) conv3x3_halo_kernel(ConvArgs a)
+{
+    using G = HaloConv<CIN, BN>;
+    extern __shared__ __align__(16) unsigned char halo_smem[];
+    unsigned char *sw = halo_smem;
+    unsigned char *const sh0 = halo_smem + G::W_BYTES;   // halo buffers sh0, sh0 + H_BYTES
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int res = a.H;   // square images, res % 16 == 0
+    const int tx_n = res / G::TW, ty_n = res / G::TH, per_img = tx_n * ty_n;
+    const long long tiles = (long long)a.N * per_img;
+    const int o0 = blockIdx.y * BN;
+    constexpr int CCH = CIN / 8;   // 16-byte chunks per pixel
+    // weights of output channels o0 .. o0 + BN - 1, all taps
+    for (int i = tid; i < BN * 9 * CCH; i += blockDim.x) {
+        const int n = i / (9 * CCH), rem = i - n * 9 * CCH;
+        const int o = o0 + n;
+        const bool ok = o < a.cout;
+        cp_async16(sw + n * G::WRB + rem * 16, ok ? a.w + ((size_t)o * 9 * CIN + rem * 8) : a.w, ok ? 16 : 0);
+    }
+    auto load_halo = [&](long long t, unsigned char *dst) {
+        const int img = (int)(t / per_img), r = (int)(t - (long long)img * per_img);
+        const int y0 = (r / tx_n) * G::TH - 1, x0 = (r % tx_n) * G::TW - 1;
+        for (int i = tid; i < G::HPX * CCH; i += blockDim.x) {
+            const int px = i / CCH, c = i - px * CCH;
+            const int yy = y0 + px / G::HW, xx = x0 + px % G::HW;
+            const bool ok = yy >= 0 && yy < res && xx >= 0 && xx < res;
+            const bf16 *src = ok ? a.x + ((size_t)(img * res + yy) * res + xx) * a.xs + a.xo + c * 8 : a.x;
+            cp_async16(dst + px * G::RB + c * 16, src, ok ? 16 : 0);
+        }
+    };
+    long long t = blockIdx.x;
+    if (t < tiles) load_halo(t, sh0);
+    cp_async_commit();
+    for (int it = 0; t < tiles; ++it, t += gridDim.x) {
+        const long long tn = t + gridDim.x;
+        if (tn < tiles) load_halo(tn, sh0 + ((it + 1) & 1) * G::H_BYTES);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const unsigned char *hb = sh0 + (it & 1) * G::H_BYTES;
+        float acc[BN / 8][4];
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+        // lane's A row: pixel (warp, lane % 16) of the tile, channel half lane / 16
+        const unsigned char *arow = hb + (warp * G::HW + (lane & 15)) * G::RB + (lane >> 4) * 16;
+        const unsigned char *brow = sw + (lane & 7) * G::WRB + ((lane >> 3) & 1) * 16;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const unsigned char *ap = arow + ((tap / 3) * G::HW + tap % 3) * G::RB;
+#pragma unroll
+            for (int kb = 0; kb < CIN / 16; ++kb) {
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(a0, a1, a2, a3, ap + kb * 32);
+#pragma unroll
+                for (int jn = 0; jn < BN / 8; ++jn) {
+                    uint32_t b0, b1;
+                    ldsm_x2(b0, b1, brow + jn * 8 * G::WRB + (tap * CIN + kb * 16) * 2);
+                    mma_bf16(acc[jn], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+        // epilogue: pixels (warp, lane / 4 (+8)), channels jn * 8 + (lane % 4) * 2 (+1)
+        const int img = (int)(t / per_img), r = (int)(t - (long long)img * per_img);
+        const int yy = (r / tx_n) * G::TH + warp, xb = (r % tx_n) * G::TW;
+#pragma unroll
+        for (int hrow = 0; hrow < 2; ++hrow) {
+            const size_t p = (size_t)(img * res + yy) * res + xb + (lane >> 2) + hrow * 8;
+#pragma unroll
+            for (int j = 0; j < BN / 8; ++j) {
+                const int o = o0 + j * 8 + (lane & 3) * 2;
+                if (o >= a.cout) continue;
+                float v0 = acc[j][hrow * 2], v1 = acc[j][hrow * 2 + 1];
+                if (a.bias) {
+                    v0 += a.bias[o];
+                    v1 += a.bias[o + 1];
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                const size_t off = p * a.ys + a.yo + o;
+                if (a.y_fp32) {
+                    float *y = reinterpret_cast<float *>(a.y);
+                    *reinterpret_cast<float2 *>(y + off) = make_float2(v0, v1);
+                } else {
+                    *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(a.y) + off) =
+                        __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+        __syncthreads();   // the halo buffer of this tile may be refilled
+    }
+    cp_async_wait<0>();
 }
 
 struct WgradArgs {

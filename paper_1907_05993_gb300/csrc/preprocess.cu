@@ -263,3 +263,75 @@ extern "C" int hrebsd_downsample_batch(hrebsd_ctx *ctx, const float *in, int n, 
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
 }
+
+// Displacement field between pyramid resolutions (learned initialiser): planar
+// [B][2][h][w] -> [B][2][h2][w2], values rescaled to the new pixel unit.
+// Shrinking by f: box mean of f x f blocks / f.  Growing by f: bilinear sample
+// at x_c = (x_f + 0.5) / f - 0.5 (clamped to the image) times f, which for f = 2
+// is the prolongation between registration levels (Section 1).
+namespace {
+__device__ __forceinline__ float bilinear_plane(const float *__restrict__ M, int h, int w, float x, float y)
+{
+    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
+    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
+    const int x0 = min((int)x, max(w - 2, 0)), y0 = min((int)y, max(h - 2, 0));
+    const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+    const float fx = x - (float)x0, fy = y - (float)y0;
+    const float a = M[y0 * w + x0], b = M[y0 * w + x1], c = M[y1 * w + x0], d = M[y1 * w + x1];
+    const float top = fmaf(fx, b, (1.0f - fx) * a), bot = fmaf(fx, d, (1.0f - fx) * c);
+    return fmaf(fy, bot, (1.0f - fy) * top);
+}
+
+__global__ void field_resample_kernel(const float *__restrict__ in, int B, int h, int w, float *__restrict__ out,
+                                      int h2, int w2)
+{
+    const size_t total = (size_t)B * 2 * h2 * w2;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t plane = idx / ((size_t)h2 * w2);   // b * 2 + component
+        const int rem = (int)(idx - plane * h2 * w2), i = rem / w2, j = rem - i * w2;
+        const float *src = in + plane * h * w;
+        float v;
+        if (h2 <= h) {
+            const int f = h / h2;
+            float acc = 0.0f;
+            for (int a = 0; a < f; ++a)
+                for (int b = 0; b < f; ++b) acc += src[(size_t)(i * f + a) * w + j * f + b];
+            v = acc / (float)(f * f) / (float)f;
+        } else {
+            const int f = h2 / h;
+            const float inv = 1.0f / (float)f;
+            v = (float)f * bilinear_plane(src, h, w, ((float)j + 0.5f) * inv - 0.5f, ((float)i + 0.5f) * inv - 0.5f);
+        }
+        out[idx] = v;
+    }
+}
+
+bool pow2_ratio(int a, int b)   // a = b * 2^k, k >= 0
+{
+    if (a < b || a % b) return false;
+    const int r = a / b;
+    return (r & (r - 1)) == 0;
+}
+}  // namespace
+
+extern "C" int hrebsd_field_resample(hrebsd_ctx *ctx, const float *in, int B, int h, int w, float *out, int h2, int w2,
+                                     void *stream)
+{
+    if (!ctx || B < 0 || h < 1 || w < 1 || h2 < 1 || w2 < 1) return HREBSD_EINVAL;
+    const bool shrink = h2 <= h;
+    if (shrink ? !(pow2_ratio(h, h2) && pow2_ratio(w, w2) && h / h2 == w / w2)
+               : !(pow2_ratio(h2, h) && pow2_ratio(w2, w) && h2 / h == w2 / w))
+        return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!in || !out) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    const size_t total = (size_t)B * 2 * h2 * w2;
+    int grid = (int)((total + 255) / 256);
+    if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+    hr_prof_begin(ctx, hr_stream(stream));
+    field_resample_kernel<<<grid, 256, 0, hr_stream(stream)>>>(in, B, h, w, out, h2, w2);
+    hr_prof_end(ctx, PROF_CNN, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}

@@ -1,10 +1,12 @@
 """Training set, training loop and model file of the learned initialiser.
 
-The network (hrebsd_cnn_*) predicts the demons field at the 64x64 pyramid
-level from the 64x64 (reference, test) pair.  Its training targets are the
-fields this library's demons registration computes at that level on
-generated pairs (the registration being parity-checked against the oracle),
-i.e. exactly what the plain path would reach there.  Every step calls the
+The network (hrebsd_cnn_*) maps the 64x64 (reference, test) pair to a coarse
+64x64 displacement field.  Its training target is the FINAL field of this
+library's full multi-resolution registration of the generated pair (the
+registration being parity-checked against the oracle), box-averaged to 64x64
+in 64x64-pixel units (hrebsd_field_resample).  The registration of a new pair
+is then started at a finer level (128x128 by default) from the prediction
+resampled to that level, skipping the coarse levels.  Every step calls the
 library; this module only schedules the calls and moves tensors.
 """
 from __future__ import annotations
@@ -12,14 +14,18 @@ from __future__ import annotations
 import numpy as np
 
 from . import (cnn_params, demons_params, hrebsd_cnn_get_params, hrebsd_cnn_init, hrebsd_cnn_train_step,
-               hrebsd_demons_register_batch, hrebsd_downsample_batch, hrebsd_preprocess_batch)
+               hrebsd_demons_register_batch, hrebsd_downsample_batch, hrebsd_field_resample, hrebsd_preprocess_batch)
 
-TARGET_CAPS = (100, 100)          # iteration caps of the 64x64 and 32x32 levels
+TARGET_CAP = 100                  # iteration cap of every level of the target registration
 STOP = dict(window=5, tol=1e-4)   # the registration's stop rule
 
 
 def build_training_set(ctx, spec, chunk: int = 8192, pairs=None):
-    """(x [n,2,64,64] bf16, target [n,2,64,64] f32) CUDA tensors for the pairs of `spec`."""
+    """(x [n,2,64,64] bf16, target [n,2,64,64] f32) CUDA tensors for the pairs of `spec`.
+
+    Target: the final field of the full registration at spec.H (pyramid down to
+    32x32), resampled to 64x64."""
+    import math
     import torch
     from synth import gpu as SG
     from synth import kikuchi as K
@@ -29,7 +35,8 @@ def build_training_set(ctx, spec, chunk: int = 8192, pairs=None):
     n = len(pairs)
     x = torch.empty((n, 2, 64, 64), dtype=torch.bfloat16, device="cuda")
     y = torch.empty((n, 2, 64, 64), dtype=torch.float32, device="cuda")
-    prm = demons_params(2, TARGET_CAPS, 1.0, 1.0, 1.0, STOP["tol"], STOP["window"])
+    levels = int(round(math.log2(H / 32))) + 1
+    prm = demons_params(levels, [TARGET_CAP] * levels, 1.0, 1.0, 1.0, STOP["tol"], STOP["window"])
     for c0 in range(0, n, chunk):
         ps = pairs[c0:c0 + chunk]
         m = len(ps)
@@ -44,21 +51,24 @@ def build_training_set(ctx, spec, chunk: int = 8192, pairs=None):
         t64 = torch.empty((m, 64, 64), device="cuda")
         hrebsd_downsample_batch(ctx, refs, m, H, H, f, r64)
         hrebsd_downsample_batch(ctx, tests, m, H, H, f, t64)
-        field = torch.empty((m, 2, 64, 64), device="cuda")
-        iters = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+        field = torch.empty((m, 2, H, H), device="cuda")
+        iters = torch.empty((m, levels), dtype=torch.int32, device="cuda")
         status = torch.empty((m,), dtype=torch.int32, device="cuda")
         ridx = torch.arange(m, dtype=torch.int32, device="cuda")
-        hrebsd_demons_register_batch(ctx, r64, t64, ridx, m, m, 64, 64, prm, None, field, iters, status)
+        hrebsd_demons_register_batch(ctx, refs, tests, ridx, m, m, H, H, prm, None, field, iters, status)
+        hrebsd_field_resample(ctx, field, m, H, H, y[c0:c0 + m], 64, 64)
         x[c0:c0 + m, 0] = r64.to(torch.bfloat16)
         x[c0:c0 + m, 1] = t64.to(torch.bfloat16)
-        y[c0:c0 + m] = field
     torch.cuda.synchronize()
     return x, y
 
 
-def train(ctx, x, y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, params=None):
+def train(ctx, x, y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int = 0, params=None,
+          lr_final: float | None = None):
     """Adam on the MSE over shuffled mini-batches; returns the mean loss of every epoch.
-    params: initial parameter vector (None: He-normal from `seed`)."""
+    params: initial parameter vector (None: He-normal from `seed`).  lr_final: if given,
+    the step size follows a cosine from lr to lr_final over all steps."""
+    import math
     import torch
     hrebsd_cnn_init(ctx, init_params(seed) if params is None else params)
     n = x.shape[0]
@@ -66,6 +76,9 @@ def train(ctx, x, y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int 
     g.manual_seed(seed)
     loss = torch.zeros(1, device="cuda")
     hist = []
+    steps_per_epoch = max(1, n // batch)
+    total = epochs * steps_per_epoch
+    step = 0
     for _ in range(epochs):
         perm = torch.randperm(n, device="cuda", generator=g)
         tot = torch.zeros(1, device="cuda")
@@ -73,7 +86,9 @@ def train(ctx, x, y, epochs: int, batch: int = 256, lr: float = 1e-3, seed: int 
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
             xb, yb = x[idx].contiguous(), y[idx].contiguous()
-            hrebsd_cnn_train_step(ctx, xb, yb, batch, lr, loss)
+            lr_k = lr if lr_final is None else lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * step / total))
+            hrebsd_cnn_train_step(ctx, xb, yb, batch, lr_k, loss)
+            step += 1
             tot += loss
             steps += 1
         hist.append(float(tot) / max(1, steps))

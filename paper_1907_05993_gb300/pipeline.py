@@ -14,7 +14,7 @@ import numpy as np
 
 from . import (demons_params, hrebsd_autotune, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
                hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
-               hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
+               hrebsd_field_resample, hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
 
 
 @dataclass
@@ -77,12 +77,13 @@ class Pipeline:
         return out
 
     def run(self, refs_raw, tests_raw, ref_idx, stream=None, init_field=None, start_level=-1, out=None,
-            learned_caps=None):
+            learned_caps=None, learned_start_res=128):
         """refs_raw [R,H,W], tests_raw [B,H,W] float32 CUDA; ref_idx [B] int32 CUDA.
 
-        learned_caps (per level, finest first): start the registration at the 64x64 level
-        from the learned initialiser's field (hrebsd_cnn_infer_patterns; the network must be
-        loaded in this pipeline's context) with these iteration caps."""
+        learned_caps (per level, finest first): start the registration at the level of
+        learned_start_res x learned_start_res pixels from the learned initialiser's 64x64
+        field (hrebsd_cnn_infer_patterns, resampled by hrebsd_field_resample; the network
+        must be loaded in this pipeline's context) with these iteration caps."""
         t = self.torch
         c = self.cfg
         R, B = refs_raw.shape[0], tests_raw.shape[0]
@@ -105,9 +106,15 @@ class Pipeline:
         params = self.params
         params.start_level = start_level
         if learned_caps is not None:
-            lvl = int(round(np.log2(H / 64)))
-            init_field = get("field64", (B, 2, 64, 64), t.float32)
-            hrebsd_cnn_infer_patterns(self.ctx, ref_p, test_p, ref_idx, B, H, W, init_field, stream)
+            r = learned_start_res
+            lvl = int(round(np.log2(H / r)))
+            net = get("field64", (B, 2, 64, 64), t.float32)
+            hrebsd_cnn_infer_patterns(self.ctx, ref_p, test_p, ref_idx, B, H, W, net, stream)
+            if r == 64:
+                init_field = net
+            else:
+                init_field = get(f"field_init{r}", (B, 2, r, r), t.float32)
+                hrebsd_field_resample(self.ctx, net, B, 64, 64, init_field, r, r, stream)
             params = demons_params(c.levels, learned_caps, c.alpha, c.sigma, c.sigma, c.stop_tol, c.stop_window, lvl)
         hrebsd_demons_register_batch(self.ctx, ref_p, test_p, ref_idx, R, B, H, W, params, init_field, field,
                                      iters, status, stream)

@@ -416,3 +416,26 @@ def test_strain_stress_parity(torch, lib, ctx, traction_free):
         assert np.abs(FS[b] - f_e).max() < 1e-12
         assert np.abs(E[b] - e_e).max() < 1e-12
         assert np.abs(SG[b] - s_e).max() < 1e-9 * max(1.0, np.abs(s_e).max())
+
+
+# ------------------------------------------------------------------ field resampling (learned start)
+def test_field_resample_parity(torch, lib, ctx, oracle):
+    """x2 growth is the registration's prolongation; /4 shrink is two 2x2 box means, /4 in value."""
+    rng = np.random.default_rng(5)
+    B = 3
+    small = rng.normal(0, 2, (B, 2, 32, 32))
+    out = torch.empty((B, 2, 64, 64), dtype=torch.float32, device="cuda")
+    lib.hrebsd_field_resample(ctx, cuda(torch, small, torch.float32), B, 32, 32, out, 64, 64)
+    big = rng.normal(0, 2, (B, 2, 128, 128))
+    out2 = torch.empty((B, 2, 32, 32), dtype=torch.float32, device="cuda")
+    lib.hrebsd_field_resample(ctx, cuda(torch, big, torch.float32), B, 128, 128, out2, 32, 32)
+    torch.cuda.synchronize()
+    g1, g2 = out.cpu().numpy(), out2.cpu().numpy()
+    for b in range(B):
+        exp = oracle.prolong(f32(small[b]))
+        assert np.abs(g1[b] - exp).max() <= 1e-5
+        for c in range(2):
+            e2 = oracle.reduce2(oracle.reduce2(f32(big[b, c]))) / 4
+            assert np.abs(g2[b, c] - e2).max() <= 1e-5
+    with pytest.raises(lib.HrebsdError):
+        lib.hrebsd_field_resample(ctx, out, B, 64, 64, out2, 48, 48)
