@@ -266,10 +266,12 @@ def run_ours(args, rank, world, local_rank):
     t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, device="cuda")
     value = world * B * args.steps / t
     tune_ms = pipe._tuned.get((B, wl["H"], wl["W"]))
+
+    def shape_name(v):
+        return "x".join(map(str, P.TILE_SHAPES[v])) + f"/{P.TILE_THREADS[v]}t"
     tile_choice = None if tune_ms is None else [
-        {"level": l, "shape": "x".join(map(str, P.TILE_SHAPES[P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l,
-                                                                                           wl["W"] >> l)])),
-         "ms_per_iteration_by_shape": {"x".join(map(str, P.TILE_SHAPES[v])): round(float(tune_ms[l, v]), 4)
+        {"level": l, "shape": shape_name(P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l)),
+         "ms_per_iteration_by_shape": {shape_name(v): round(float(tune_ms[l, v]), 4)
                                        for v in range(P.TILE_VARIANTS) if np.isfinite(tune_ms[l, v])}}
         for l in range(wl["levels"])]
     iters = out["iters"].cpu().numpy()

@@ -257,8 +257,9 @@ def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, s
          "hrebsd_solve_F")
 
 
-TILE_VARIANTS = 3
-TILE_SHAPES = ((64, 32), (32, 32), (64, 16))
+TILE_VARIANTS = 4
+TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32))
+TILE_THREADS = (256, 256, 256, 512)
 
 
 def hrebsd_autotune(ctx, B, H, W, params, stream=None):

@@ -429,14 +429,14 @@ __device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, 
     }
 }
 
-template <int RAD, int TX_, int TY_, int MINB>
-__global__ void __launch_bounds__(kIterThreads, MINB) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
+template <int RAD, int TX_, int TY_, int MINB, int NT_>
+__global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
                                                                              const __grid_constant__ CUtensorMap tmF,
                                                                              IterArgs a)
 {
     using L = Geo<RAD, TX_, TY_>;
     using G = GeoT<RAD, TX_, TY_>;
-    constexpr int NT = kIterThreads;
+    constexpr int NT = NT_;
     extern __shared__ __align__(1024) unsigned char smraw[];
     float2 *sS = reinterpret_cast<float2 *>(smraw + G::S_OFF);   // [AHP][AST]
     float *sF = reinterpret_cast<float *>(smraw + G::F_OFF);     // [FH][FWB]
@@ -527,51 +527,51 @@ __global__ void __launch_bounds__(kIterThreads, MINB) demons_iter_tma_kernel(con
         }
         __syncthreads();
 
-        // ---- warp + force on T + r, runs of 4 pixels.  Every run is computed the
-        // same way (no divergent border path): the test-image tile has replicated
-        // borders, so the central difference becomes the one-sided one at the
-        // image edge once scaled by 1 instead of 1/2; points outside the image
-        // are overwritten below by the replicated in-image values.
+        // ---- warp + force on T + r, vertical runs of 4 pixels (one column, four
+        // rows per thread; consecutive threads take consecutive columns, so the
+        // moving-image gathers of a warp are row-contiguous and the shared-memory
+        // accesses conflict-free).  Every run is computed the same way (no
+        // divergent border path): the test-image tile has replicated borders, so
+        // the central difference becomes the one-sided one at the image edge once
+        // scaled by 1 instead of 1/2; points outside the image are overwritten
+        // below by the replicated in-image values.  Rows of the last group beyond
+        // T + r are computed from padding and discarded.
         float ssd = 0.0f;
-        constexpr int NRUN = (L::BW + 3) / 4;
+        constexpr int NG = (L::BH + 3) / 4;
         constexpr int FC = G::FOFF - RAD;   // test-image column of local column 0
-        for (int it = tid; it < NRUN * L::BH; it += NT) {
-            const int r = it / NRUN, c0 = 4 * (it - r * NRUN);
-            const int vy = y0 - RAD + r, vx0 = x0 - RAD + c0;
-            const bool rowT = r >= RAD && r < RAD + TY_ && vy < h;
-            const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
-            const float4 *up = reinterpret_cast<const float4 *>(sU + r * L::UST + c0);
-            const float4 ua = up[0], ub = up[1];
-            const float ux[4] = {ua.x, ua.z, ub.x, ub.z}, uy[4] = {ua.y, ua.w, ub.y, ub.w};
-            const float *fm = sF + (r + 1) * G::FWB + c0 + FC;
-            float fl[6], fu[4], fd[4];
+        for (int it = tid; it < NG * L::BW; it += NT) {
+            const int g = it / L::BW, c = it - g * L::BW;
+            const int r0 = 4 * g;
+            const int vx = x0 - RAD + c, vy0 = y0 - RAD + r0;
+            const bool colT = c >= RAD && c < RAD + TX_ && vx < w;
+            const float sx = (vx == 0 || vx == w - 1) ? 1.0f : 0.5f;
+            const float *fcol = sF + r0 * G::FWB + c + FC;   // test image, local rows r0 - 1 .. r0 + 4
+            float fv[6], fl[4], fr[4];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) fl[i] = fm[i - 1];
+            for (int j = 0; j < 6; ++j) fv[j] = fcol[j * G::FWB];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                fu[i] = fm[i - G::FWB];
-                fd[i] = fm[i + G::FWB];
+                fl[i] = fcol[(i + 1) * G::FWB - 1];
+                fr[i] = fcol[(i + 1) * G::FWB + 1];
             }
+            float2 u[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[i] = sU[(r0 + i) * L::UST + c];
             float mw[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) mw[i] = bilinear_clamped(M, h, w, (float)(vx0 + i) - ux[i], (float)vy - uy[i]);
-            float2 du[4];
+            for (int i = 0; i < 4; ++i) mw[i] = bilinear_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int vx = vx0 + i;
-                const float sx = (vx == 0 || vx == w - 1) ? 1.0f : 0.5f;
-                const float gx = sx * (fl[i + 2] - fl[i]);
-                const float gy = sy * (fd[i] - fu[i]);
-                const float d = mw[i] - fl[i + 1];
+                const int r = r0 + i, vy = vy0 + i;
+                const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
+                const float gx = sx * (fr[i] - fl[i]);
+                const float gy = sy * (fv[i + 2] - fv[i]);
+                const float d = mw[i] - fv[i + 1];
                 const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
                 const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
-                du[i] = make_float2(t * gx, t * gy);
-                const int c = c0 + i;
-                if (rowT && c >= RAD && c < RAD + TX_ && vx < w) ssd = fmaf(d, d, ssd);
+                if (L::BH % 4 == 0 || r < L::BH) sD[r * L::DST + c] = make_float2(t * gx, t * gy);
+                if (colT && r >= RAD && r < RAD + TY_ && vy < h) ssd = fmaf(d, d, ssd);
             }
-            float4 *dp = reinterpret_cast<float4 *>(sD + r * L::DST + c0);
-            dp[0] = make_float4(du[0].x, du[0].y, du[1].x, du[1].y);
-            dp[1] = make_float4(du[2].x, du[2].y, du[3].x, du[3].y);
         }
         if (border) {   // du outside the image = du at the clamped position
             __syncthreads();
@@ -778,7 +778,7 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
-template <int RAD, int TX_, int TY_, int MINB>
+template <int RAD, int TX_, int TY_, int MINB, int NT_>
 int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a, int max_items,
                     cudaStream_t st)
 {
@@ -786,9 +786,9 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB>;
+        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_>;
         HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kIterThreads, smem));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT_, smem));
         if (occ < 1) occ = 1;
         configured_dev = ctx->device;
     }
@@ -796,7 +796,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    demons_iter_tma_kernel<RAD, TX_, TY_, MINB><<<grid, kIterThreads, smem, st>>>(tmS, tmF, a);
+    demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_><<<grid, NT_, smem, st>>>(tmS, tmF, a);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -823,9 +823,9 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, i
 // (and hence the last bits of the level SSD) are grouped differently.  The
 // extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
 // use shape 0.
-constexpr int kTileVariants = 3;
-constexpr int kVarTX[kTileVariants] = {64, 32, 64};
-constexpr int kVarTY[kTileVariants] = {32, 32, 16};
+constexpr int kTileVariants = 4;
+constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32};
 constexpr int kMinTX = 32, kMinTY = 16;
 bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }   // smallest tile extents (sizes the SSD partials)
 static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
@@ -901,23 +901,24 @@ int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit
 
 
 #define HR_TMA_VARIANTS(RAD, CALL)                                                                                 \
-    case 0: return CALL(RAD, 64, 32, 2);                                                                           \
-    case 1: if (RAD == 3) return CALL(3, 32, 32, 3); break;                                                        \
-    case 2: if (RAD == 3) return CALL(3, 64, 16, 3); break;
+    case 0: return CALL(RAD, 64, 32, 2, 256);                                                                      \
+    case 1: if (RAD == 3) return CALL(3, 32, 32, 3, 256); break;                                                   \
+    case 2: if (RAD == 3) return CALL(3, 64, 16, 3, 256); break;                                                   \
+    case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512); break;
 
 bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w,
                  CUtensorMap *tmS, CUtensorMap *tmF)
 {
-#define HR_ENC(R, X, Y, MB) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
+#define HR_ENC(R, X, Y, MB, NT) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
     switch (rad) {
-    case 1: return var == 0 && HR_ENC(1, 64, 32, 2);
-    case 2: return var == 0 && HR_ENC(2, 64, 32, 2);
+    case 1: return var == 0 && HR_ENC(1, 64, 32, 2, 256);
+    case 2: return var == 0 && HR_ENC(2, 64, 32, 2, 256);
     case 3:
         switch (var) { HR_TMA_VARIANTS(3, HR_ENC) default: break; }
         return false;
-    case 4: return var == 0 && HR_ENC(4, 64, 32, 2);
-    case 5: return var == 0 && HR_ENC(5, 64, 32, 2);
-    case 6: return var == 0 && HR_ENC(6, 64, 32, 2);
+    case 4: return var == 0 && HR_ENC(4, 64, 32, 2, 256);
+    case 5: return var == 0 && HR_ENC(5, 64, 32, 2, 256);
+    case 6: return var == 0 && HR_ENC(6, 64, 32, 2, 256);
     default: return false;
     }
 #undef HR_ENC
@@ -926,16 +927,16 @@ bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const flo
 int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, int var, const CUtensorMap &tmS, const CUtensorMap &tmF,
                       const IterArgs &a, int max_items, cudaStream_t st)
 {
-#define HR_LT(R, X, Y, MB) launch_iter_tma<R, X, Y, MB>(ctx, tmS, tmF, a, max_items, st)
+#define HR_LT(R, X, Y, MB, NT) launch_iter_tma<R, X, Y, MB, NT>(ctx, tmS, tmF, a, max_items, st)
     switch (rad) {
-    case 1: if (var == 0) return HR_LT(1, 64, 32, 2); break;
-    case 2: if (var == 0) return HR_LT(2, 64, 32, 2); break;
+    case 1: if (var == 0) return HR_LT(1, 64, 32, 2, 256); break;
+    case 2: if (var == 0) return HR_LT(2, 64, 32, 2, 256); break;
     case 3:
         switch (var) { HR_TMA_VARIANTS(3, HR_LT) default: break; }
         break;
-    case 4: if (var == 0) return HR_LT(4, 64, 32, 2); break;
-    case 5: if (var == 0) return HR_LT(5, 64, 32, 2); break;
-    case 6: if (var == 0) return HR_LT(6, 64, 32, 2); break;
+    case 4: if (var == 0) return HR_LT(4, 64, 32, 2, 256); break;
+    case 5: if (var == 0) return HR_LT(5, 64, 32, 2, 256); break;
+    case 6: if (var == 0) return HR_LT(6, 64, 32, 2, 256); break;
     default: break;
     }
 #undef HR_LT
