@@ -429,7 +429,7 @@ __device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, 
     }
 }
 
-template <int RAD, int TX_, int TY_, int MINB, int NT_>
+template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR>
 __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
                                                                              const __grid_constant__ CUtensorMap tmF,
                                                                              IterArgs a)
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         }
         __syncthreads();
 
-        // ---- warp + force on T + r, vertical runs of 4 pixels (one column, four
+        // ---- warp + force on T + r, vertical runs of FR pixels (one column, FR
         // rows per thread; consecutive threads take consecutive columns, so the
         // moving-image gathers of a warp are row-contiguous and the shared-memory
         // accesses conflict-free).  Every run is computed the same way (no
@@ -537,31 +537,31 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         // below by the replicated in-image values.  Rows of the last group beyond
         // T + r are computed from padding and discarded.
         float ssd = 0.0f;
-        constexpr int NG = (L::BH + 3) / 4;
+        constexpr int NG = (L::BH + FR - 1) / FR;
         constexpr int FC = G::FOFF - RAD;   // test-image column of local column 0
         for (int it = tid; it < NG * L::BW; it += NT) {
             const int g = it / L::BW, c = it - g * L::BW;
-            const int r0 = 4 * g;
+            const int r0 = FR * g;
             const int vx = x0 - RAD + c, vy0 = y0 - RAD + r0;
             const bool colT = c >= RAD && c < RAD + TX_ && vx < w;
             const float sx = (vx == 0 || vx == w - 1) ? 1.0f : 0.5f;
-            const float *fcol = sF + r0 * G::FWB + c + FC;   // test image, local rows r0 - 1 .. r0 + 4
-            float fv[6], fl[4], fr[4];
+            const float *fcol = sF + r0 * G::FWB + c + FC;   // test image, local rows r0 - 1 .. r0 + FR
+            float fv[FR + 2], fl[FR], fr[FR];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) fv[j] = fcol[j * G::FWB];
+            for (int j = 0; j < FR + 2; ++j) fv[j] = fcol[j * G::FWB];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < FR; ++i) {
                 fl[i] = fcol[(i + 1) * G::FWB - 1];
                 fr[i] = fcol[(i + 1) * G::FWB + 1];
             }
-            float2 u[4];
+            float2 u[FR];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) u[i] = sU[(r0 + i) * L::UST + c];
-            float mw[4];
+            for (int i = 0; i < FR; ++i) u[i] = sU[(r0 + i) * L::UST + c];
+            float mw[FR];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) mw[i] = bilinear_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y);
+            for (int i = 0; i < FR; ++i) mw[i] = bilinear_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < FR; ++i) {
                 const int r = r0 + i, vy = vy0 + i;
                 const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
                 const float gx = sx * (fr[i] - fl[i]);
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 const float d = mw[i] - fv[i + 1];
                 const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
                 const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
-                if (L::BH % 4 == 0 || r < L::BH) sD[r * L::DST + c] = make_float2(t * gx, t * gy);
+                if (L::BH % FR == 0 || r < L::BH) sD[r * L::DST + c] = make_float2(t * gx, t * gy);
                 if (colT && r >= RAD && r < RAD + TY_ && vy < h) ssd = fmaf(d, d, ssd);
             }
         }
@@ -778,7 +778,7 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
-template <int RAD, int TX_, int TY_, int MINB, int NT_>
+template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR>
 int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a, int max_items,
                     cudaStream_t st)
 {
@@ -786,7 +786,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_>;
+        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR>;
         HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT_, smem));
         if (occ < 1) occ = 1;
@@ -796,7 +796,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_><<<grid, NT_, smem, st>>>(tmS, tmF, a);
+    demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR><<<grid, NT_, smem, st>>>(tmS, tmF, a);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -901,24 +901,24 @@ int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit
 
 
 #define HR_TMA_VARIANTS(RAD, CALL)                                                                                 \
-    case 0: return CALL(RAD, 64, 32, 2, 256);                                                                      \
-    case 1: if (RAD == 3) return CALL(3, 32, 32, 3, 256); break;                                                   \
-    case 2: if (RAD == 3) return CALL(3, 64, 16, 3, 256); break;                                                   \
-    case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512); break;
+    case 0: return CALL(RAD, 64, 32, 2, 256, 4);                                                                   \
+    case 1: if (RAD == 3) return CALL(3, 32, 32, 3, 256, 4); break;                                                \
+    case 2: if (RAD == 3) return CALL(3, 64, 16, 3, 256, 4); break;                                                \
+    case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512, 4); break;
 
 bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w,
                  CUtensorMap *tmS, CUtensorMap *tmF)
 {
-#define HR_ENC(R, X, Y, MB, NT) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
+#define HR_ENC(R, X, Y, MB, NT, FR) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
     switch (rad) {
-    case 1: return var == 0 && HR_ENC(1, 64, 32, 2, 256);
-    case 2: return var == 0 && HR_ENC(2, 64, 32, 2, 256);
+    case 1: return var == 0 && HR_ENC(1, 64, 32, 2, 256, 4);
+    case 2: return var == 0 && HR_ENC(2, 64, 32, 2, 256, 4);
     case 3:
         switch (var) { HR_TMA_VARIANTS(3, HR_ENC) default: break; }
         return false;
-    case 4: return var == 0 && HR_ENC(4, 64, 32, 2, 256);
-    case 5: return var == 0 && HR_ENC(5, 64, 32, 2, 256);
-    case 6: return var == 0 && HR_ENC(6, 64, 32, 2, 256);
+    case 4: return var == 0 && HR_ENC(4, 64, 32, 2, 256, 4);
+    case 5: return var == 0 && HR_ENC(5, 64, 32, 2, 256, 4);
+    case 6: return var == 0 && HR_ENC(6, 64, 32, 2, 256, 4);
     default: return false;
     }
 #undef HR_ENC
@@ -927,16 +927,16 @@ bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const flo
 int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, int var, const CUtensorMap &tmS, const CUtensorMap &tmF,
                       const IterArgs &a, int max_items, cudaStream_t st)
 {
-#define HR_LT(R, X, Y, MB, NT) launch_iter_tma<R, X, Y, MB, NT>(ctx, tmS, tmF, a, max_items, st)
+#define HR_LT(R, X, Y, MB, NT, FR) launch_iter_tma<R, X, Y, MB, NT, FR>(ctx, tmS, tmF, a, max_items, st)
     switch (rad) {
-    case 1: if (var == 0) return HR_LT(1, 64, 32, 2, 256); break;
-    case 2: if (var == 0) return HR_LT(2, 64, 32, 2, 256); break;
+    case 1: if (var == 0) return HR_LT(1, 64, 32, 2, 256, 4); break;
+    case 2: if (var == 0) return HR_LT(2, 64, 32, 2, 256, 4); break;
     case 3:
         switch (var) { HR_TMA_VARIANTS(3, HR_LT) default: break; }
         break;
-    case 4: if (var == 0) return HR_LT(4, 64, 32, 2, 256); break;
-    case 5: if (var == 0) return HR_LT(5, 64, 32, 2, 256); break;
-    case 6: if (var == 0) return HR_LT(6, 64, 32, 2, 256); break;
+    case 4: if (var == 0) return HR_LT(4, 64, 32, 2, 256, 4); break;
+    case 5: if (var == 0) return HR_LT(5, 64, 32, 2, 256, 4); break;
+    case 6: if (var == 0) return HR_LT(6, 64, 32, 2, 256, 4); break;
     default: break;
     }
 #undef HR_LT
