@@ -141,18 +141,18 @@ __device__ __forceinline__ void run_x(const float2 *in, float2 *out, const float
         win[2 * j] = make_float2(v.x, v.y);
         win[2 * j + 1] = make_float2(v.z, v.w);
     }
+    // tap-outer order: RUN independent accumulation chains per step (the sum
+    // order of every output is still k = 0 .. 2r)
+    float2 acc[RUN];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o) acc[o] = __fmul2_rn(t[0], win[o]);
+#pragma unroll
+    for (int k = 1; k <= 2 * RAD; ++k)
+#pragma unroll
+        for (int o = 0; o < RUN; ++o) acc[o] = ffma2(t[k], win[o + k], acc[o]);
     float4 *out4 = reinterpret_cast<float4 *>(out);
 #pragma unroll
-    for (int o = 0; o < RUN; o += 2) {
-        float2 a0 = __fmul2_rn(t[0], win[o]);
-        float2 a1 = __fmul2_rn(t[0], win[o + 1]);
-#pragma unroll
-        for (int k = 1; k <= 2 * RAD; ++k) {
-            a0 = ffma2(t[k], win[o + k], a0);
-            a1 = ffma2(t[k], win[o + 1 + k], a1);
-        }
-        out4[o / 2] = make_float4(a0.x, a0.y, a1.x, a1.y);
-    }
+    for (int o = 0; o < RUN; o += 2) out4[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
 }
 
 // Same along a column: in[j * stride], j = 0..RUN + 2r - 1 -> acc[o].
@@ -164,12 +164,11 @@ __device__ __forceinline__ void run_y(const float2 *in, int stride, const float2
 #pragma unroll
     for (int j = 0; j < NW; ++j) win[j] = in[j * stride];
 #pragma unroll
-    for (int o = 0; o < RUN; ++o) {
-        float2 v = __fmul2_rn(t[0], win[o]);
+    for (int o = 0; o < RUN; ++o) acc[o] = __fmul2_rn(t[0], win[o]);
 #pragma unroll
-        for (int k = 1; k <= 2 * RAD; ++k) v = ffma2(t[k], win[o + k], v);
-        acc[o] = v;
-    }
+    for (int k = 1; k <= 2 * RAD; ++k)
+#pragma unroll
+        for (int o = 0; o < RUN; ++o) acc[o] = ffma2(t[k], win[o + k], acc[o]);
 }
 
 // One item of work: a tile of one active pair.
@@ -517,15 +516,8 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             hr_tma::fence_proxy_async();
             issue_S(tile_of<TX_, TY_>(a, next));
         }
-        constexpr int NSY = L::BHP / RUN;
-        for (int it = tid; it < NSY * L::BWP; it += NT) {
-            const int seg = it / L::BWP, col = it - seg * L::BWP;
-            float2 acc[RUN];
-            run_y<RAD>(sX + seg * RUN * L::XST + col, L::XST, tf, acc);
-#pragma unroll
-            for (int o = 0; o < RUN; ++o) sU[(seg * RUN + o) * L::UST + col] = acc[o];
-        }
-        __syncthreads();
+        // ---- (the y pass of G_f runs inside the force stage below, on each
+        // thread's own column run; u on T + r is kept in sU for the last stage)
 
         // ---- warp + force on T + r, vertical runs of FR pixels (one column, FR
         // rows per thread; consecutive threads take consecutive columns, so the
@@ -555,8 +547,20 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 fr[i] = fcol[(i + 1) * G::FWB + 1];
             }
             float2 u[FR];
+            {   // y pass of G_f for rows r0 .. r0 + FR - 1 of column c (same sum order as run_y)
+                static_assert(((L::BH + FR - 1) / FR) * FR <= L::BHP, "force runs stay inside sU");
+                float2 win[FR + 2 * RAD];
 #pragma unroll
-            for (int i = 0; i < FR; ++i) u[i] = sU[(r0 + i) * L::UST + c];
+                for (int j = 0; j < FR + 2 * RAD; ++j) win[j] = sX[(r0 + j) * L::XST + c];
+#pragma unroll
+                for (int i = 0; i < FR; ++i) u[i] = __fmul2_rn(tf[0], win[i]);
+#pragma unroll
+                for (int k = 1; k <= 2 * RAD; ++k)
+#pragma unroll
+                    for (int i = 0; i < FR; ++i) u[i] = ffma2(tf[k], win[i + k], u[i]);
+#pragma unroll
+                for (int i = 0; i < FR; ++i) sU[(r0 + i) * L::UST + c] = u[i];
+            }
             float mw[FR];
 #pragma unroll
             for (int i = 0; i < FR; ++i) mw[i] = bilinear_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y);
