@@ -215,8 +215,8 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small
- * rotation field (min(B, 2048) pairs; 2 warm-up then 5 timed iterations,
- * CUDA events on `stream`) and keep the fastest for later registrations of
+ * rotation field (min(B, 2048) pairs; 2 warm-up iterations, then the best of
+ * 3 timed batches of 4, CUDA events on `stream`) and keep the fastest for later registrations of
  * that level size in this context.  Synchronises `stream`; uses context
  * workspace.  ms_out (host, nullable): [levels][HREBSD_TILE_VARIANTS]
  * milliseconds per iteration, NaN where a shape is unavailable.  Returns

@@ -1332,19 +1332,31 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 a.in_is_s = 1;
                 a.alpha2 = p->alpha * p->alpha;
                 a.taps = taps;
-                constexpr int kWarm = 2, kTimed = 5;
-                for (int k = 0; k < kWarm + kTimed; ++k) {
-                    if (k == kWarm) HR_CHECK(cudaEventRecord(ev[0], st));
+                // 2 warm-up iterations, then the best of 3 timed batches of 4
+                constexpr int kWarm = 2, kBatch = 4, kRounds = 3;
+                float ms = 0.0f;
+                int k = 0;
+                for (; k < kWarm; ++k) {
                     a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                     a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
                     int e2 = dispatch_iter_tma(ctx, rad, v, tmS[k & 1], tmF, a, Bt * tiles, st);
                     if (e2) return e2;
                 }
-                HR_CHECK(cudaEventRecord(ev[1], st));
-                HR_CHECK(cudaEventSynchronize(ev[1]));
-                float ms = 0.0f;
-                HR_CHECK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-                ms /= (float)kTimed;
+                for (int rep = 0; rep < kRounds; ++rep) {
+                    HR_CHECK(cudaEventRecord(ev[0], st));
+                    for (int j = 0; j < kBatch; ++j, ++k) {
+                        a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
+                        a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
+                        int e2 = dispatch_iter_tma(ctx, rad, v, tmS[k & 1], tmF, a, Bt * tiles, st);
+                        if (e2) return e2;
+                    }
+                    HR_CHECK(cudaEventRecord(ev[1], st));
+                    HR_CHECK(cudaEventSynchronize(ev[1]));
+                    float t = 0.0f;
+                    HR_CHECK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+                    t /= (float)kBatch;
+                    if (rep == 0 || t < ms) ms = t;
+                }
                 if (ms_out) ms_out[l * kTileVariants + v] = ms;
                 if (best_v == 0 && best == 0.0f) {
                     best = ms;
