@@ -156,6 +156,22 @@ def measured_peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def xcf_roofline(ms, B, wl, fp32_peak_tflops, hbm_peak):
+    """ROI cross-correlation against the FP32 FMA peak (probe) and HBM.  Algorithmic work
+    per ROI of S x S: one packed complex forward FFT and one inverse (5 S^2 log2 S^2 each)
+    plus ~20 S^2 for the cross power and unpacking; bytes: both ROIs read, 2 S^2 x 4 B."""
+    import math
+    S, N = wl["S"], len(wl["roi"])
+    flops = B * N * (2 * 5 * S * S * math.log2(S * S) + 20 * S * S)
+    nbytes = B * N * 2 * S * S * 4
+    t = ms / 1e3
+    return {"kernel": "xcf64_kernel", "ms_per_step": ms,
+            "tflops": flops / t / 1e12, "fp32_peak_tflops_probe": fp32_peak_tflops,
+            "frac_fp32": flops / t / 1e12 / fp32_peak_tflops,
+            "gbs": nbytes / t / 1e9, "frac_hbm": nbytes / t / 1e9 / hbm_peak,
+            "algorithmic": f"{flops / B / 1e6:.2f} MFLOP and {nbytes / B / 1e3:.0f} KB per pair"}
+
+
 def traffic_per_launch(px_per_launch):
     """DRAM bytes per demons-iteration launch from the committed ncu summary, if it still matches the kernel."""
     path = os.path.join(ROOT, "profiles", "demons_iter_traffic.json")
@@ -307,6 +323,16 @@ def run_ours(args, rank, world, local_rank):
     h2d = tests.numel() * 4 + refs.numel() * 4 + ridx.numel() * 4
     d2h = B * 9 * 8 * 2 + B * 4
 
+    # FP32 FMA throughput of this GPU (probe kernel), the ALU peak of the XCF roofline
+    P.hrebsd_probe_fp32_fma(pipe.ctx, 256)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    probe_flops = sum(P.hrebsd_probe_fp32_fma(pipe.ctx, 4096) for _ in range(3))
+    p1.record(stream)
+    torch.cuda.synchronize()
+    fp32_peak = probe_flops / (p0.elapsed_time(p1) / 1e3) / 1e12
+
     if rank == 0:
         it = prof["demons_iter"]
         px = prof["pixel_iters"]
@@ -331,6 +357,7 @@ def run_ours(args, rank, world, local_rank):
                                               f"{px_per_launch:.0f} pixel-iterations per launch (average)",
                          "avg_launch_ms": it["ms"] / max(1, it["launches"]),
                          "share_of_step": it["ms"] / total_ms if total_ms else None},
+            "xcf_roofline": xcf_roofline(prof["xcf"]["ms"] / args.steps, B, wl, fp32_peak, peak),
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if k != "pixel_iters"},
             "demons_tile_shape_per_level": tile_choice,
             "demons_iters_mean_per_level": [float(x) for x in iters.mean(axis=0)],

@@ -269,6 +269,13 @@ int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N
                    const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
                    void *stream);
 
+/* Measurement helper (no counterpart in the paper): launch an FP32 FMA
+ * throughput probe on `stream` (SMs x 8 CTAs of 256 threads, each thread 8
+ * independent chains of packed FP32x2 FMAs, `iters` steps); *flops receives the
+ * floating-point operations of the launch, to be divided by its event time.
+ * The denominator of the ALU roofline of the ROI cross-correlation. */
+int hrebsd_probe_fp32_fma(hrebsd_ctx *ctx, int iters, double *flops, void *stream);
+
 /* f1 -- strain and stress of each pair (Eq. 13-16; Supplementary Part 2).
  * F [B][9]: detector-frame deformation gradients (e.g. from hrebsd_solve_F).
  * F_S = T F T^T with the tilt rotation T = [[c, s, 0], [-s, c, 0], [0, 0, 1]]

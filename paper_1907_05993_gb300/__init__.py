@@ -21,7 +21,7 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -100,6 +100,7 @@ def load(build: bool = False):
         "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
         "hrebsd_field_resample": (i, [vp, vp, i, i, i, vp, i, i, vp]),
         "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
+        "hrebsd_probe_fp32_fma": (i, [vp, i, C.POINTER(C.c_double), vp]),
         "hrebsd_set_tile_variant": (i, [vp, i, i, i]),
         "hrebsd_get_tile_variant": (i, [vp, i, i]),
         "hrebsd_strain_stress": (i, [vp, vp, vp, vp, i, i, C.c_double, C.c_double, C.c_double, C.c_double, i, vp,
@@ -268,6 +269,13 @@ def hrebsd_autotune(ctx, B, H, W, params, stream=None):
     ms = (C.c_float * (params.levels * TILE_VARIANTS))()
     _chk(load().hrebsd_autotune(ctx, B, H, W, C.byref(params), ms, _s(stream)), "hrebsd_autotune")
     return np.array(ms[:], dtype=np.float32).reshape(params.levels, TILE_VARIANTS)
+
+
+def hrebsd_probe_fp32_fma(ctx, iters, stream=None):
+    """Launch the FP32 FMA probe; returns the floating-point operations of the launch."""
+    f = C.c_double()
+    _chk(load().hrebsd_probe_fp32_fma(ctx, iters, C.byref(f), _s(stream)), "hrebsd_probe_fp32_fma")
+    return f.value
 
 
 def hrebsd_set_tile_variant(ctx, h, w, variant):

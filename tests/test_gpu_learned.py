@@ -75,3 +75,37 @@ def test_learned_start_reaches_plain_rotation(trained):
           np.median(err_p), np.median(err_l), "iterations plain/learned", it_p.mean(), it_l.mean())
     assert np.median(err_l) <= 1.5 * np.median(err_p) + 1e-4
     pipe.close()
+
+
+def test_training_targets_spot_checked_against_oracle(oracle):
+    """Training targets (the final field of the full registration, box-averaged to 64x64 in
+    64x64-pixel units) from the library path, against the oracle's registration of the same
+    numpy-rendered training pairs replayed with the library's per-level iteration counts."""
+    import torch
+    import paper_1907_05993_gb300 as P
+    spec = K.config4(200_000)
+    pairs = [3, 70_001, 150_007]
+    ctx = P.hrebsd_create(0)
+    prm = P.demons_params(3, [100] * 3, 1.0, 1.0, 1.0, 1e-4, 5)
+    for p in pairs:
+        ref = K.render_ref(spec, K.ref_index(spec, p))
+        test = K.render_test(spec, p)
+        r_d, t_d = torch.from_numpy(ref[None]).cuda(), torch.from_numpy(test[None]).cuda()
+        P.hrebsd_preprocess_batch(ctx, r_d, 1, 128, 128, 1, r_d)
+        P.hrebsd_preprocess_batch(ctx, t_d, 1, 128, 128, 1, t_d)
+        field = torch.empty((1, 2, 128, 128), device="cuda")
+        iters = torch.empty((1, 3), dtype=torch.int32, device="cuda")
+        status = torch.empty((1,), dtype=torch.int32, device="cuda")
+        P.hrebsd_demons_register_batch(ctx, r_d, t_d, torch.zeros(1, dtype=torch.int32, device="cuda"), 1, 1, 128,
+                                       128, prm, None, field, iters, status)
+        target = torch.empty((1, 2, 64, 64), device="cuda")
+        P.hrebsd_field_resample(ctx, field, 1, 128, 128, target, 64, 64)
+        torch.cuda.synchronize()
+        it = iters.cpu().numpy()[0]
+        pr = oracle.preprocess(ref.astype(np.float64), True)
+        pt = oracle.preprocess(test.astype(np.float64), True)
+        fo, _ = oracle.demons_register(pr, pt, 3, [100] * 3, 1.0, 1.0, 1.0, 5, 1e-4, replay=it)
+        exp = np.stack([oracle.reduce2(fo[c]) / 2 for c in range(2)])
+        d = np.abs(target.cpu().numpy()[0] - exp)
+        assert np.mean(d <= 1e-3) >= 0.99 and d.max() <= 0.05, (p, d.max(), np.mean(d <= 1e-3))
+    P.hrebsd_destroy(ctx)
