@@ -269,6 +269,38 @@ int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N
                    const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
                    void *stream);
 
+/* f3 -- comparison methods and quality measures (Section 3.1, Fig. 2-3).
+ * The four rotation measurements of Fig. 2 compose the calls above:
+ * (a) hrebsd_xcf_roi_batch on the un-remapped reference + hrebsd_solve_F with
+ * R_finite = NULL; (b) F_first of hrebsd_fit_rotation; (c) (a), then
+ * hrebsd_polar_batch, hrebsd_remap by that rotation, hrebsd_xcf_roi_batch,
+ * hrebsd_solve_F; (d) the method of the paper (a1-a8).
+ *
+ * hrebsd_polar_batch: R [B][9] = rotation part of each F [B][9] (Eq. 4-5).
+ *
+ * hrebsd_fit_quality: per pair, MAE = the mean over the N ROIs of the angle
+ * (rad) between the measured test direction (r' - PC, Z*) and the direction
+ * F_m (r - PC, Z*) predicted by the fitted model, F_m = F R^T when R is given
+ * (a second-pass F of Eq. 12 with its R_finite), else F.  Point pairs from XCF
+ * shifts q [B][N][2] (r = c, r' = c + q) or from a demons field [B][2][H][W]
+ * (r = c - u(c), r' = c); exactly one of q and field is non-null.  ph [B][N]
+ * (nullable) gives ph_mean [B] = mean peak height (PH of Fig. 3).  Outputs
+ * mae [B], ph_mean [B] (nullable) FP64.  EINVAL for bad arguments. */
+int hrebsd_polar_batch(hrebsd_ctx *ctx, const double *F, int B, double *R, void *stream);
+int hrebsd_fit_quality(hrebsd_ctx *ctx, const double *F, const double *R, const float *q, const float *field,
+                       const float *ph, int B, int H, int W, const int32_t *roi_xy, int N, const hrebsd_geometry *g,
+                       double *mae, double *ph_mean, void *stream);
+
+/* SSIM of Fig. 3 (the quality measure of the demons-only method): mean SSIM
+ * between the warped reference M(x - u(x)) (ref[ref_idx[b]], clamped bilinear as
+ * in the registration; field NULL = no warp) and test[b], 11 x 11 Gaussian
+ * window of sigma 1.5, C1 = (0.01 L)^2, C2 = (0.03 L)^2, L = max - min of the
+ * test pattern, over the window centres whose window lies inside the image.
+ * ref [R][H][W], test [B][H][W], field [B][2][H][W]; ref_idx may be NULL
+ * (all pairs use ref[0]).  Output ssim [B] FP64.  H, W >= 11. */
+int hrebsd_ssim_warped(hrebsd_ctx *ctx, const float *ref, const int32_t *ref_idx, const float *test,
+                       const float *field, int B, int H, int W, double *ssim, void *stream);
+
 /* Measurement helper (no counterpart in the paper): launch an FP32 FMA
  * throughput probe on `stream` (SMs x 8 CTAs of 256 threads, each thread 8
  * independent chains of packed FP32x2 FMAs, `iters` steps); *flops receives the

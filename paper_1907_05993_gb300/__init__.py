@@ -21,7 +21,7 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_fit_quality", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -101,6 +101,9 @@ def load(build: bool = False):
         "hrebsd_field_resample": (i, [vp, vp, i, i, i, vp, i, i, vp]),
         "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
         "hrebsd_probe_fp32_fma": (i, [vp, i, C.POINTER(C.c_double), vp]),
+        "hrebsd_polar_batch": (i, [vp, vp, i, vp, vp]),
+        "hrebsd_fit_quality": (i, [vp, vp, vp, vp, vp, vp, i, i, i, vp, i, C.POINTER(hrebsd_geometry), vp, vp, vp]),
+        "hrebsd_ssim_warped": (i, [vp, vp, vp, vp, vp, i, i, i, vp, vp]),
         "hrebsd_set_tile_variant": (i, [vp, i, i, i]),
         "hrebsd_get_tile_variant": (i, [vp, i, i]),
         "hrebsd_strain_stress": (i, [vp, vp, vp, vp, i, i, C.c_double, C.c_double, C.c_double, C.c_double, i, vp,
@@ -269,6 +272,25 @@ def hrebsd_autotune(ctx, B, H, W, params, stream=None):
     ms = (C.c_float * (params.levels * TILE_VARIANTS))()
     _chk(load().hrebsd_autotune(ctx, B, H, W, C.byref(params), ms, _s(stream)), "hrebsd_autotune")
     return np.array(ms[:], dtype=np.float32).reshape(params.levels, TILE_VARIANTS)
+
+
+def hrebsd_polar_batch(ctx, F, B, R, stream=None):
+    t = _t()
+    _chk(load().hrebsd_polar_batch(ctx, _p(F, t.float64), B, _p(R, t.float64), _s(stream)), "hrebsd_polar_batch")
+
+
+def hrebsd_fit_quality(ctx, F, R, q, field, ph, B, H, W, roi_xy, N, geom, mae, ph_mean=None, stream=None):
+    t = _t()
+    _chk(load().hrebsd_fit_quality(ctx, _p(F, t.float64), _p(R, t.float64), _p(q, t.float32), _p(field, t.float32),
+                                   _p(ph, t.float32), B, H, W, _p(roi_xy, t.int32), N, C.byref(geom),
+                                   _p(mae, t.float64), _p(ph_mean, t.float64), _s(stream)), "hrebsd_fit_quality")
+
+
+def hrebsd_ssim_warped(ctx, ref, ref_idx, test, field, B, H, W, ssim, stream=None):
+    t = _t()
+    _chk(load().hrebsd_ssim_warped(ctx, _p(ref, t.float32), _p(ref_idx, t.int32), _p(test, t.float32),
+                                   _p(field, t.float32), B, H, W, _p(ssim, t.float64), _s(stream)),
+         "hrebsd_ssim_warped")
 
 
 def hrebsd_probe_fp32_fma(ctx, iters, stream=None):

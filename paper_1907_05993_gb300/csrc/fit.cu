@@ -252,6 +252,69 @@ __global__ void solve_F_kernel(const float *__restrict__ q, const int32_t *__res
     for (int k = 0; k < 9; ++k) Fout[(size_t)b * 9 + k] = F[k];
 }
 
+// Rotation part of arbitrary F (Eq. 4-5), one thread per pair.
+__global__ void polar_kernel(const double *__restrict__ F, int B, double *R)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double Fb[9], Rb[9];
+    for (int k = 0; k < 9; ++k) Fb[k] = F[(size_t)b * 9 + k];
+    polar_newton(Fb, Rb);
+    for (int k = 0; k < 9; ++k) R[(size_t)b * 9 + k] = Rb[k];
+}
+
+// Quality of an Eq. 3 fit (Section 3.1, Fig. 3).  Point pairs: from the XCF
+// shifts (r = c, r' = c + q) or from the demons field (r = c - u(c), r' = c).
+// Model F_m = F R^T when R is given (the second pass, Eq. 12), else F.
+// MAE = mean over ROIs of the angle between the measured test direction
+// (r' - PC, Z*) and F_m (r - PC, Z*); PH = mean of the peak heights.
+__global__ void fit_quality_kernel(const double *__restrict__ F, const double *__restrict__ R,
+                                   const float *__restrict__ q, const float *__restrict__ field,
+                                   const float *__restrict__ ph, int B, int H, int W, const int32_t *__restrict__ roi,
+                                   int N, double xpc, double ypc, double zs, double *mae, double *ph_mean)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double Fm[9];
+    const double *Fb = F + (size_t)b * 9;
+    if (R) {
+        const double *Rb = R + (size_t)b * 9;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                Fm[i * 3 + j] = Fb[i * 3] * Rb[j * 3] + Fb[i * 3 + 1] * Rb[j * 3 + 1] + Fb[i * 3 + 2] * Rb[j * 3 + 2];
+    } else {
+        for (int k = 0; k < 9; ++k) Fm[k] = Fb[k];
+    }
+    const float *fx = field ? field + (size_t)b * 2 * H * W : nullptr;
+    double sum = 0.0, phs = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double cx = roi[2 * i], cy = roi[2 * i + 1];
+        double r[2], rp[2];
+        if (q) {
+            r[0] = cx;
+            r[1] = cy;
+            rp[0] = cx + (double)q[((size_t)b * N + i) * 2];
+            rp[1] = cy + (double)q[((size_t)b * N + i) * 2 + 1];
+        } else {
+            const float ux = bilinear_clamped(fx, H, W, (float)(cx - 0.5), (float)(cy - 0.5));
+            const float uy = bilinear_clamped(fx + (size_t)H * W, H, W, (float)(cx - 0.5), (float)(cy - 0.5));
+            r[0] = cx - (double)ux;
+            r[1] = cy - (double)uy;
+            rp[0] = cx;
+            rp[1] = cy;
+        }
+        const double v[3] = {r[0] - xpc, r[1] - ypc, zs};
+        double p[3];
+        for (int a = 0; a < 3; ++a) p[a] = Fm[a * 3] * v[0] + Fm[a * 3 + 1] * v[1] + Fm[a * 3 + 2] * v[2];
+        const double m[3] = {rp[0] - xpc, rp[1] - ypc, zs};
+        const double cr[3] = {p[1] * m[2] - p[2] * m[1], p[2] * m[0] - p[0] * m[2], p[0] * m[1] - p[1] * m[0]};
+        sum += atan2(sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]), p[0] * m[0] + p[1] * m[1] + p[2] * m[2]);
+        if (ph) phs += (double)ph[(size_t)b * N + i];
+    }
+    mae[b] = sum / N;
+    if (ph_mean) ph_mean[b] = ph ? phs / N : 0.0;
+}
+
 }  // namespace
 
 extern "C" int hrebsd_fit_rotation(hrebsd_ctx *ctx, const float *field, int B, int H, int W, const int32_t *roi_xy,
@@ -284,6 +347,38 @@ extern "C" int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *ro
     hr_prof_begin(ctx, hr_stream(stream));
     solve_F_kernel<<<(B + 63) / 64, 64, 0, hr_stream(stream)>>>(q, roi_xy, N, B, g->xstar * W, g->ystar * H,
                                                                 g->zstar * W, R_finite, F, pair_status);
+    hr_prof_end(ctx, PROF_SOLVE, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_polar_batch(hrebsd_ctx *ctx, const double *F, int B, double *R, void *stream)
+{
+    if (!ctx || B < 0) return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!F || !R) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    hr_prof_begin(ctx, hr_stream(stream));
+    polar_kernel<<<(B + 63) / 64, 64, 0, hr_stream(stream)>>>(F, B, R);
+    hr_prof_end(ctx, PROF_FIT, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_fit_quality(hrebsd_ctx *ctx, const double *F, const double *R, const float *q, const float *field,
+                                  const float *ph, int B, int H, int W, const int32_t *roi_xy, int N,
+                                  const hrebsd_geometry *g, double *mae, double *ph_mean, void *stream)
+{
+    if (!ctx || !g || B < 0 || H < 2 || W < 2 || N < 1 || N > kMaxRoi) return HREBSD_EINVAL;
+    if (B == 0) return HREBSD_OK;
+    if (!F || !roi_xy || !mae || (!q) == (!field)) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    hr_prof_begin(ctx, hr_stream(stream));
+    fit_quality_kernel<<<(B + 63) / 64, 64, 0, hr_stream(stream)>>>(F, R, q, field, ph, B, H, W, roi_xy, N,
+                                                                    g->xstar * W, g->ystar * H, g->zstar * W, mae,
+                                                                    ph_mean);
     hr_prof_end(ctx, PROF_SOLVE, hr_stream(stream));
     HR_LAUNCHED(ctx);
     return HREBSD_OK;

@@ -12,7 +12,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (demons_params, hrebsd_autotune, hrebsd_cnn_infer_patterns, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
+from . import (demons_params, hrebsd_autotune, hrebsd_cnn_infer_patterns, hrebsd_fit_quality, hrebsd_polar_batch,
+               hrebsd_ssim_warped, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
                hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
                hrebsd_field_resample, hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
 
@@ -145,3 +146,53 @@ class Pipeline:
         hrebsd_strain_stress(self.ctx, F, ref_idx, g, g.shape[0], B, tilt_rad, stiffness, traction_free, out["F_S"],
                              out["eps"], out["sigma"], stream)
         return out
+
+    def compare(self, refs_raw, tests_raw, ref_idx, stream=None, out=None):
+        """The four rotation measurements of Fig. 2 and the quality measures of Fig. 3 (Section 3.1).
+
+        Runs the method of the paper (d) through ``run`` and adds: (a) XCF without remapping
+        (the per-pair reference obtained by hrebsd_remap with identity rotations), (b) the demons
+        fit alone (F_first), (c) remapping by polar((a)) then the second pass.  Per method m in
+        a, b, c, d: F_m [B, 9], mae_m [B] (rad); ph_a, ph_c, ph_d [B]; ssim_b [B] of the warped
+        reference and ssim_none [B] without warp.  Every step is a library call."""
+        t = self.torch
+        c = self.cfg
+        o = self.run(refs_raw, tests_raw, ref_idx, stream=stream, out=out)
+        B, H, W, N = tests_raw.shape[0], c.H, c.W, self.N
+
+        def get(name, shape, dtype):
+            if name not in o:
+                o[name] = self._buf(name, shape, dtype)
+            return o[name]
+        eye = get("R_identity", (B, 9), t.float64)
+        eye.copy_(t.eye(3, dtype=t.float64, device=self.dev).reshape(1, 9).expand(B, 9))
+        ref_i = get("ref_per_pair", (B, H, W), t.float32)
+        hrebsd_remap(self.ctx, o["ref_pre"], ref_idx, eye, B, H, W, self.geom, ref_i, stream)
+        q_a, pk_a = get("q_a", (B, N, 2), t.float32), get("peak_a", (B, N, 2), t.int32)
+        ph_a, tie_a = get("ph_a", (B, N), t.float32), get("near_tie_a", (B, N), t.int32)
+        hrebsd_xcf_roi_batch(self.ctx, ref_i, o["test_pre"], B, H, W, self.roi, N, c.S, c.window, q_a, pk_a, ph_a,
+                             tie_a, stream)
+        st_a = get("status_a", (B,), t.int32)
+        st_a.zero_()
+        F_a = get("F_a", (B, 9), t.float64)
+        hrebsd_solve_F(self.ctx, q_a, self.roi, N, B, H, W, self.geom, None, F_a, st_a, stream)
+        R_a = get("R_a", (B, 9), t.float64)
+        hrebsd_polar_batch(self.ctx, F_a, B, R_a, stream)
+        rem_c = get("remapped_c", (B, H, W), t.float32)
+        hrebsd_remap(self.ctx, o["ref_pre"], ref_idx, R_a, B, H, W, self.geom, rem_c, stream)
+        q_c, pk_c = get("q_c", (B, N, 2), t.float32), get("peak_c", (B, N, 2), t.int32)
+        ph_c, tie_c = get("ph_c", (B, N), t.float32), get("near_tie_c", (B, N), t.int32)
+        hrebsd_xcf_roi_batch(self.ctx, rem_c, o["test_pre"], B, H, W, self.roi, N, c.S, c.window, q_c, pk_c, ph_c,
+                             tie_c, stream)
+        F_c = get("F_c", (B, 9), t.float64)
+        hrebsd_solve_F(self.ctx, q_c, self.roi, N, B, H, W, self.geom, R_a, F_c, st_a, stream)
+        o["F_b"], o["F_d"] = o["F_first"], o["F"]
+        for m, F, R, q, field, ph in (("a", F_a, None, q_a, None, ph_a), ("b", o["F_first"], None, None, o["field"], None),
+                                      ("c", F_c, R_a, q_c, None, ph_c), ("d", o["F"], o["R_finite"], o["q"], None, o["ph"])):
+            mae = get(f"mae_{m}", (B,), t.float64)
+            phm = get(f"phm_{m}", (B,), t.float64) if ph is not None else None
+            hrebsd_fit_quality(self.ctx, F, R, q, field, ph, B, H, W, self.roi, N, self.geom, mae, phm, stream)
+        for name, field in (("ssim_b", o["field"]), ("ssim_none", None)):
+            hrebsd_ssim_warped(self.ctx, o["ref_pre"], ref_idx, o["test_pre"], field, B, H, W,
+                               get(name, (B,), t.float64), stream)
+        return o
