@@ -269,6 +269,34 @@ int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N
                    const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
                    void *stream);
 
+/* f2 -- pattern preprocessing for real scans (Section 3.2-3.3).  The paper
+ * names the steps without kernels; the readings (FP32, replicated borders):
+ * Gaussian filters of radius ceil(3 sigma) (at most 96, i.e. sigma <= 32) with
+ * weights exp(-k^2 / 2 sigma^2) normalised to one, x pass then y pass.
+ * Arrays [n][H][W] FP32 on the device; in and out may alias except for
+ * hrebsd_shift_zoom_batch.  EINVAL for bad sizes, sigmas or pointers.
+ *
+ * hrebsd_bandpass_batch: out = LP(in) - G_hp * in, LP(in) = G_lp * in
+ * (sigma_lp = 0: LP = identity; sigma_hp = 0: no high-pass term), the
+ * low-pass / high-pass pair applied before the demons registration.
+ * hrebsd_mean_pattern: out [H][W] = mean of the n patterns (the static
+ * background of a scan).
+ * hrebsd_background_batch: static correction out = in / static_bg (nullable,
+ * [H][W]) then dynamic correction out = out / (G_dyn * out) (sigma_dyn = 0:
+ * none); a divisor below 1e-12 in magnitude gives 0.
+ * hrebsd_shift_zoom_batch: out(x) = in(pc + (x - pc - t) / s) in index
+ * coordinates, pc = (xstar W - 0.5, ystar H - 0.5), t = shift[b] (pixels,
+ * nullable: 0), s = zoom[b] (nullable: 1), Keys cubic (a = -0.5): the pattern
+ * shift correction (beam-position shift moved to the detector frame) and the
+ * zoom/shrink by the ratio of detector distances. */
+int hrebsd_bandpass_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, float sigma_lp, float sigma_hp,
+                          float *out, void *stream);
+int hrebsd_mean_pattern(hrebsd_ctx *ctx, const float *in, int n, int H, int W, float *out, void *stream);
+int hrebsd_background_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, const float *static_bg,
+                            float sigma_dyn, float *out, void *stream);
+int hrebsd_shift_zoom_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, const float *shift,
+                            const float *zoom, const hrebsd_geometry *g, float *out, void *stream);
+
 /* f3 -- comparison methods and quality measures (Section 3.1, Fig. 2-3).
  * The four rotation measurements of Fig. 2 compose the calls above:
  * (a) hrebsd_xcf_roi_batch on the un-remapped reference + hrebsd_solve_F with

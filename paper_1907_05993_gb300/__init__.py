@@ -21,7 +21,8 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_fit_quality", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
+    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
+    "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
@@ -102,6 +103,10 @@ def load(build: bool = False):
         "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
         "hrebsd_probe_fp32_fma": (i, [vp, i, C.POINTER(C.c_double), vp]),
         "hrebsd_polar_batch": (i, [vp, vp, i, vp, vp]),
+        "hrebsd_bandpass_batch": (i, [vp, vp, i, i, i, C.c_float, C.c_float, vp, vp]),
+        "hrebsd_mean_pattern": (i, [vp, vp, i, i, i, vp, vp]),
+        "hrebsd_background_batch": (i, [vp, vp, i, i, i, vp, C.c_float, vp, vp]),
+        "hrebsd_shift_zoom_batch": (i, [vp, vp, i, i, i, vp, vp, C.POINTER(hrebsd_geometry), vp, vp]),
         "hrebsd_fit_quality": (i, [vp, vp, vp, vp, vp, vp, i, i, i, vp, i, C.POINTER(hrebsd_geometry), vp, vp, vp]),
         "hrebsd_ssim_warped": (i, [vp, vp, vp, vp, vp, i, i, i, vp, vp]),
         "hrebsd_set_tile_variant": (i, [vp, i, i, i]),
@@ -272,6 +277,29 @@ def hrebsd_autotune(ctx, B, H, W, params, stream=None):
     ms = (C.c_float * (params.levels * TILE_VARIANTS))()
     _chk(load().hrebsd_autotune(ctx, B, H, W, C.byref(params), ms, _s(stream)), "hrebsd_autotune")
     return np.array(ms[:], dtype=np.float32).reshape(params.levels, TILE_VARIANTS)
+
+
+def hrebsd_bandpass_batch(ctx, inp, n, H, W, sigma_lp, sigma_hp, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_bandpass_batch(ctx, _p(inp, f32), n, H, W, float(sigma_lp), float(sigma_hp), _p(out, f32),
+                                      _s(stream)), "hrebsd_bandpass_batch")
+
+
+def hrebsd_mean_pattern(ctx, inp, n, H, W, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_mean_pattern(ctx, _p(inp, f32), n, H, W, _p(out, f32), _s(stream)), "hrebsd_mean_pattern")
+
+
+def hrebsd_background_batch(ctx, inp, n, H, W, static_bg, sigma_dyn, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_background_batch(ctx, _p(inp, f32), n, H, W, _p(static_bg, f32), float(sigma_dyn),
+                                        _p(out, f32), _s(stream)), "hrebsd_background_batch")
+
+
+def hrebsd_shift_zoom_batch(ctx, inp, n, H, W, shift, zoom, geom, out, stream=None):
+    f32 = _t().float32
+    _chk(load().hrebsd_shift_zoom_batch(ctx, _p(inp, f32), n, H, W, _p(shift, f32), _p(zoom, f32), C.byref(geom),
+                                        _p(out, f32), _s(stream)), "hrebsd_shift_zoom_batch")
 
 
 def hrebsd_polar_batch(ctx, F, B, R, stream=None):

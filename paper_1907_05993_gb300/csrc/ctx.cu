@@ -22,7 +22,7 @@ int hr_set_device(hrebsd_ctx *ctx)
 
 int hr_ws(hrebsd_ctx *ctx, int slot, size_t bytes, void **out)
 {
-    if (slot < 0 || slot >= 16) return HREBSD_EINVAL;
+    if (slot < 0 || slot >= (int)(sizeof(ctx->ws) / sizeof(ctx->ws[0]))) return HREBSD_EINVAL;
     hr_buf &b = ctx->ws[slot];
     if (b.bytes < bytes) {
         if (b.ptr) {

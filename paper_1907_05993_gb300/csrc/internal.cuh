@@ -61,7 +61,7 @@ struct hrebsd_ctx {
     int device = 0;
     int num_sms = 0;
     long long launches = 0;
-    hr_buf ws[16];   // named workspace slots (see demons.cu)
+    hr_buf ws[24];   // named workspace slots (demons.cu 0-13, metrics.cu 14, probe.cu 15, filters.cu 16-18)
     // tracing
     int prof_on = 0;
     int no_events = 0;   // set while a call must not create CUDA events

@@ -12,7 +12,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (demons_params, hrebsd_autotune, hrebsd_cnn_infer_patterns, hrebsd_fit_quality, hrebsd_polar_batch,
+from . import (demons_params, hrebsd_autotune, hrebsd_background_batch, hrebsd_bandpass_batch, hrebsd_mean_pattern, hrebsd_cnn_infer_patterns, hrebsd_fit_quality, hrebsd_polar_batch,
                hrebsd_ssim_warped, hrebsd_create, hrebsd_demons_register_batch, hrebsd_destroy,
                hrebsd_fit_rotation, hrebsd_geometry, hrebsd_preprocess_batch, hrebsd_remap, hrebsd_solve_F,
                hrebsd_field_resample, hrebsd_strain_stress, hrebsd_xcf_roi_batch, NI_STIFFNESS)
@@ -36,6 +36,11 @@ class PipelineConfig:
     flat: bool = True
     window: bool = True
     autotune: bool = True       # pick the demons tile shape per level on the first batch of a size
+    # preprocessing for real scans (Section 3.2-3.3), off by default: static background = the
+    # batch's mean test pattern, dynamic background blur sigma, band-pass (sigma_lp, sigma_hp)
+    static_background: bool = False
+    dynamic_background: float = 0.0
+    bandpass: tuple = (0.0, 0.0)
 
 
 class Pipeline:
@@ -99,8 +104,20 @@ class Pipeline:
         test_p = get("test_pre", (B, H, W), t.float32)
         if c.autotune and (B, H, W) not in self._tuned:
             self._tuned[(B, H, W)] = hrebsd_autotune(self.ctx, B, H, W, self.params, stream)
-        hrebsd_preprocess_batch(self.ctx, refs_raw, R, H, W, c.flat, ref_p, stream)
-        hrebsd_preprocess_batch(self.ctx, tests_raw, B, H, W, c.flat, test_p, stream)
+        src_r, src_t = refs_raw, tests_raw
+        if c.static_background or c.dynamic_background > 0 or c.bandpass[0] > 0 or c.bandpass[1] > 0:
+            src_r, src_t = get("ref_filtered", (R, H, W), t.float32), get("test_filtered", (B, H, W), t.float32)
+            bg = None
+            if c.static_background:
+                bg = get("static_background", (H, W), t.float32)
+                hrebsd_mean_pattern(self.ctx, tests_raw, B, H, W, bg, stream)
+            hrebsd_background_batch(self.ctx, refs_raw, R, H, W, bg, c.dynamic_background, src_r, stream)
+            hrebsd_background_batch(self.ctx, tests_raw, B, H, W, bg, c.dynamic_background, src_t, stream)
+            if c.bandpass[0] > 0 or c.bandpass[1] > 0:
+                hrebsd_bandpass_batch(self.ctx, src_r, R, H, W, c.bandpass[0], c.bandpass[1], src_r, stream)
+                hrebsd_bandpass_batch(self.ctx, src_t, B, H, W, c.bandpass[0], c.bandpass[1], src_t, stream)
+        hrebsd_preprocess_batch(self.ctx, src_r, R, H, W, c.flat, ref_p, stream)
+        hrebsd_preprocess_batch(self.ctx, src_t, B, H, W, c.flat, test_p, stream)
         field = get("field", (B, 2, H, W), t.float32)
         iters = get("iters", (B, L), t.int32)
         status = get("status", (B,), t.int32)
