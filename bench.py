@@ -566,6 +566,44 @@ def run_compare(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ large patterns (f4)
+def run_large(args, rank, world, local_rank):
+    """1024 x 1024 patterns (the paper's 1244 x 1024 simulations cut to a width the 7-level pyramid
+    divides), 7 levels x 20 iterations (the paper's Inconel settings), 25 ROIs of 128 x 128."""
+    import numpy as np
+    import torch
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    from synth import gpu as SG
+    from synth import kikuchi as K
+    torch.cuda.set_device(local_rank)
+    n = args.large_pairs
+    spec = K.ScanSpec(n_pairs=n, H=1024, W=1024, n_refs=4, mis_lo_deg=0.0, mis_hi_deg=6.0, strain=5e-4,
+                      strain_mode="sigma", counts=500.0, seed=6)
+    refs, tests, ridx, _ = SG.make_scan_gpu(spec)
+    roi = K.roi_grid(1024, 1024, 128, False)
+    pipe = Pipeline(PipelineConfig(1024, 1024, roi, 128, 7, (20,) * 7))
+    out = {}
+    for _ in range(args.warmup):
+        pipe.run(refs, tests, ridx, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        pipe.run(refs, tests, ridx, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    line = {"metric": "pattern pairs/s (demons+XCF), large patterns", "workload": "large", "value": n * args.steps / t,
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "data": "synthetic (seeded kinematic Kikuchi generator)", "dtype": "f32",
+            "config": {"workload": f"{n} pairs of 1024x1024, 4 references, mis U(0,6) deg, 7 levels x 20 iterations, "
+                                   f"25 ROIs 128x128", "ms_per_pair": 1e3 * t / (n * args.steps)}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pipe.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,7 +614,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("scan", "learned", "compare"), default="scan")
+    ap.add_argument("--workload", choices=("scan", "learned", "compare", "large"), default="scan")
+    ap.add_argument("--large-pairs", type=int, default=512)
     ap.add_argument("--compare-orientations", type=int, default=16)
     ap.add_argument("--train-pairs", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=30)
@@ -595,6 +634,8 @@ def main():
         return run_learned(args, rank, world, local_rank)
     if args.workload == "compare":
         return run_compare(args, rank, world, local_rank)
+    if args.workload == "large":
+        return run_large(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -87,8 +87,10 @@ def test_shift_zoom_parity(env):
 
 
 def test_pipeline_with_real_scan_preprocessing(env, oracle):
-    """Static + dynamic background correction and band-pass ahead of the method: the filtered
-    patterns match the oracle's filters and the rotation is still recovered."""
+    """Dynamic background correction and band-pass ahead of the method: the filtered patterns
+    match the oracle's filters and the rotation is still recovered.  (A static background is the
+    mean over a whole scan of many orientations; over a few similar patterns it keeps their bands,
+    so this end-to-end check leaves it out; its arithmetic is checked above.)"""
     torch, P, ctx = env
     import math
     from oracle import filters as FL
@@ -97,13 +99,11 @@ def test_pipeline_with_real_scan_preprocessing(env, oracle):
                       counts=500.0, seed=21)
     refs, tests, ridx, Ft = K.make_scan(spec)
     roi = K.roi_grid(128, 128, 32, True)
-    cfg = PipelineConfig(128, 128, roi, 32, 3, (50, 50, 50), static_background=True, dynamic_background=12.0,
-                         bandpass=(0.7, 0.0))
+    cfg = PipelineConfig(128, 128, roi, 32, 3, (50, 50, 50), dynamic_background=12.0, bandpass=(0.7, 0.0))
     pipe = Pipeline(cfg)
     o = pipe.run(torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(), torch.from_numpy(ridx).cuda())
     torch.cuda.synchronize()
-    bg = FL.mean_pattern(tests.astype(np.float64))
-    exp = FL.bandpass(FL.background(tests[1].astype(np.float64), bg, 12.0), 0.7, 0.0)
+    exp = FL.bandpass(FL.background(tests[1].astype(np.float64), None, 12.0), 0.7, 0.0)
     got = o["test_filtered"].cpu().numpy()[1]
     assert np.abs(got - exp).max() <= 1e-4 * np.abs(exp).max()
     Fg = o["F"].cpu().numpy().reshape(-1, 3, 3)
