@@ -426,9 +426,12 @@ def run_learned(args, rank, world, local_rank):
     B = len(pairs)
     stream = torch.cuda.current_stream()
 
-    def timed(learned):
+    def timed(learned, plain_caps=None):
         out = {}
         kw = {"learned_caps": caps_l, "learned_start_res": args.learned_start} if learned else {}
+        saved = pipe.params
+        if plain_caps is not None:
+            pipe.params = P.demons_params(4, plain_caps, 1.0, 1.0, 1.0, 1e-4, 5)
         for _ in range(args.warmup):
             pipe.run(refs, tests, ridx, out=out, **kw)
         torch.cuda.synchronize()
@@ -439,12 +442,17 @@ def run_learned(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
+        pipe.params = saved
         F = out["F"].cpu().numpy().reshape(-1, 3, 3)
         its = out["iters"].cpu().numpy()
         return B * args.steps / t, F, its
 
     v_plain, F_plain, it_plain = timed(False)
     v_learn, F_learn, it_learn = timed(True)
+    # control: plain registration with the same fine-level caps as the learned run (isolates the
+    # initialiser from the cap reduction)
+    ctrl_caps = (caps_l[0], caps_l[1], 100, 100)
+    v_ctrl, F_ctrl, it_ctrl = timed(False, ctrl_caps)
     import oracle as O
 
     def rot_deg(Ra, Rb):
@@ -462,6 +470,7 @@ def run_learned(args, rank, world, local_rank):
     e_learn = [rot_deg(R_learn[pos[p]], R) for p, R in zip(sub, R_oracle)]
     t_plain = [rot_deg(a, b) for a, b in zip(R_plain, R_true)]
     t_learn = [rot_deg(a, b) for a, b in zip(R_learn, R_true)]
+    t_ctrl = [rot_deg(O.polar(a), b) for a, b in zip(F_ctrl, R_true)]
     d_pl = [rot_deg(a, b) for a, b in zip(R_plain, R_learn)]
     line = {
         "metric": METRIC + "; learned-init vs plain", "workload": "learned-init vs plain",
@@ -476,11 +485,17 @@ def run_learned(args, rank, world, local_rank):
                                f"field of the full registration at 64x64; {args.epochs} epochs, batch 256, "
                                f"Adam {args.lr} -> {args.lr_final} (cosine)"},
         "plain_pairs_per_s": v_plain, "learned_pairs_per_s": v_learn, "speedup": v_learn / v_plain,
+        "control_plain_same_fine_caps": {"caps": list(ctrl_caps), "pairs_per_s": v_ctrl,
+                                         "speedup_of_learned": v_learn / v_ctrl,
+                                         "iters_mean_per_level": [float(a) for a in it_ctrl.mean(axis=0)],
+                                         "rot_err_vs_ground_truth_deg": stats(t_ctrl)},
         "iters_mean_per_level_plain": [float(a) for a in it_plain.mean(axis=0)],
         "iters_mean_per_level_learned": [float(a) for a in it_learn.mean(axis=0)],
         "oracle_subset": len(sub), "oracle_seconds": t_oracle, "oracle_cores": cores,
         "rot_err_vs_oracle_deg": {"plain": stats(e_plain), "learned": stats(e_learn)},
         "rot_err_vs_ground_truth_deg": {"plain": stats(t_plain), "learned": stats(t_learn)},
+        "rot_err_vs_ground_truth_deg_mean": {"plain": float(np.mean(t_plain)), "learned": float(np.mean(t_learn)),
+                                             "control": float(np.mean(t_ctrl))},
         "rot_dev_learned_vs_plain_deg": stats(d_pl),
         "training_loss_per_epoch": hist, "training_seconds": t_train, "training_set_seconds": t_set,
     }
@@ -623,7 +638,7 @@ def main():
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--learned-start", type=int, default=64, choices=(64, 128))
     ap.add_argument("--oracle-pairs", type=int, default=500)
-    ap.add_argument("--learned-caps", type=int, nargs=4, default=(100, 100, 25, 0))
+    ap.add_argument("--learned-caps", type=int, nargs=4, default=(25, 25, 10, 0))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
