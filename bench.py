@@ -302,6 +302,12 @@ def run_ours(args, rank, world, local_rank):
     h_R = torch.empty((B, 9), dtype=torch.float64).pin_memory()
     h_st = torch.empty((B,), dtype=torch.int32).pin_memory()
     e_steps = max(1, min(args.steps, 3))
+    # one untimed pass through the host-buffer path (its device buffers are new, so the per-level
+    # graphs are captured here, as in any warm-up)
+    d_tests.copy_(h_tests, non_blocking=True)
+    d_refs.copy_(h_refs, non_blocking=True)
+    d_ridx.copy_(h_ridx, non_blocking=True)
+    pipe.run(d_refs, d_tests, d_ridx, out=out)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
