@@ -587,6 +587,48 @@ def run_compare(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ single pair (latency)
+def run_single(args, rank, world, local_rank):
+    """The single-pair workload (128x128, 3 levels x 50 iterations, 21 ROIs 32x32): latency of one
+    pair through the whole chain, with the per-level CUDA graphs and with direct launches."""
+    import numpy as np
+    import torch
+    import paper_1907_05993_gb300 as P
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    from synth import kikuchi as K
+    torch.cuda.set_device(local_rank)
+    spec = K.config1()
+    refs, tests, ridx, _ = K.make_scan(spec)
+    refs, tests, ridx = (torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(), torch.from_numpy(ridx).cuda())
+    roi = K.roi_grid(128, 128, 32, True)
+    res = {}
+    for graphs in (1, 0):
+        pipe = Pipeline(PipelineConfig(128, 128, roi, 32, 3, (50, 50, 50)))
+        P.hrebsd_set_option(pipe.ctx, P.OPT_GRAPHS, graphs)
+        out = {}
+        for _ in range(max(3, args.warmup)):
+            pipe.run(refs, tests, ridx, out=out)
+        torch.cuda.synchronize()
+        reps = max(20, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = P.hrebsd_launch_count(pipe.ctx)
+        e0.record()
+        for _ in range(reps):
+            pipe.run(refs, tests, ridx, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        res[graphs] = (e0.elapsed_time(e1) / reps, (P.hrebsd_launch_count(pipe.ctx) - l0) / reps)
+        pipe.close()
+    line = {"metric": "single-pair latency (demons+XCF)", "workload": "single", "value": res[1][0], "unit": "ms/pair",
+            "higher_is_better": False, "n_gpus": 1, "steps": max(20, args.steps), "warmup": max(3, args.warmup),
+            "data": "synthetic (seeded kinematic Kikuchi generator)", "dtype": "f32",
+            "config": {"workload": "1 pair 128x128, 2 deg, 3 levels x 50 iterations, 21 ROIs 32x32"},
+            "ms_per_pair_graphs": res[1][0], "ms_per_pair_direct": res[0][0], "kernel_launches_per_pair": res[1][1]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ large patterns (f4)
 def run_large(args, rank, world, local_rank):
     """1024 x 1024 patterns (the paper's 1244 x 1024 simulations cut to a width the 7-level pyramid
@@ -635,7 +677,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("scan", "learned", "compare", "large"), default="scan")
+    ap.add_argument("--workload", choices=("scan", "learned", "compare", "large", "single"), default="scan")
     ap.add_argument("--large-pairs", type=int, default=512)
     ap.add_argument("--compare-orientations", type=int, default=16)
     ap.add_argument("--train-pairs", type=int, default=200_000)
@@ -657,6 +699,8 @@ def main():
         return run_compare(args, rank, world, local_rank)
     if args.workload == "large":
         return run_large(args, rank, world, local_rank)
+    if args.workload == "single":
+        return run_single(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 
