@@ -62,7 +62,7 @@ def test_learned_start_reaches_plain_rotation(trained):
     # the learned start needs the trained network in the pipeline's context
     w, _ = P.hrebsd_cnn_get_params(ctx)
     P.hrebsd_cnn_init(pipe.ctx, w)
-    learned = pipe.run(refs, tests, ridx, learned_caps=(100, 100, 100, 0))
+    learned = pipe.run(refs, tests, ridx, learned_caps=(100, 100, 25, 0), learned_start_res=64)
     torch.cuda.synchronize()
     Fp = plain["F"].cpu().numpy().reshape(-1, 3, 3)
     Fl = learned["F"].cpu().numpy().reshape(-1, 3, 3)
