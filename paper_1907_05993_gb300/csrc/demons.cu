@@ -108,6 +108,29 @@ __device__ __forceinline__ float2 bilinear2_clamped(const float2 *__restrict__ M
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Two bilinear samples (the same arithmetic as bilinear_clamped, each rounding
+// step identical) with the interpolation done in packed FP32x2 operations.
+// 1 - f is formed as fma(f, -1, 1), which rounds like the subtraction.
+__device__ __forceinline__ float2 bilinear_pair_clamped(const float *__restrict__ M, int h, int w, float xa, float ya,
+                                                         float xb, float yb)
+{
+    xa = fminf(fmaxf(xa, 0.0f), (float)(w - 1));
+    ya = fminf(fmaxf(ya, 0.0f), (float)(h - 1));
+    xb = fminf(fmaxf(xb, 0.0f), (float)(w - 1));
+    yb = fminf(fmaxf(yb, 0.0f), (float)(h - 1));
+    const int xa0 = min((int)xa, w - 2), ya0 = min((int)ya, h - 2);
+    const int xb0 = min((int)xb, w - 2), yb0 = min((int)yb, h - 2);
+    const float2 fx = make_float2(xa - (float)xa0, xb - (float)xb0), fy = make_float2(ya - (float)ya0, yb - (float)yb0);
+    const float *pa = M + ya0 * w + xa0, *pb = M + yb0 * w + xb0;
+    const float2 A = make_float2(__ldg(pa), __ldg(pb)), Bv = make_float2(__ldg(pa + 1), __ldg(pb + 1));
+    const float2 C = make_float2(__ldg(pa + w), __ldg(pb + w)), D = make_float2(__ldg(pa + w + 1), __ldg(pb + w + 1));
+    const float2 n1 = make_float2(-1.0f, -1.0f), one = make_float2(1.0f, 1.0f);
+    const float2 omx = __ffma2_rn(fx, n1, one), omy = __ffma2_rn(fy, n1, one);
+    const float2 top = __ffma2_rn(fx, Bv, __fmul2_rn(omx, A));
+    const float2 bot = __ffma2_rn(fx, D, __fmul2_rn(omx, C));
+    return __ffma2_rn(fy, bot, __fmul2_rn(omy, top));
+}
+
 template <int RAD, int TX_ = TX, int TY_ = TY>
 struct Geo {
     static constexpr int BW = TX_ + 2 * RAD, BH = TY_ + 2 * RAD;       // u and du (T + r)
@@ -561,20 +584,33 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
 #pragma unroll
                 for (int i = 0; i < FR; ++i) sU[(r0 + i) * L::UST + c] = u[i];
             }
-            float mw[FR];
+            // pixel pairs (i, i + 1) in packed FP32x2 arithmetic; every rounding step is the
+            // scalar one (a - b as fma(b, -1, a), products and fmas in the same order)
+            static_assert(FR % 2 == 0, "force runs are processed in pixel pairs");
+            const float2 n1 = make_float2(-1.0f, -1.0f), sx2 = make_float2(sx, sx);
+            const float2 al2 = make_float2(a.alpha2, a.alpha2);
 #pragma unroll
-            for (int i = 0; i < FR; ++i) mw[i] = bilinear_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y);
+            for (int i = 0; i < FR; i += 2) {
+                const float2 mw = bilinear_pair_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y,
+                                                        (float)vx - u[i + 1].x, (float)(vy0 + i + 1) - u[i + 1].y);
+                const int vya = vy0 + i, vyb = vya + 1;
+                const float2 sy2 = make_float2((vya == 0 || vya == h - 1) ? 1.0f : 0.5f,
+                                               (vyb == 0 || vyb == h - 1) ? 1.0f : 0.5f);
+                const float2 gx = __fmul2_rn(sx2, __ffma2_rn(make_float2(fl[i], fl[i + 1]), n1,
+                                                             make_float2(fr[i], fr[i + 1])));
+                const float2 gy = __fmul2_rn(sy2, __ffma2_rn(make_float2(fv[i], fv[i + 1]), n1,
+                                                             make_float2(fv[i + 2], fv[i + 3])));
+                const float2 d = __ffma2_rn(make_float2(fv[i + 1], fv[i + 2]), n1, mw);
+                const float2 den = __ffma2_rn(gx, gx, __ffma2_rn(gy, gy, __fmul2_rn(__fmul2_rn(al2, d), d)));
 #pragma unroll
-            for (int i = 0; i < FR; ++i) {
-                const int r = r0 + i, vy = vy0 + i;
-                const float sy = (vy == 0 || vy == h - 1) ? 1.0f : 0.5f;
-                const float gx = sx * (fr[i] - fl[i]);
-                const float gy = sy * (fv[i + 2] - fv[i]);
-                const float d = mw[i] - fv[i + 1];
-                const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
-                const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
-                if (L::BH % FR == 0 || r < L::BH) sD[r * L::DST + c] = make_float2(t * gx, t * gy);
-                if (colT && r >= RAD && r < RAD + TY_ && vy < h) ssd = fmaf(d, d, ssd);
+                for (int j = 0; j < 2; ++j) {
+                    const int r = r0 + i + j, vy = vya + j;
+                    const float dj = j ? d.y : d.x, denj = j ? den.y : den.x;
+                    const float t = denj > 1e-9f ? __fdividef(dj, denj) : 0.0f;
+                    const float2 g = j ? make_float2(gx.y, gy.y) : make_float2(gx.x, gy.x);
+                    if (L::BH % FR == 0 || r < L::BH) sD[r * L::DST + c] = __fmul2_rn(make_float2(t, t), g);
+                    if (colT && r >= RAD && r < RAD + TY_ && vy < h) ssd = fmaf(dj, dj, ssd);
+                }
             }
         }
         if (border) {   // du outside the image = du at the clamped position
