@@ -329,6 +329,14 @@ int hrebsd_fit_quality(hrebsd_ctx *ctx, const double *F, const double *R, const 
 int hrebsd_ssim_warped(hrebsd_ctx *ctx, const float *ref, const int32_t *ref_idx, const float *test,
                        const float *field, int B, int H, int W, double *ssim, void *stream);
 
+/* Check of the fifth-generation tensor-core building blocks the library uses
+ * (no counterpart in the paper; a test hook): D[128][N] = A[128][16 KS] x
+ * B[N][16 KS]^T with BF16 A, B (row-major, device) and FP32 D, computed by
+ * tcgen05 MMAs from shared-memory descriptors into tensor memory.  N in
+ * {16, 32, 64}, KS in 1..4.  One CTA on `stream`; a bounded wait that gives up
+ * sets the flag read by hrebsd_device_error (D is then not written). */
+int hrebsd_tc_selftest(hrebsd_ctx *ctx, const uint16_t *A, const uint16_t *B, int N, int KS, float *D, void *stream);
+
 /* Measurement helper (no counterpart in the paper): launch an FP32 FMA
  * throughput probe on `stream` (SMs x 8 CTAs of 256 threads, each thread 8
  * independent chains of packed FP32x2 FMAs, `iters` steps); *flops receives the
