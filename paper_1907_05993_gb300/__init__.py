@@ -20,7 +20,7 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "TILE_VARIANTS",
+    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
     "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
     "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
@@ -182,6 +182,7 @@ def hrebsd_launch_count(ctx) -> int:
 
 OPT_NO_TMA = 1
 OPT_GRAPHS = 2
+OPT_CNN_TC = 3
 
 
 def hrebsd_device_error(ctx):

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cnn_kernels.cuh"
+#include "cnn_tc.cuh"
 #include "internal.cuh"
 
 using namespace hr_cnn;
@@ -473,6 +474,37 @@ int launch_halo_t(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
     return HREBSD_OK;
 }
 
+// tcgen05 implicit GEMM (cnn_tc.cuh); returns 1 when the shape or the TMEM
+// budget (resident CTAs x columns <= 512 per SM) rules it out.
+template <int BN, int KS>
+int launch_tc_t(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
+{
+    constexpr int kStages = 3;
+    using G = TcConv<BN, KS, kStages>;
+    static int configured = -1, occ = 0;
+    if (configured != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(conv3x3_tc_kernel<BN, KS, kStages>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tc_kernel<BN, KS, kStages>, 128, G::SMEM));
+        configured = ctx->device;
+    }
+    if (occ < 1 || occ * (int)G::TMEM_COLS > 512) return 1;
+    const int P = a.N * a.H * a.W;
+    dim3 grid((P + 127) / 128, (a.cout + BN - 1) / BN);
+    conv3x3_tc_kernel<BN, KS, kStages><<<grid, 128, G::SMEM, st>>>(a, ctx->d_err);
+    return HREBSD_OK;
+}
+
+int launch_tc_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
+{
+    if (!ctx->cnn_tc || a.cin % 16 || a.N < 1) return 1;
+    const int co = a.cout;
+    if (co % 64 == 0) return launch_tc_t<64, 2>(ctx, a, st);
+    if (co % 32 == 0) return launch_tc_t<32, 2>(ctx, a, st);
+    if (co % 16 == 0) return launch_tc_t<16, 4>(ctx, a, st);
+    return 1;
+}
+
 int launch_halo_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
 {
     if (a.H != a.W || a.H < 16 || a.H % 16 || a.N < 1) return 1;
@@ -515,7 +547,8 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
     a.W = res;
     const int P = N * res * res;
     hr_prof_begin(ctx, st);
-    int e = launch_halo_conv(ctx, a, st);
+    int e = launch_tc_conv(ctx, a, st);
+    if (e == 1) e = launch_halo_conv(ctx, a, st);
     if (e == 1) {   // no halo variant for this shape: pipelined implicit GEMM
         // output-channel tile: the largest of 64, 32, 16 that divides cout
         const int bn = cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16);

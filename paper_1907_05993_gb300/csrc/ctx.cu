@@ -241,6 +241,7 @@ int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value)
     switch (option) {
     case HREBSD_OPT_NO_TMA: ctx->no_tma = value ? 1 : 0; return HREBSD_OK;
     case HREBSD_OPT_GRAPHS: ctx->graphs = value ? 1 : 0; return HREBSD_OK;
+    case HREBSD_OPT_CNN_TC: ctx->cnn_tc = value ? 1 : 0; return HREBSD_OK;
     default: return HREBSD_EINVAL;
     }
 }

@@ -107,3 +107,50 @@ def test_training_reduces_loss(env):
         P.hrebsd_cnn_train_step(ctx, xg, tg, 8, 2e-3, loss)
         losses.append(float(loss))
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_tcgen05_convolutions_match_oracle_and_mma_path(env):
+    """HREBSD_OPT_CNN_TC: every 3x3 convolution (forward and input gradient) on tcgen05 MMAs
+    into tensor memory; same bars against the oracle, and close to the mma.sync path."""
+    torch, P, CP, OC, ctx0 = env
+    ctx = P.hrebsd_create(0)
+    P.hrebsd_set_option(ctx, P.OPT_CNN_TC, 1)
+    try:
+        p = _params(OC, 1)
+        v = CP.pack(p)
+        rng = np.random.default_rng(2)
+        xg, xr = _bf16_tensor(torch, OC, rng.normal(size=(3, 2, 64, 64)))
+        outs = []
+        for c in (ctx, ctx0):
+            P.hrebsd_cnn_init(c, v)
+            out = torch.empty((3, 2, 64, 64), device="cuda")
+            P.hrebsd_cnn_infer(c, xg, 3, out)
+            P.hrebsd_device_error(c)
+            outs.append(out.cpu().numpy())
+        exp, _ = OC.forward(CP.unpack(v), xr, bf16=True)
+        scale = np.abs(exp).max()
+        assert np.abs(outs[0] - exp).max() <= 0.02 * scale
+        assert np.abs(outs[0] - outs[1]).max() <= 0.02 * scale
+        # gradients
+        p3 = _params(OC, 3)
+        v3 = CP.pack(p3)
+        P.hrebsd_cnn_init(ctx, v3)
+        rng = np.random.default_rng(4)
+        xg, xr = _bf16_tensor(torch, OC, rng.normal(size=(2, 2, 64, 64)))
+        target = rng.normal(0, 0.5, (2, 2, 64, 64)).astype(np.float32)
+        loss = torch.zeros(1, device="cuda")
+        P.hrebsd_cnn_train_step(ctx, xg, torch.from_numpy(target).cuda(), 2, 0.0, loss)
+        P.hrebsd_device_error(ctx)
+        _, grads = P.hrebsd_cnn_get_params(ctx)
+        pu = CP.unpack(v3)
+        o, cache = OC.forward(pu, xr, bf16=True)
+        l_exp, dout = OC.mse(o, target.astype(np.float64))
+        assert abs(float(loss) - l_exp) <= 0.02 * l_exp
+        g_exp = OC.backward(pu, cache, dout, bf16=True)
+        g = CP.unpack(grads)
+        for k in g_exp:
+            num = np.linalg.norm(g[k] - g_exp[k])
+            den = np.linalg.norm(g_exp[k]) + 1e-30
+            assert num <= 0.05 * den, (k, num / den)
+    finally:
+        P.hrebsd_destroy(ctx)
