@@ -29,6 +29,16 @@ constexpr LayerDef kLayers[NCONV] = {{2, 16, 64},   {16, 16, 64},  {16, 32, 32},
                                      {96, 32, 32},  {32, 32, 32},  {48, 16, 64}, {16, 16, 64}};
 constexpr int HEAD_CIN = 16, HEAD_COUT = 2;
 
+// Tile of the TMA + tensor-memory convolution per image size: Ht output rows of
+// TI images per CTA and BN output channels (every layer's cout is a multiple).
+struct TmaGeo {
+    int Ht, TI, BN;
+};
+constexpr TmaGeo tma_geo(int res)
+{
+    return res >= 64 ? TmaGeo{8, 1, 16} : res >= 32 ? TmaGeo{16, 1, 32} : res >= 16 ? TmaGeo{16, 1, 64} : TmaGeo{8, 5, 64};
+}
+
 __host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
 
 // Grid of the per-image element-wise kernels: x covers `per` items of one
@@ -287,7 +297,7 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, size_t
 // and they stay at zero).  -> BF16 copy of the same layout, and the BF16
 // input-gradient layout [ci][tap'][co] with tap' = 8 - tap (the flipped
 // kernel with input and output channels exchanged).
-__global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp, bf16 *wf, bf16 *wd)
+__global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp, bf16 *wf, bf16 *wd, bf16 *wt, int bn)
 {
     const int total = co * 9 * cinp;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -295,6 +305,10 @@ __global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp,
         const float v = c < ci ? w[i] : 0.0f;
         wf[i] = __float2bfloat16_rn(v);
         if (wd && c < ci) wd[((size_t)c * 9 + (8 - tap)) * co + o] = __float2bfloat16_rn(v);
+        // tensor-memory path: [co / bn][cinp / 16][c % 16 / 8][tap][o % bn][c % 8]
+        if (wt)
+            wt[(((((size_t)(o / bn) * (cinp / 16) + c / 16) * 2 + (c % 16) / 8) * 9 + tap) * bn + o % bn) * 8 + c % 8] =
+                __float2bfloat16_rn(v);
     }
 }
 
@@ -319,7 +333,7 @@ struct hr_cnn_net {
     size_t n_params = 0;
     size_t w_off[NCONV + 1], b_off[NCONV + 1];   // index NCONV = head
     float *W = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
-    bf16 *wf[NCONV + 1] = {}, *wd[NCONV] = {};
+    bf16 *wf[NCONV + 1] = {}, *wd[NCONV] = {}, *wt[NCONV] = {};
     int step = 0;
     // activations for a batch capacity
     int cap = 0;
@@ -350,8 +364,8 @@ int net_alloc(std::vector<void *> &allocs, size_t bytes, void **p)
 
 void net_free_acts(hr_cnn_net *n)
 {
-    // activations are the allocations after the parameter block (index >= 4 + 15 + 14)
-    const size_t keep = 4 + (NCONV + 1) + NCONV;
+    // activations are the allocations after the parameter block (index >= 4 + 15 + 14 + 14)
+    const size_t keep = 4 + (NCONV + 1) + 2 * NCONV;
     for (size_t i = keep; i < n->allocs.size(); ++i) cudaFree(n->allocs[i]);
     if (n->allocs.size() > keep) n->allocs.resize(keep);
     n->cap = 0;
@@ -387,6 +401,13 @@ int ensure_net(hrebsd_ctx *ctx)
     for (int l = 0; l < NCONV; ++l) {
         if ((e = net_alloc(n->allocs, (size_t)kLayers[l].cin * 9 * kLayers[l].cout * sizeof(bf16), &p))) { delete n; return e; }
         n->wd[l] = (bf16 *)p;
+    }
+    for (int l = 0; l < NCONV; ++l) {
+        if ((e = net_alloc(n->allocs, (size_t)pad16(kLayers[l].cin) * 9 * kLayers[l].cout * sizeof(bf16), &p))) {
+            delete n;
+            return e;
+        }
+        n->wt[l] = (bf16 *)p;
     }
     ctx->cnn = n;
     return HREBSD_OK;
@@ -439,8 +460,8 @@ int refresh_bf16(hrebsd_ctx *ctx, cudaStream_t st)
     hr_cnn_net *n = ctx->cnn;
     for (int l = 0; l < NCONV; ++l) {
         const int ci = kLayers[l].cin, co = kLayers[l].cout;
-        weights_to_bf16_kernel<<<grid_for(ctx, (size_t)co * 9 * pad16(ci)), 256, 0, st>>>(n->W + n->w_off[l], ci, co,
-                                                                                          pad16(ci), n->wf[l], n->wd[l]);
+        weights_to_bf16_kernel<<<grid_for(ctx, (size_t)co * 9 * pad16(ci)), 256, 0, st>>>(
+            n->W + n->w_off[l], ci, co, pad16(ci), n->wf[l], n->wd[l], n->wt[l], tma_geo(kLayers[l].res).BN);
         HR_LAUNCHED(ctx);
     }
     cast_bf16_kernel<<<1, 64, 0, st>>>(n->W + n->w_off[NCONV], HEAD_COUT * HEAD_CIN, n->wf[NCONV]);
@@ -505,6 +526,73 @@ int launch_tc_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
     return 1;
 }
 
+// Halo tiles by TMA into tcgen05 MMAs (forward convolutions with BF16 output and
+// the tiled weight copy).  Returns 1 when the shape is not covered.
+template <int BN>
+int launch_tma_t(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_t st)
+{
+    const TmaGeo g = tma_geo(a.H);
+    const int res = a.H, Wp = res + 2, Rimg = (g.Ht + 2) * Wp;
+    TmaConvArgs t;
+    t.wt = wt;
+    t.bias = a.bias;
+    t.y = reinterpret_cast<bf16 *>(a.y);
+    t.ys = a.ys;
+    t.yo = a.yo;
+    t.relu = a.relu;
+    t.cin = a.cin;
+    t.cout = a.cout;
+    t.N = a.N;
+    t.res = res;
+    t.Ht = g.Ht;
+    t.TI = g.TI;
+    const int qneed = (g.TI - 1) * Rimg + (g.Ht - 1) * Wp + res;   // last stored flat row + 1
+    t.nM = (qneed + 127) / 128;
+    const int rows = g.TI * Rimg > t.nM * 128 + 2 * Wp + 2 ? g.TI * Rimg : t.nM * 128 + 2 * Wp + 2;
+    t.PR = (rows + 7) / 8 * 8;
+    int cols = 32;
+    while (cols < t.nM * BN) cols *= 2;
+    if (cols > 256) return 1;
+    t.tmem_cols = cols;
+    t.nst = a.cin / 16 < 3 ? a.cin / 16 : 3;
+    size_t smem = (size_t)t.nst * (2 * (size_t)t.PR * 16 + 9 * BN * 32);
+    if (smem > 200 * 1024) return 1;
+    // at most 512 / cols CTAs per SM, so that tcgen05.alloc never waits
+    const size_t cap = (size_t)(228 * 1024) / (size_t)(512 / cols + 1);
+    if (smem + 1024 < cap) smem = cap - 1024 + 16;
+    static int configured = -1;
+    if (configured != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(conv3x3_tma_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        configured = ctx->device;
+    }
+    CUtensorMap tm;
+    const uint64_t xs2 = (uint64_t)a.xs * 2;
+    const uint64_t dims[4] = {(uint64_t)a.cin, (uint64_t)res, (uint64_t)res, (uint64_t)a.N};
+    const uint64_t strides[3] = {xs2, xs2 * res, xs2 * res * res};
+    const uint32_t box[4] = {8, (uint32_t)Wp, (uint32_t)(g.Ht + 2), (uint32_t)g.TI};
+    if (hr_encode_tmap_bf16_4d(&tm, a.x + a.xo, dims, strides, box)) {
+        fprintf(stderr, "hrebsd: tensor map of a %dx%d x %d-channel convolution input refused\n", res, res, a.cin);
+        return HREBSD_ECUDA;   // the tensor-memory path was asked for: no silent fallback
+    }
+    const long long tiles = (long long)((a.N + g.TI - 1) / g.TI) * (res / g.Ht) * (a.cout / BN);
+    if (tiles > 0x7fffffffLL) return 1;
+    conv3x3_tma_tc_kernel<BN><<<(unsigned)tiles, 128, smem, st>>>(tm, t, ctx->d_err);
+    return cudaGetLastError() == cudaSuccess ? HREBSD_OK : HREBSD_ECUDA;
+}
+
+int launch_tma_conv(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_t st)
+{
+    if (!wt || !ctx->cnn_tc || a.y_fp32 || a.H != a.W || a.N < 1 || a.cin % 16) return 1;
+    const TmaGeo g = tma_geo(a.H);
+    if ((a.H != 64 && a.H != 32 && a.H != 16 && a.H != 8) || a.H % g.Ht || a.cout % g.BN) return 1;
+    if (a.xs % 8 || a.xo % 8 || a.ys % 8 || a.yo % 8) return 1;
+    if (g.BN == 16) return launch_tma_t<16>(ctx, a, wt, st);
+    if (g.BN == 32) return launch_tma_t<32>(ctx, a, wt, st);
+    if (g.BN == 64) return launch_tma_t<64>(ctx, a, wt, st);
+    return 1;
+}
+
 int launch_halo_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
 {
     if (a.H != a.W || a.H < 16 || a.H % 16 || a.N < 1) return 1;
@@ -527,7 +615,7 @@ int launch_halo_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
 }
 
 int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w, const float *bias, int cout, void *y,
-         int ys, int yo, int y_fp32, int relu, int N, int res, cudaStream_t st)
+         int ys, int yo, int y_fp32, int relu, int N, int res, cudaStream_t st, const bf16 *wt = nullptr)
 {
     ConvArgs a;
     a.x = x;
@@ -547,7 +635,8 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
     a.W = res;
     const int P = N * res * res;
     hr_prof_begin(ctx, st);
-    int e = launch_tc_conv(ctx, a, st);
+    int e = launch_tma_conv(ctx, a, wt, st);
+    if (e == 1) e = launch_tc_conv(ctx, a, st);
     if (e == 1) e = launch_halo_conv(ctx, a, st);
     if (e == 1) {   // no halo variant for this shape: pipelined implicit GEMM
         // output-channel tile: the largest of 64, 32, 16 that divides cout
@@ -649,7 +738,7 @@ int forward(hrebsd_ctx *ctx, int B, cudaStream_t st)
     int e;
     auto run = [&](int l) {
         return conv(ctx, in[l].p, in[l].s, in[l].o, pad16(kLayers[l].cin), n->wf[l], n->W + n->b_off[l],
-                    kLayers[l].cout, out[l].p, out[l].s, out[l].o, 0, 1, B, kLayers[l].res, st);
+                    kLayers[l].cout, out[l].p, out[l].s, out[l].o, 0, 1, B, kLayers[l].res, st, n->wt[l]);
     };
     auto pool = [&](int k, const View &v, int C, int res) {
         maxpool_kernel<<<grid2(res * res / 4 * C / 8, B), 256, 0, st>>>(v.p, v.s, v.o, C, B, res, res, n->pool[k],

@@ -73,6 +73,25 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *tm, uint64
         : "memory");
 }
 
+// 4-D tiled bulk tensor load of the box at (x, y, z, w) into shared memory.
+__device__ __forceinline__ void load_4d(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y, int z, int w)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plain (untiled) bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned).
+__device__ __forceinline__ void load_bulk(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 }  // namespace hr_tma
 
 // Host: encode a 3-D FP32 tiled tensor map (dims innermost first, strides in
@@ -80,3 +99,9 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *tm, uint64
 // refuses the shape (the caller then uses a path without TMA).
 int hr_encode_tmap_3d(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1,
                       uint64_t s2, uint32_t b0, uint32_t b1, uint32_t b2);
+
+// Host: encode a 4-D BF16 tiled tensor map (dims innermost first, byte strides
+// of dims 1..3, box b0..b3; out-of-range elements read as zero).  Same return
+// convention as hr_encode_tmap_3d.
+int hr_encode_tmap_bf16_4d(CUtensorMap *tm, const void *base, const uint64_t dims[4], const uint64_t strides[3],
+                           const uint32_t box[4]);
