@@ -89,11 +89,12 @@ int hrebsd_device_error(hrebsd_ctx *ctx);
  * point, or when the caller's stream is itself capturing (the launches then go
  * into the caller's graph).  Same results either way. */
 #define HREBSD_OPT_GRAPHS 2
-/* HREBSD_OPT_CNN_TC (value 0/1, default 0): run the 3x3 convolutions of the
- * learned initialiser (forward and input gradient) as implicit GEMMs on the
- * fifth-generation tensor cores (tcgen05 MMAs into tensor memory) instead of
- * the mma.sync kernels.  Same operands and FP32 accumulation; the sums are
- * grouped differently, so results agree to FP32 rounding. */
+/* HREBSD_OPT_CNN_TC (value 0/1, default 1): run the forward 3x3 convolutions
+ * of the learned initialiser on the fifth-generation tensor cores (input halo
+ * tiles by TMA, tcgen05 MMAs into tensor memory); 0 selects the mma.sync
+ * kernels.  Gradients always use the mma.sync kernels.  Same operands and
+ * FP32 accumulation; the sums are grouped differently, so results agree to
+ * FP32 rounding before the BF16 store. */
 #define HREBSD_OPT_CNN_TC 3
 int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value);
 

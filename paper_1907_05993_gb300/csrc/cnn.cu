@@ -29,14 +29,11 @@ constexpr LayerDef kLayers[NCONV] = {{2, 16, 64},   {16, 16, 64},  {16, 32, 32},
                                      {96, 32, 32},  {32, 32, 32},  {48, 16, 64}, {16, 16, 64}};
 constexpr int HEAD_CIN = 16, HEAD_COUT = 2;
 
-// Tile of the TMA + tensor-memory convolution per image size: Ht output rows of
-// TI images per CTA and BN output channels (every layer's cout is a multiple).
-struct TmaGeo {
-    int Ht, TI, BN;
-};
-constexpr TmaGeo tma_geo(int res)
+// Output channels per CTA of the TMA + tensor-memory convolution at an image
+// size (the tiled weight copy is laid out for it).
+int tma_bn(int res)
 {
-    return res >= 64 ? TmaGeo{8, 1, 16} : res >= 32 ? TmaGeo{16, 1, 32} : res >= 16 ? TmaGeo{16, 1, 64} : TmaGeo{8, 5, 64};
+    return res >= 64 ? TmaGeom<64>::BN : res >= 32 ? TmaGeom<32>::BN : res >= 16 ? TmaGeom<16>::BN : TmaGeom<8>::BN;
 }
 
 __host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
@@ -461,7 +458,7 @@ int refresh_bf16(hrebsd_ctx *ctx, cudaStream_t st)
     for (int l = 0; l < NCONV; ++l) {
         const int ci = kLayers[l].cin, co = kLayers[l].cout;
         weights_to_bf16_kernel<<<grid_for(ctx, (size_t)co * 9 * pad16(ci)), 256, 0, st>>>(
-            n->W + n->w_off[l], ci, co, pad16(ci), n->wf[l], n->wd[l], n->wt[l], tma_geo(kLayers[l].res).BN);
+            n->W + n->w_off[l], ci, co, pad16(ci), n->wf[l], n->wd[l], n->wt[l], tma_bn(kLayers[l].res));
         HR_LAUNCHED(ctx);
     }
     cast_bf16_kernel<<<1, 64, 0, st>>>(n->W + n->w_off[NCONV], HEAD_COUT * HEAD_CIN, n->wf[NCONV]);
@@ -495,44 +492,14 @@ int launch_halo_t(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
     return HREBSD_OK;
 }
 
-// tcgen05 implicit GEMM (cnn_tc.cuh); returns 1 when the shape or the TMEM
-// budget (resident CTAs x columns <= 512 per SM) rules it out.
-template <int BN, int KS>
-int launch_tc_t(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
-{
-    constexpr int kStages = 3;
-    using G = TcConv<BN, KS, kStages>;
-    static int configured = -1, occ = 0;
-    if (configured != ctx->device) {
-        HR_CHECK(cudaFuncSetAttribute(conv3x3_tc_kernel<BN, KS, kStages>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM));
-        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tc_kernel<BN, KS, kStages>, 128, G::SMEM));
-        configured = ctx->device;
-    }
-    if (occ < 1 || occ * (int)G::TMEM_COLS > 512) return 1;
-    const int P = a.N * a.H * a.W;
-    dim3 grid((P + 127) / 128, (a.cout + BN - 1) / BN);
-    conv3x3_tc_kernel<BN, KS, kStages><<<grid, 128, G::SMEM, st>>>(a, ctx->d_err);
-    return HREBSD_OK;
-}
-
-int launch_tc_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
-{
-    if (!ctx->cnn_tc || a.cin % 16 || a.N < 1) return 1;
-    const int co = a.cout;
-    if (co % 64 == 0) return launch_tc_t<64, 2>(ctx, a, st);
-    if (co % 32 == 0) return launch_tc_t<32, 2>(ctx, a, st);
-    if (co % 16 == 0) return launch_tc_t<16, 4>(ctx, a, st);
-    return 1;
-}
-
 // Halo tiles by TMA into tcgen05 MMAs (forward convolutions with BF16 output and
 // the tiled weight copy).  Returns 1 when the shape is not covered.
-template <int BN>
+template <int RES>
 int launch_tma_t(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_t st)
 {
-    const TmaGeo g = tma_geo(a.H);
-    const int res = a.H, Wp = res + 2, Rimg = (g.Ht + 2) * Wp;
+    using G = TmaGeom<RES>;
+    constexpr int BN = G::BN;
+    if (a.cout % BN || a.cout > 256) return 1;
     TmaConvArgs t;
     t.wt = wt;
     t.bias = a.bias;
@@ -543,54 +510,66 @@ int launch_tma_t(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_
     t.cin = a.cin;
     t.cout = a.cout;
     t.N = a.N;
-    t.res = res;
-    t.Ht = g.Ht;
-    t.TI = g.TI;
-    const int qneed = (g.TI - 1) * Rimg + (g.Ht - 1) * Wp + res;   // last stored flat row + 1
-    t.nM = (qneed + 127) / 128;
-    const int rows = g.TI * Rimg > t.nM * 128 + 2 * Wp + 2 ? g.TI * Rimg : t.nM * 128 + 2 * Wp + 2;
-    t.PR = (rows + 7) / 8 * 8;
-    int cols = 32;
-    while (cols < t.nM * BN) cols *= 2;
-    if (cols > 256) return 1;
-    t.tmem_cols = cols;
-    t.nst = a.cin / 16 < 3 ? a.cin / 16 : 3;
-    size_t smem = (size_t)t.nst * (2 * (size_t)t.PR * 16 + 9 * BN * 32);
-    if (smem > 200 * 1024) return 1;
-    // at most 512 / cols CTAs per SM, so that tcgen05.alloc never waits
-    const size_t cap = (size_t)(228 * 1024) / (size_t)(512 / cols + 1);
-    if (smem + 1024 < cap) smem = cap - 1024 + 16;
+    // channels per box: the widest of 64, 32, 16 dividing cin that leaves room for 3 stages (else 2)
+    t.cw = 0;
+    for (int pass = 0; pass < 2 && !t.cw; ++pass) {
+        for (int cw = 64; cw >= 16; cw /= 2) {
+            if (a.cin % cw) continue;
+            const size_t ab = ((size_t)G::PR * cw * 2 + 1023) / 1024 * 1024;
+            const size_t st_b = (ab + (size_t)(cw / 16) * 9 * BN * 32 + 1023) / 1024 * 1024;
+            if (st_b * (pass == 0 ? 3 : 2) <= 200 * 1024) {
+                t.cw = cw;
+                t.a_bytes = (int)ab;
+                t.stage_bytes = (int)st_b;
+                break;
+            }
+        }
+    }
+    if (!t.cw) return 1;
+    t.nst = (int)((200 * 1024) / (size_t)t.stage_bytes);
+    if (t.nst > 8) t.nst = 8;
+    if (t.nst < 2) return 1;
+    size_t smem = (size_t)t.nst * t.stage_bytes + 1024;   // + slack for 1024-byte alignment
+    // at most 512 / TMEM CTAs per SM, so that tcgen05.alloc never waits
+    const size_t cap = (size_t)(228 * 1024) / (size_t)(512 / G::TMEM + 1);
+    if (smem + 2048 < cap) smem = cap - 2048 + 16;
     static int configured = -1;
     if (configured != ctx->device) {
-        HR_CHECK(cudaFuncSetAttribute(conv3x3_tma_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      200 * 1024));
+        HR_CHECK(cudaFuncSetAttribute(conv3x3_tma_tc_kernel<RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      210 * 1024));
         configured = ctx->device;
     }
     CUtensorMap tm;
     const uint64_t xs2 = (uint64_t)a.xs * 2;
-    const uint64_t dims[4] = {(uint64_t)a.cin, (uint64_t)res, (uint64_t)res, (uint64_t)a.N};
-    const uint64_t strides[3] = {xs2, xs2 * res, xs2 * res * res};
-    const uint32_t box[4] = {8, (uint32_t)Wp, (uint32_t)(g.Ht + 2), (uint32_t)g.TI};
-    if (hr_encode_tmap_bf16_4d(&tm, a.x + a.xo, dims, strides, box)) {
-        fprintf(stderr, "hrebsd: tensor map of a %dx%d x %d-channel convolution input refused\n", res, res, a.cin);
+    const uint64_t dims[4] = {(uint64_t)a.cin, (uint64_t)RES, (uint64_t)RES, (uint64_t)a.N};
+    const uint64_t strides[3] = {xs2, xs2 * RES, xs2 * RES * RES};
+    const uint32_t box[4] = {(uint32_t)t.cw, (uint32_t)G::Wp, (uint32_t)(G::Ht + 2), (uint32_t)G::TI};
+    if (hr_encode_tmap_bf16_4d(&tm, a.x + a.xo, dims, strides, box, t.cw * 2)) {
+        fprintf(stderr, "hrebsd: tensor map of a %dx%d x %d-channel convolution input refused\n", RES, RES, a.cin);
         return HREBSD_ECUDA;   // the tensor-memory path was asked for: no silent fallback
     }
-    const long long tiles = (long long)((a.N + g.TI - 1) / g.TI) * (res / g.Ht) * (a.cout / BN);
+    const long long tiles = (long long)((a.N + G::TI - 1) / G::TI) * (RES / G::Ht) * (a.cout / BN);
     if (tiles > 0x7fffffffLL) return 1;
-    conv3x3_tma_tc_kernel<BN><<<(unsigned)tiles, 128, smem, st>>>(tm, t, ctx->d_err);
+    t.ntiles = (int)tiles;
+    int per_sm = 512 / G::TMEM;
+    const int by_smem = (int)((size_t)(228 * 1024) / (smem + 2048));
+    if (by_smem < per_sm) per_sm = by_smem;
+    const long long grid = tiles < (long long)ctx->num_sms * per_sm ? tiles : (long long)ctx->num_sms * per_sm;
+    conv3x3_tma_tc_kernel<RES><<<(unsigned)grid, kTmaConvThreads, smem, st>>>(tm, t, ctx->d_err);
     return cudaGetLastError() == cudaSuccess ? HREBSD_OK : HREBSD_ECUDA;
 }
 
 int launch_tma_conv(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_t st)
 {
     if (!wt || !ctx->cnn_tc || a.y_fp32 || a.H != a.W || a.N < 1 || a.cin % 16) return 1;
-    const TmaGeo g = tma_geo(a.H);
-    if ((a.H != 64 && a.H != 32 && a.H != 16 && a.H != 8) || a.H % g.Ht || a.cout % g.BN) return 1;
     if (a.xs % 8 || a.xo % 8 || a.ys % 8 || a.yo % 8) return 1;
-    if (g.BN == 16) return launch_tma_t<16>(ctx, a, wt, st);
-    if (g.BN == 32) return launch_tma_t<32>(ctx, a, wt, st);
-    if (g.BN == 64) return launch_tma_t<64>(ctx, a, wt, st);
-    return 1;
+    switch (a.H) {
+    case 64: return launch_tma_t<64>(ctx, a, wt, st);
+    case 32: return launch_tma_t<32>(ctx, a, wt, st);
+    case 16: return launch_tma_t<16>(ctx, a, wt, st);
+    case 8: return launch_tma_t<8>(ctx, a, wt, st);
+    default: return 1;
+    }
 }
 
 int launch_halo_conv(hrebsd_ctx *ctx, const ConvArgs &a, cudaStream_t st)
@@ -636,7 +615,6 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
     const int P = N * res * res;
     hr_prof_begin(ctx, st);
     int e = launch_tma_conv(ctx, a, wt, st);
-    if (e == 1) e = launch_tc_conv(ctx, a, st);
     if (e == 1) e = launch_halo_conv(ctx, a, st);
     if (e == 1) {   // no halo variant for this shape: pipelined implicit GEMM
         // output-channel tile: the largest of 64, 32, 16 that divides cout

@@ -1,15 +1,6 @@
-// 3x3 convolution on the fifth-generation tensor cores (tcgen05): the
-// implicit GEMM of conv3x3_kernel (128 output pixels x BN output channels per
-// CTA, K = 9 taps x cin walked in k-steps of 16 channels of one tap, STAGES
-// cp.async stages of KS k-steps) with the MMAs issued by one thread from
-// shared-memory descriptors into an FP32 accumulator in tensor memory.
-//
-// Shared layout of a k-step: the A rows (shifted input pixels) and B rows
-// (weights) in the K-major core-matrix layout: row r, 8-channel group g at
-// base + g * plane + 16 r (plane = rows x 16 bytes).  A stage is reused only
-// after the MMAs that read it have completed (one mbarrier per stage, armed by
-// tcgen05.commit).  Every wait is bounded; a wait that gives up sets the error
-// flag and the CTA skips its epilogue.
+// 3x3 convolutions of the learned initialiser on the fifth-generation tensor
+// cores (tcgen05): input halo tiles by TMA, MMAs issued by one thread from
+// shared-memory descriptors into FP32 accumulators in tensor memory.
 #pragma once
 
 #include "cnn_kernels.cuh"
@@ -17,278 +8,257 @@
 
 namespace hr_cnn {
 
-template <int BN, int KS, int STAGES>
-struct TcConv {
-    static constexpr int BM = 128;
-    static constexpr uint32_t A_PLANE = BM * 16, B_PLANE = BN * 16;
-    static constexpr uint32_t STEP = 2 * A_PLANE + 2 * B_PLANE;   // one k-step: 16 channels of A and B
-    static constexpr uint32_t STAGE = KS * STEP;
-    static constexpr uint32_t SMEM = STAGES * STAGE;
-    static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;      // power of two >= 32
+// ------------------------------------------------------------------ halo tiles by TMA
+// 3x3 convolution on tcgen05 with the input halo loaded once per tile.  A tile
+// is TI images x Ht rows x all W columns of the output, for BN output channels.
+// The input window (Ht + 2 rows, W + 2 columns, zero outside the image) of CW
+// channels (16, 32 or 64) is one TMA box, stored as a flat run of pixels
+// [image][row][column] of CW x 2 bytes each in the matching 32/64/128-byte
+// swizzled layout.  In this flat order the input of tap (dy, dx) for the output
+// at flat index q is at q + dy (W + 2) + dx, so the A operand of a tap is the
+// run shifted by a constant number of rows: one shared-memory descriptor per
+// (tap, 128-row block, 16-channel step), no copy.  Rows q whose column is W or
+// W + 1 (or that lie past the tile) are computed, never stored.  The weights of
+// a 16-channel step are laid out on the host side as [half][tap][BN][8] (no
+// swizzle) and arrive by one bulk copy with the box.
+//
+// Persistent and warp-specialised (320 threads, one CTA per SM): warp 0 lane 0
+// streams (tile, box) copies through a ring of `nst` shared-memory stages;
+// warp 1 lane 0 issues 9 x nM MMAs of 128 x BN x 16 per 16-channel step into
+// one of two accumulators in tensor memory and releases each stage with
+// tcgen05.commit; warps 2-9 read the finished accumulator (two warps per TMEM
+// lane quadrant, alternate 128-row blocks), add the bias, apply ReLU, store
+// BF16 and hand the accumulator back, so that the epilogue of one tile
+// overlaps the MMAs of the next.  Every
+// wait is bounded and also gives up when another role has given up; the CTA
+// then stores nothing more and sets the error flag.
+// Tile geometry per image size (compile-time, shared by host and kernel): Ht
+// output rows of TI images per tile, BN output channels; NM 128-row MMA blocks
+// cover the tile's last stored flat row; PR rows per box buffer cover the box
+// and the furthest row an MMA reads; two accumulators of ACC TMEM columns.
+template <int RES>
+struct TmaGeom {
+    static constexpr int Ht = RES >= 16 ? 16 : 8;
+    static constexpr int TI = RES >= 16 ? 1 : 5;
+    static constexpr int BN = RES >= 64 ? 16 : (RES >= 32 ? 32 : 64);
+    static constexpr int Wp = RES + 2, Rimg = (Ht + 2) * Wp;
+    static constexpr int QN = (TI - 1) * Rimg + (Ht - 1) * Wp + RES;
+    static constexpr int NM = (QN + 127) / 128;
+    static constexpr int ROWS = TI * Rimg > NM * 128 + 2 * Wp + 2 ? TI * Rimg : NM * 128 + 2 * Wp + 2;
+    static constexpr int PR = (ROWS + 7) / 8 * 8;
+    static constexpr int ACC = NM * BN <= 32 ? 32 : NM * BN <= 64 ? 64 : NM * BN <= 128 ? 128 : 256;
+    static constexpr int TMEM = 2 * ACC;
+    static constexpr int EM = (NM + 1) / 2;   // row blocks per epilogue warp
+    static_assert(NM * BN <= 256 && RES % Ht == 0 && Wp <= 256 && Ht + 2 <= 256, "tile geometry");
 };
 
-template <int BN, int KS, int STAGES>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(ConvArgs a, int *err)
-{
-    using G = TcConv<BN, KS, STAGES>;
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ uint32_t tmem_base;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int P = a.N * a.H * a.W;
-    const int p0 = blockIdx.x * G::BM, o0 = blockIdx.y * BN;
-    // loader: A row tid (one output pixel), both 8-channel halves; B rows tid / 2 (half tid % 2) for tid < 2 BN
-    const int lp = p0 + tid;
-    int pn = 0, py = 0, px = 0;
-    if (lp < P) {
-        pn = lp / (a.H * a.W);
-        const int rem = lp - pn * a.H * a.W;
-        py = rem / a.W;
-        px = rem - py * a.W;
-    }
-    const int lo = o0 + (tid >> 1), bhalf = tid & 1;
-    const int ncb = a.cin / 16, KT = 9 * ncb, nstage = (KT + KS - 1) / KS;
-    auto load_stage = [&](int s) {
-        unsigned char *base = tc_smem + (s % STAGES) * G::STAGE;
-#pragma unroll
-        for (int j = 0; j < KS; ++j) {
-            const int kt = s * KS + j;
-            const int tap = kt / ncb, cb = kt - tap * ncb;
-            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-            const bool oka = kt < KT && lp < P && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            unsigned char *st = base + j * G::STEP;
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const bf16 *src = oka ? a.x + ((size_t)(pn * a.H + yy) * a.W + xx) * a.xs + a.xo + cb * 16 + hh * 8 : a.x;
-                cp_async16(st + hh * G::A_PLANE + tid * 16, src, oka ? 16 : 0);
-            }
-            if (tid < 2 * BN) {
-                const bool okb = kt < KT && lo < a.cout;
-                const bf16 *src = okb ? a.w + ((size_t)lo * 9 + tap) * a.cin + cb * 16 + bhalf * 8 : a.w;
-                cp_async16(st + 2 * G::A_PLANE + bhalf * G::B_PLANE + (tid >> 1) * 16, src, okb ? 16 : 0);
-            }
-        }
-    };
-    if (tid == 0) {
-        for (int i = 0; i < STAGES; ++i) hr_tma::mbar_init(&bar[i], 1);
-        hr_tma::fence_mbar_init();
-    }
-    if (warp == 0) hr_tc::tmem_alloc(&tmem_base, G::TMEM_COLS);
-#pragma unroll
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nstage) load_stage(s);
-        cp_async_commit();
-    }
-    hr_tc::fence_before_sync();
-    __syncthreads();
-    hr_tc::fence_after_sync();
-    const uint32_t tb = tmem_base;
-    constexpr uint32_t idesc = hr_tc::idesc_bf16(128, BN);
-    bool ok = true;
-    for (int s = 0; s < nstage; ++s) {
-        cp_async_wait<STAGES - 2>();
-        hr_tma::fence_proxy_async();   // this thread's cp.async data -> visible to the tensor cores
-        __syncthreads();
-        if (tid == 0) {
-            hr_tc::fence_after_sync();
-            const uint32_t sb = hr_tma::smem_u32(tc_smem + (s % STAGES) * G::STAGE);
-#pragma unroll
-            for (int j = 0; j < KS; ++j) {
-                const uint32_t st = sb + j * G::STEP;
-                hr_tc::mma_bf16(tb, hr_tc::smem_desc(st, G::A_PLANE, 128),
-                                hr_tc::smem_desc(st + 2 * G::A_PLANE, G::B_PLANE, 128), idesc, (s | j) != 0);
-            }
-            hr_tc::commit(&bar[s % STAGES]);
-        }
-        // the buffer of stage s + STAGES - 1 was read by the MMAs of stage s - 1
-        const int nx = s + STAGES - 1;
-        if (nx < nstage) {
-            if (s >= 1) ok = hr_tma::mbar_wait(&bar[(s - 1) % STAGES], ((s - 1) / STAGES) & 1) && ok;
-            load_stage(nx);
-        }
-        cp_async_commit();
-    }
-    // the last commit covers every MMA of this CTA
-    ok = hr_tma::mbar_wait(&bar[(nstage - 1) % STAGES], ((nstage - 1) / STAGES) & 1) && ok;
-    ok = __syncthreads_and(ok);
-    cp_async_wait<0>();
-    hr_tc::fence_after_sync();
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-    } else {
-        const int p = p0 + warp * 32 + (tid & 31);   // TMEM lane = A row = output pixel
-#pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float v[16];
-            hr_tc::ld16(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (p < P) {
-#pragma unroll
-                for (int i = 0; i < 16; i += 2) {
-                    const int o = o0 + c0 + i;
-                    if (o >= a.cout) continue;
-                    float v0 = v[i], v1 = v[i + 1];
-                    if (a.bias) {
-                        v0 += a.bias[o];
-                        v1 += a.bias[o + 1];
-                    }
-                    if (a.relu) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
-                    }
-                    const size_t off = (size_t)p * a.ys + a.yo + o;
-                    if (a.y_fp32) {
-                        *reinterpret_cast<float2 *>(reinterpret_cast<float *>(a.y) + off) = make_float2(v0, v1);
-                    } else {
-                        *reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<bf16 *>(a.y) + off) =
-                            __floats2bfloat162_rn(v0, v1);
-                    }
-                }
-            }
-        }
-    }
-    hr_tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) hr_tc::tmem_dealloc(tb, G::TMEM_COLS);
-}
-
-// ------------------------------------------------------------------ halo tiles by TMA
-// 3x3 convolution on tcgen05 with the input halo loaded once per tile.  The
-// CTA computes a tile of TI images x Ht rows x all W columns of the output, for
-// BN output channels.  The input window (Ht + 2 rows, W + 2 columns, zero
-// outside the image) of each 8-channel group is one TMA box, stored as a flat
-// run of pixels [image][row][column] of 16 bytes each ("plane").  In this
-// flat order the input of tap (dy, dx) for the output at flat index q is at
-// q + dy (W + 2) + dx, so the A operand of a tap is the plane's rows shifted by
-// a constant: one shared-memory descriptor per (tap, 128-row block), no copy.
-// Rows q whose column is W or W + 1 (or whose row lies past the tile) are
-// computed but never stored.  The weights of a 16-channel chunk are laid out on
-// the host side as [half][tap][BN][8] and arrive by one bulk copy.
-//
-// Roles: thread 0 issues the copies of chunk c into stage c % nst once the MMAs
-// that read the stage before have completed (mbarrier `empty`, armed by
-// tcgen05.commit); thread 32 waits for the copies (mbarrier `full`, transaction
-// bytes), issues 9 x nM MMAs of 128 x BN x 16 into nM accumulators in tensor
-// memory, and commits; after the last chunk all four warps read their TMEM
-// lanes, add the bias, apply ReLU and store BF16.  Waits are bounded; a wait
-// that gives up sets the error flag and the CTA skips its stores.
 struct TmaConvArgs {
     const bf16 *wt;      // [cout / BN][cin / 16][2][9][BN][8]
     const float *bias;   // [cout] or null
     bf16 *y;             // output (NHWC, channel stride ys, offset yo)
     int ys, yo, relu;
-    int cin, cout, N, res;
-    int Ht, TI, nM, PR;  // tile rows, images per tile, 128-row MMA blocks, rows per plane
-    int nst;             // pipeline stages in use (<= 3)
-    int tmem_cols;
+    int cin, cout, N;
+    int cw;              // channels per box (16, 32 or 64)
+    int a_bytes;         // bytes of a box buffer (multiple of 1024)
+    int stage_bytes;     // box buffer + weights of its 16-channel steps (multiple of 1024)
+    int nst;             // shared-memory stages in the ring (<= 8)
+    int ntiles;          // tiles x output-channel blocks
 };
 
-template <int BN>
-__global__ void __launch_bounds__(128) conv3x3_tma_tc_kernel(const __grid_constant__ CUtensorMap tmX, TmaConvArgs a,
-                                                            int *err)
+namespace tmaconv {
+
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, volatile int *abort)
 {
-    constexpr int MAXST = 3;
-    constexpr uint32_t B_BYTES = 9 * BN * 32;
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], done;
+    for (uint32_t i = 0; i < hr_tma::kSpinLimit; ++i) {
+        if (hr_tma::mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+struct Tile {
+    int cot, n0, y0;
+};
+template <int RES>
+__device__ __forceinline__ Tile tile_of(int t, int ncot)
+{
+    using G = TmaGeom<RES>;
+    constexpr int ty_tiles = RES / G::Ht;
+    const int sp = t / ncot;
+    return Tile{t - sp * ncot, (sp / ty_tiles) * G::TI, (sp % ty_tiles) * G::Ht};
+}
+
+}  // namespace tmaconv
+
+constexpr int kTmaConvThreads = 320;   // producer warp, MMA warp, 8 epilogue warps
+
+template <int RES>
+__global__ void __launch_bounds__(kTmaConvThreads, 1)
+    conv3x3_tma_tc_kernel(const __grid_constant__ CUtensorMap tmX, TmaConvArgs a, int *err)
+{
+    using G = TmaGeom<RES>;
+    constexpr int BN = G::BN, NM = G::NM, Wp = G::Wp, Rimg = G::Rimg;
+    constexpr int MAXST = 8;
+    constexpr uint32_t B_BYTES = 9 * BN * 32;   // weights of one 16-channel step
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], accf[2], acce[2], drain;
     __shared__ uint32_t tmem_base;
+    __shared__ int abort_s;
+    __shared__ float bias_s[256];
+    // swizzled boxes need 1024-byte aligned buffers: the host adds 1 KB of slack
+    unsigned char *tc_smem = tc_smem_raw + ((1024u - (hr_tma::smem_u32(tc_smem_raw) & 1023u)) & 1023u);
+    volatile int *abort = &abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nchunk = a.cin / 16, nst = a.nst;
-    const int Wp = a.res + 2, Rimg = (a.Ht + 2) * Wp;
-    const uint32_t A_PL = (uint32_t)a.PR * 16, STAGE = 2 * A_PL + B_BYTES;
-    const uint32_t box_bytes = 16u * (uint32_t)(Rimg * a.TI);
-    const int ncot = a.cout / BN, ty_tiles = a.res / a.Ht;
-    const int cot = blockIdx.x % ncot, tile = blockIdx.x / ncot;
-    const int n0 = (tile / ty_tiles) * a.TI, y0 = (tile % ty_tiles) * a.Ht;
+    const int ksub = a.cw / 16, nbox = a.cin / a.cw, nst = a.nst, ncot = a.cout / BN;
+    const uint32_t RB = (uint32_t)a.cw * 2;   // bytes per pixel row of a box
+    const uint32_t STAGE = (uint32_t)a.stage_bytes;
+    const uint32_t box_bytes = RB * (uint32_t)(Rimg * G::TI);
     if (tid == 0) {
         for (int i = 0; i < nst; ++i) {
             hr_tma::mbar_init(&full[i], 1);
             hr_tma::mbar_init(&empty[i], 1);
         }
-        hr_tma::mbar_init(&done, 1);
+        for (int i = 0; i < 2; ++i) {
+            hr_tma::mbar_init(&accf[i], 1);
+            hr_tma::mbar_init(&acce[i], 8);
+        }
+        hr_tma::mbar_init(&drain, 1);
+        abort_s = 0;
         hr_tma::fence_mbar_init();
     }
-    if (warp == 0) hr_tc::tmem_alloc(&tmem_base, (uint32_t)a.tmem_cols);
+    for (int i = tid; i < a.cout; i += blockDim.x) bias_s[i] = a.bias ? a.bias[i] : 0.0f;
+    if (warp == 1) hr_tc::tmem_alloc(&tmem_base, (uint32_t)G::TMEM);
     hr_tc::fence_before_sync();
     __syncthreads();
     hr_tc::fence_after_sync();
     const uint32_t tb = tmem_base;
-    bool ok = true;
-    if (tid == 0) {
-        const bf16 *wsrc = a.wt + (size_t)cot * nchunk * (B_BYTES / 2);
-        for (int c = 0; c < nchunk; ++c) {
-            const int s = c % nst, k = c / nst;
-            if (k >= 1) ok = hr_tma::mbar_wait(&empty[s], (k - 1) & 1) && ok;
-            unsigned char *base = tc_smem + s * STAGE;
-            hr_tma::mbar_arrive_expect_tx(&full[s], 2 * box_bytes + B_BYTES);
-            hr_tma::load_4d(base, &tmX, &full[s], c * 16, -1, y0 - 1, n0);
-            hr_tma::load_4d(base + A_PL, &tmX, &full[s], c * 16 + 8, -1, y0 - 1, n0);
-            hr_tma::load_bulk(base + 2 * A_PL, wsrc + (size_t)c * (B_BYTES / 2), B_BYTES, &full[s]);
-        }
-    } else if (tid == 32) {
-        constexpr uint32_t idesc = hr_tc::idesc_bf16(128, BN);
-        for (int c = 0; c < nchunk; ++c) {
-            const int s = c % nst, k = c / nst;
-            ok = hr_tma::mbar_wait(&full[s], k & 1) && ok;
-            hr_tc::fence_after_sync();
-            const uint32_t sa = hr_tma::smem_u32(tc_smem + s * STAGE), sb = sa + 2 * A_PL;
-#pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const uint32_t off = (uint32_t)((t / 3) * Wp + t % 3) * 16;
-                const uint64_t bdesc = hr_tc::smem_desc(sb + t * BN * 16, 9 * BN * 16, 128);
-                for (int m = 0; m < a.nM; ++m)
-                    hr_tc::mma_bf16(tb + (uint32_t)(m * BN), hr_tc::smem_desc(sa + m * 2048 + off, A_PL, 128), bdesc,
-                                    idesc, (c | t) != 0);
-            }
-            hr_tc::commit(&empty[s]);
-        }
-        hr_tc::commit(&done);
-    }
-    ok = hr_tma::mbar_wait(&done, 0) && ok;
-    ok = __syncthreads_and(ok);
-    hr_tc::fence_after_sync();
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            // copies still in flight land before the CTA leaves (bounded)
-            for (int c = nchunk - nst < 0 ? 0 : nchunk - nst; c < nchunk; ++c)
-                (void)hr_tma::mbar_wait(&full[c % nst], (c / nst) & 1);
-        }
-    } else {
-        const int o0 = cot * BN;
-        for (int m = 0; m < a.nM; ++m) {
-            const int q = m * 128 + warp * 32 + lane;
-            const int nl = q / Rimg, rem = q - nl * Rimg, ty = rem / Wp, tx = rem - ty * Wp;
-            const bool valid = nl < a.TI && ty < a.Ht && tx < a.res && n0 + nl < a.N;
-            const size_t p = ((size_t)(n0 + nl) * a.res + (y0 + ty)) * a.res + tx;
-#pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                hr_tc::ld16(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * BN + c0), v);
-                if (valid) {
-                    __align__(16) __nv_bfloat162 o2[8];
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2) {
-                        float v0 = v[i], v1 = v[i + 1];
-                        if (a.bias) {
-                            v0 += a.bias[o0 + c0 + i];
-                            v1 += a.bias[o0 + c0 + i + 1];
-                        }
-                        if (a.relu) {
-                            v0 = fmaxf(v0, 0.0f);
-                            v1 = fmaxf(v1, 0.0f);
-                        }
-                        o2[i / 2] = __floats2bfloat162_rn(v0, v1);
-                    }
-                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + p * a.ys + a.yo + o0 + c0);
-                    dst[0] = *reinterpret_cast<const uint4 *>(&o2[0]);
-                    dst[1] = *reinterpret_cast<const uint4 *>(&o2[4]);
+    if (warp == 0) {
+        if (lane == 0) {   // producer
+            int it = 0;
+            for (int t = blockIdx.x; t < a.ntiles && !*abort; t += gridDim.x) {
+                const tmaconv::Tile T = tmaconv::tile_of<RES>(t, ncot);
+                const bf16 *wsrc = a.wt + (size_t)T.cot * (a.cin / 16) * (B_BYTES / 2);
+                for (int c = 0; c < nbox; ++c, ++it) {
+                    const int s = it % nst, k = it / nst;
+                    if (k >= 1 && !tmaconv::wait(&empty[s], (k - 1) & 1, abort)) break;
+                    unsigned char *base = tc_smem + s * STAGE;
+                    hr_tma::mbar_arrive_expect_tx(&full[s], box_bytes + ksub * B_BYTES);
+                    hr_tma::load_4d(base, &tmX, &full[s], c * a.cw, -1, T.y0 - 1, T.n0);
+                    hr_tma::load_bulk(base + a.a_bytes, wsrc + (size_t)c * ksub * (B_BYTES / 2), ksub * B_BYTES,
+                                      &full[s]);
                 }
             }
+            if (*abort) {   // copies still in flight land before the CTA leaves (bounded)
+                for (int j = it - nst < 0 ? 0 : it - nst; j < it; ++j)
+                    (void)hr_tma::mbar_wait(&full[j % nst], (j / nst) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = hr_tc::idesc_bf16(128, BN);
+            // descriptors are linear in the start address (field = address >> 4, no carry for
+            // addresses below 256 KB): per stage one base, per MMA one add
+            uint32_t toff[9];
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) toff[tap] = ((uint32_t)((tap / 3) * Wp + tap % 3) * RB) >> 4;
+            const uint32_t mstep = (128u * RB) >> 4;
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < a.ntiles && !*abort; t += gridDim.x, ++i) {
+                const int b = i & 1, u = i >> 1;
+                if (u >= 1 && !tmaconv::wait(&acce[b], (u - 1) & 1, abort)) break;
+                hr_tc::fence_after_sync();
+                const uint32_t d = tb + (uint32_t)(b * G::ACC);
+                for (int c = 0; c < nbox; ++c, ++it) {
+                    const int s = it % nst, k = it / nst;
+                    if (!tmaconv::wait(&full[s], k & 1, abort)) break;
+                    hr_tc::fence_after_sync();
+                    const uint32_t sa = hr_tma::smem_u32(tc_smem + s * STAGE);
+                    const uint64_t a0 = hr_tc::smem_desc_swz(sa, RB);
+                    const uint64_t b0 = hr_tc::smem_desc(sa + (uint32_t)a.a_bytes, 9 * BN * 16, 128);
+                    for (int kk = 0; kk < ksub; ++kk) {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const uint64_t at = a0 + (toff[tap] + 2u * kk);
+                            const uint64_t bt = b0 + ((kk * B_BYTES + tap * BN * 16) >> 4);
+                            const uint32_t acc = (c | kk | tap) != 0;
+#pragma unroll
+                            for (int m = 0; m < NM; ++m)
+                                hr_tc::mma_bf16(d + (uint32_t)(m * BN), at + m * mstep, bt, idesc, acc);
+                        }
+                    }
+                    hr_tc::commit(&empty[s]);
+                }
+                hr_tc::commit(&accf[b]);
+            }
+        }
+    } else {   // epilogue: warps 2..9; TMEM lane quadrant warp % 4, 128-row blocks m = (warp - 2) / 4 (mod 2)
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        // the flat row -> pixel decode is the same for every tile: once per thread
+        int prel[G::EM], pnl[G::EM];
+#pragma unroll
+        for (int j = 0; j < G::EM; ++j) {
+            const int m = 2 * j + half;
+            const int q = m * 128 + quad * 32 + lane;
+            const int nl = q / Rimg, rem = q - nl * Rimg, ty = rem / Wp, tx = rem - ty * Wp;
+            const bool ok = m < NM && nl < G::TI && ty < G::Ht && tx < RES;
+            prel[j] = ok ? (nl * RES + ty) * RES + tx : -1;
+            pnl[j] = nl;
+        }
+        int i = 0;
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++i) {
+            const int b = i & 1, u = i >> 1;
+            const bool got = tmaconv::wait(&accf[b], u & 1, abort);
+            if (!__all_sync(0xffffffffu, got)) break;
+            hr_tc::fence_after_sync();
+            const tmaconv::Tile T = tmaconv::tile_of<RES>(t, ncot);
+            const int o0 = T.cot * BN;
+            const size_t pbase = ((size_t)T.n0 * RES + T.y0) * RES;
+            const uint32_t d = tb + (uint32_t)(b * G::ACC) + ((uint32_t)(quad * 32) << 16);
+#pragma unroll
+            for (int j = 0; j < G::EM; ++j) {
+                const int m = 2 * j + half;
+                if (m >= NM) break;
+                float v[BN];
+#pragma unroll
+                for (int c0 = 0; c0 < BN; c0 += 16) hr_tc::ld16_async(d + (uint32_t)(m * BN + c0), &v[c0]);
+                hr_tc::wait_ld();
+                if (prel[j] >= 0 && T.n0 + pnl[j] < a.N) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(a.y + (pbase + prel[j]) * a.ys + a.yo + o0);
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += 8) {
+                        __align__(16) __nv_bfloat162 o2[4];
+#pragma unroll
+                        for (int k = 0; k < 8; k += 2) {
+                            float v0 = v[c0 + k] + bias_s[o0 + c0 + k], v1 = v[c0 + k + 1] + bias_s[o0 + c0 + k + 1];
+                            if (a.relu) {
+                                v0 = fmaxf(v0, 0.0f);
+                                v1 = fmaxf(v1, 0.0f);
+                            }
+                            o2[k / 2] = __floats2bfloat162_rn(v0, v1);
+                        }
+                        dst[c0 / 8] = *reinterpret_cast<const uint4 *>(o2);
+                    }
+                }
+            }
+            hr_tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) hr_tma::mbar_arrive(&acce[b]);
         }
     }
+    // an MMA thread that gave up may leave MMAs in flight: let them finish before TMEM is freed
     hr_tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) hr_tc::tmem_dealloc(tb, (uint32_t)a.tmem_cols);
+    if (*abort) {
+        if (tid == 32) {
+            hr_tc::commit(&drain);   // arrives once every MMA issued so far has completed
+            (void)hr_tma::mbar_wait(&drain, 0);
+        }
+        if (tid == 0) atomicExch(err, 1);
+        __syncthreads();
+    }
+    hr_tc::fence_after_sync();
+    if (warp == 1) hr_tc::tmem_dealloc(tb, (uint32_t)G::TMEM);
 }
 
 }  // namespace hr_cnn

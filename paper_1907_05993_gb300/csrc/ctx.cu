@@ -292,11 +292,20 @@ int hr_encode_tmap_3d(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d
 }
 
 int hr_encode_tmap_bf16_4d(CUtensorMap *tm, const void *base, const uint64_t dims[4], const uint64_t strides[3],
-                           const uint32_t box[4])
+                           const uint32_t box[4], int swizzle_bytes)
 {
     hr_encode_tiled_fn fn = encode_fn();
     if (!fn) return -1;
     if ((reinterpret_cast<uintptr_t>(base) & 15) || ((box[0] * 2) & 15)) return -1;
+    CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_NONE;
+    if (swizzle_bytes) {
+        if ((int)box[0] * 2 != swizzle_bytes) return -1;
+        sw = swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+             : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+             : swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                    : CU_TENSOR_MAP_SWIZZLE_NONE;
+        if (sw == CU_TENSOR_MAP_SWIZZLE_NONE) return -1;
+    }
     for (int i = 0; i < 3; ++i)
         if (strides[i] & 15) return -1;
     for (int i = 0; i < 4; ++i)
@@ -306,7 +315,7 @@ int hr_encode_tmap_bf16_4d(CUtensorMap *tm, const void *base, const uint64_t dim
     cuuint32_t bx[4] = {box[0], box[1], box[2], box[3]};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), d, st, bx, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -1;
 }

@@ -67,7 +67,7 @@ struct hrebsd_ctx {
     int no_events = 0;   // set while a call must not create CUDA events
     int no_tma = 0;      // force the non-TMA demons iteration (testing, unsupported shapes)
     int graphs = 1;      // replay each registration level from a cached CUDA graph
-    int cnn_tc = 0;      // learned initialiser: 3x3 convolutions on tcgen05 (else mma.sync kernels)
+    int cnn_tc = 1;      // learned initialiser: forward 3x3 convolutions on tcgen05 (else mma.sync kernels)
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
     std::vector<hr_graph_entry> graph_cache;
     unsigned long long graph_clock = 0;

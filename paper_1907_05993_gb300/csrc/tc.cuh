@@ -30,6 +30,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
+// Descriptor of a K-major operand in a swizzled layout: rows of `row_bytes`
+// (32, 64 or 128 = the swizzle span) whose 16-byte chunks are XOR-permuted by
+// the row's position in its 8-row atom, as TMA writes them; sbo = 8 rows.
+// The start may be any row (and any 32-byte K step inside a row) with the base
+// offset field left at zero: the permutation follows the absolute shared-memory
+// address bits, as TMA applies it (measured on sm_103a for all three spans and
+// row shifts 0-133).
+__device__ __forceinline__ uint64_t smem_desc_swz(uint32_t saddr, uint32_t row_bytes)
+{
+    const uint64_t mode = row_bytes == 128 ? 2 : (row_bytes == 64 ? 4 : 6);
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                                 // leading offset: unused for K-major swizzled
+    d |= (uint64_t)(((8 * row_bytes) >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= mode << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
@@ -88,5 +106,22 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16])
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// As ld16 without the wait: several loads may be in flight before wait_ld().
+__device__ __forceinline__ void ld16_async(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 }  // namespace hr_tc

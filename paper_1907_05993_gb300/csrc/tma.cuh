@@ -55,6 +55,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Plain arrival (no transaction bytes).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bounded wait for phase `parity`; false if the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
@@ -101,7 +107,8 @@ int hr_encode_tmap_3d(CUtensorMap *tm, const void *base, uint64_t d0, uint64_t d
                       uint64_t s2, uint32_t b0, uint32_t b1, uint32_t b2);
 
 // Host: encode a 4-D BF16 tiled tensor map (dims innermost first, byte strides
-// of dims 1..3, box b0..b3; out-of-range elements read as zero).  Same return
-// convention as hr_encode_tmap_3d.
+// of dims 1..3, box b0..b3; out-of-range elements read as zero).  swizzle_bytes
+// 0 (none), 32, 64 or 128: the box's inner extent must then equal it.  Same
+// return convention as hr_encode_tmap_3d.
 int hr_encode_tmap_bf16_4d(CUtensorMap *tm, const void *base, const uint64_t dims[4], const uint64_t strides[3],
-                           const uint32_t box[4]);
+                           const uint32_t box[4], int swizzle_bytes = 0);

@@ -110,9 +110,10 @@ def test_training_reduces_loss(env):
 
 
 def test_tcgen05_convolutions_match_oracle_and_mma_path(env):
-    """HREBSD_OPT_CNN_TC: every 3x3 convolution (forward and input gradient) on tcgen05 MMAs
-    into tensor memory; same bars against the oracle, and close to the mma.sync path."""
+    """HREBSD_OPT_CNN_TC on (the default): forward 3x3 convolutions on tcgen05 MMAs into tensor
+    memory fed by TMA halo tiles; same bars against the oracle, and close to the mma.sync path."""
     torch, P, CP, OC, ctx0 = env
+    P.hrebsd_set_option(ctx0, P.OPT_CNN_TC, 0)
     ctx = P.hrebsd_create(0)
     P.hrebsd_set_option(ctx, P.OPT_CNN_TC, 1)
     try:
@@ -131,6 +132,19 @@ def test_tcgen05_convolutions_match_oracle_and_mma_path(env):
         scale = np.abs(exp).max()
         assert np.abs(outs[0] - exp).max() <= 0.02 * scale
         assert np.abs(outs[0] - outs[1]).max() <= 0.02 * scale
+        # a batch with more tiles than CTAs at every level (persistent loop, both accumulators, ragged
+        # last group of 8x8 images): same result as the mma.sync path
+        xg2 = torch.from_numpy(rng.normal(size=(523, 2, 64, 64)).astype(np.float32)).cuda().to(torch.bfloat16)
+        big = []
+        for c in (ctx, ctx0):
+            out = torch.empty((523, 2, 64, 64), device="cuda")
+            P.hrebsd_cnn_infer(c, xg2, 523, out)
+            P.hrebsd_device_error(c)
+            big.append(out.cpu().numpy())
+        sc2 = np.abs(big[1]).max()
+        assert np.isfinite(big[0]).all()
+        assert np.abs(big[0] - big[1]).max() <= 0.02 * sc2
+        assert np.abs(big[0] - big[1]).mean() <= 1e-3 * sc2
         # gradients
         p3 = _params(OC, 3)
         v3 = CP.pack(p3)
@@ -153,4 +167,5 @@ def test_tcgen05_convolutions_match_oracle_and_mma_path(env):
             den = np.linalg.norm(g_exp[k]) + 1e-30
             assert num <= 0.05 * den, (k, num / den)
     finally:
+        P.hrebsd_set_option(ctx0, P.OPT_CNN_TC, 1)
         P.hrebsd_destroy(ctx)
