@@ -629,6 +629,55 @@ def run_single(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ learned initialiser alone (a10)
+def run_cnn(args, rank, world, local_rank):
+    """U-Net inference of the learned initialiser alone: --pairs pairs of 64x64 (reference, test)
+    BF16 inputs, He-normal weights; forward on the tcgen05 convolutions (the default) and on the
+    mma.sync kernels.  The timed region is device work only (inputs resident)."""
+    import torch
+    import paper_1907_05993_gb300 as P
+    from paper_1907_05993_gb300 import learned as LN
+    torch.cuda.set_device(local_rank)
+    B = args.pairs
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn((B, 2, 64, 64), device="cuda", generator=g).to(torch.bfloat16)
+    out = torch.empty((B, 2, 64, 64), device="cuda")
+    # 2 x MACs per pair: 3x3 layers (input channels padded to 16) + the 1x1 head
+    layers = [(16, 16, 64), (16, 16, 64), (16, 32, 32), (32, 32, 32), (32, 64, 16), (64, 64, 16), (64, 128, 8),
+              (128, 128, 8), (192, 64, 16), (64, 64, 16), (96, 32, 32), (32, 32, 32), (48, 16, 64), (16, 16, 64)]
+    flop = sum(2 * 9 * ci * co * r * r for ci, co, r in layers) + 2 * 16 * 2 * 64 * 64
+    res = {}
+    for tc in (1, 0):
+        ctx = P.hrebsd_create(local_rank)
+        P.hrebsd_set_option(ctx, P.OPT_CNN_TC, tc)
+        P.hrebsd_cnn_init(ctx, LN.init_params(0))
+        for _ in range(max(3, args.warmup)):
+            P.hrebsd_cnn_infer(ctx, x, B, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = P.hrebsd_launch_count(ctx)
+        e0.record()
+        for _ in range(args.steps):
+            P.hrebsd_cnn_infer(ctx, x, B, out)
+        e1.record()
+        torch.cuda.synchronize()
+        P.hrebsd_device_error(ctx)
+        ms = e0.elapsed_time(e1) / args.steps
+        res[tc] = (ms, (P.hrebsd_launch_count(ctx) - l0) / args.steps)
+        P.hrebsd_destroy(ctx)
+    line = {"metric": "learned-initialiser inference pairs/s", "workload": "cnn", "value": B / (res[1][0] / 1e3),
+            "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "higher_is_better": True,
+            "data": "synthetic (random BF16 inputs, He-normal weights)", "dtype": "bf16 (FP32 accumulation)",
+            "config": {"workload": f"U-Net 16-32-64-128 inference, {B} pairs of 64x64",
+                       "gflop_per_pair": flop / 1e9},
+            "ms_per_step": res[1][0], "tflops": flop * B / (res[1][0] / 1e3) / 1e12, "gpu_launches": res[1][1],
+            "mma_sync": {"ms_per_step": res[0][0], "pairs_per_s": B / (res[0][0] / 1e3),
+                         "tflops": flop * B / (res[0][0] / 1e3) / 1e12}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ large patterns (f4)
 def run_large(args, rank, world, local_rank):
     """1024 x 1024 patterns (the paper's 1244 x 1024 simulations cut to a width the 7-level pyramid
@@ -677,7 +726,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=48)
     ap.add_argument("--ref-sample", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("scan", "learned", "compare", "large", "single"), default="scan")
+    ap.add_argument("--workload", choices=("scan", "learned", "compare", "large", "single", "cnn"),
+                    default="scan")
     ap.add_argument("--large-pairs", type=int, default=512)
     ap.add_argument("--compare-orientations", type=int, default=16)
     ap.add_argument("--train-pairs", type=int, default=200_000)
@@ -701,6 +751,8 @@ def main():
         return run_large(args, rank, world, local_rank)
     if args.workload == "single":
         return run_single(args, rank, world, local_rank)
+    if args.workload == "cnn":
+        return run_cnn(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 
