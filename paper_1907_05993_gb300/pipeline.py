@@ -2,9 +2,10 @@
 
 ``Pipeline.run`` calls, in order: hrebsd_autotune (first batch of a size
 only), hrebsd_preprocess_batch (references and tests), hrebsd_demons_register_batch, hrebsd_fit_rotation, hrebsd_remap,
-hrebsd_xcf_roi_batch and hrebsd_solve_F, all on one stream.  This module
-only allocates the output tensors and passes pointers; every step runs in
-the CUDA library.
+hrebsd_xcf_roi_batch and hrebsd_solve_F, all on one stream.  ``Pipeline.run_host``
+takes pinned host inputs and overlaps their copy with the processing, slice
+by slice.  This module only allocates the output tensors and passes
+pointers; every step runs in the CUDA library.
 """
 from __future__ import annotations
 
@@ -56,6 +57,7 @@ class Pipeline:
         self.roi = torch.as_tensor(np.ascontiguousarray(cfg.roi_xy, dtype=np.int32), device=self.dev)
         self.N = int(cfg.roi_xy.shape[0])
         self._bufs = {}
+        self._copy_stream = None
         self._tuned = {}
 
     def close(self):
@@ -148,6 +150,60 @@ class Pipeline:
         hrebsd_xcf_roi_batch(self.ctx, rem, test_p, B, H, W, self.roi, N, c.S, c.window, q, peak, ph, tie, stream)
         F = get("F", (B, 9), t.float64)
         hrebsd_solve_F(self.ctx, q, self.roi, N, B, H, W, self.geom, Rf, F, status, stream)
+        return o
+
+    def run_host(self, refs_host, tests_host, ref_idx_host, chunks=4, out=None):
+        """Host-resident inputs: refs [R,H,W] and tests [B,H,W] float32, ref_idx [B] int32, in pinned CPU
+        memory.  The batch runs through ``run`` as ``chunks`` consecutive slices on the current stream;
+        the host -> device copy of slice k + 1 runs on a side stream while slice k is processed, and
+        F, R_finite (FP64 [B, 9]) and status ([B]) of every slice are copied into pinned host tensors,
+        returned in a dict (valid once the current stream has synchronised).  Each pair's result is
+        the one ``run`` gives on the whole batch (pairs are independent); the static background,
+        a statistic of the whole batch, needs chunks=1."""
+        t = self.torch
+        if self.cfg.static_background and chunks > 1:
+            raise ValueError("the static background is a whole-batch statistic: use chunks=1")
+        B, H, W = tests_host.shape
+        R = refs_host.shape[0]
+        n = -(-B // max(1, chunks))
+        nk = -(-B // n)
+        cs = t.cuda.current_stream(self.dev)
+        if self._copy_stream is None:
+            self._copy_stream = t.cuda.Stream(self.dev)
+        xs = self._copy_stream
+        d_refs = self._buf("host_refs", (R, H, W), t.float32)
+        d_refs.copy_(refs_host, non_blocking=True)
+        slots = [(self._buf(f"host_tests{k}", (n, H, W), t.float32), self._buf(f"host_idx{k}", (n,), t.int32))
+                 for k in range(2)]
+        o = {} if out is None else out
+        for name, shape, dtype in (("F", (B, 9), t.float64), ("R_finite", (B, 9), t.float64),
+                                   ("status", (B,), t.int32)):
+            if name not in o or tuple(o[name].shape) != shape or o[name].is_cuda:
+                o[name] = t.empty(shape, dtype=dtype).pin_memory()
+        copied = [t.cuda.Event(), t.cuda.Event()]
+        freed = [None, None]
+
+        def issue_copy(k):
+            sl, a, b = k % 2, k * n, min(B, (k + 1) * n)
+            with t.cuda.stream(xs):
+                if freed[sl] is not None:   # the slice two back is done with this staging slot
+                    xs.wait_event(freed[sl])
+                slots[sl][0][: b - a].copy_(tests_host[a:b], non_blocking=True)
+                slots[sl][1][: b - a].copy_(ref_idx_host[a:b], non_blocking=True)
+                copied[sl].record(xs)
+
+        issue_copy(0)
+        for k in range(nk):
+            sl, a, b = k % 2, k * n, min(B, (k + 1) * n)
+            if k + 1 < nk:
+                issue_copy(k + 1)
+            cs.wait_event(copied[sl])
+            r = self.run(d_refs, slots[sl][0][: b - a], slots[sl][1][: b - a])
+            ev = t.cuda.Event()
+            ev.record(cs)
+            freed[sl] = ev
+            for name in ("F", "R_finite", "status"):
+                o[name][a:b].copy_(r[name], non_blocking=True)
         return o
 
     def strain_stress(self, out, g, ref_idx, tilt_rad, stiffness=NI_STIFFNESS, traction_free=True, stream=None):

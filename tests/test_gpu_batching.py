@@ -118,3 +118,22 @@ def test_graphs_on_a_side_stream(torch, lib, pairs):
     s.synchronize()
     assert np.array_equal(field.cpu().numpy(), base[0])
     lib.hrebsd_destroy(ctx)
+
+
+def test_run_host_matches_run(torch, lib):
+    """Pinned host inputs processed in slices with overlapped copies (3 slices of 2, 2 and 1 pairs,
+    staging slots reused): the same F, rotation and status as one run on the whole batch."""
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    spec = K.ScanSpec(n_pairs=5, H=128, W=128, n_refs=2, mis_lo_deg=0.5, mis_hi_deg=4.0, seed=5)
+    refs, tests, ridx, _ = K.make_scan(spec)
+    roi = K.roi_grid(128, 128, 32, True)
+    pipe = Pipeline(PipelineConfig(128, 128, roi, 32, 3, (40, 40, 40), stop_tol=1e-4, stop_window=5))
+    whole = pipe.run(torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(), torch.from_numpy(ridx).cuda())
+    exp = {k: whole[k].cpu().numpy().copy() for k in ("F", "R_finite", "status")}
+    h = pipe.run_host(torch.from_numpy(refs).pin_memory(), torch.from_numpy(tests).pin_memory(),
+                      torch.from_numpy(ridx).pin_memory(), chunks=3)
+    torch.cuda.synchronize()
+    lib.hrebsd_device_error(pipe.ctx)
+    for k, v in exp.items():
+        assert np.array_equal(h[k].numpy(), v), k
+    pipe.close()
