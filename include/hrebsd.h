@@ -344,6 +344,14 @@ int hrebsd_ssim_warped(hrebsd_ctx *ctx, const float *ref, const int32_t *ref_idx
  * sets the flag read by hrebsd_device_error (D is then not written). */
 int hrebsd_tc_selftest(hrebsd_ctx *ctx, const uint16_t *A, const uint16_t *B, int N, int KS, float *D, void *stream);
 
+/* Failure-path self-test (no counterpart in the paper): one CTA on `stream`
+ * waits on an mbarrier that nothing completes, with the try-wait loop of the
+ * library's kernels limited to `max_polls` polls (1 .. 2^22); when the limit
+ * runs out it sets the flag that hrebsd_device_error reports as
+ * HREBSD_ETIMEOUT, and returns.  The context stays usable.  EINVAL for a
+ * limit outside the range. */
+int hrebsd_wait_selftest(hrebsd_ctx *ctx, unsigned max_polls, void *stream);
+
 /* Measurement helper (no counterpart in the paper): launch an FP32 FMA
  * throughput probe on `stream` (SMs x 8 CTAs of 256 threads, each thread 8
  * independent chains of packed FP32x2 FMAs, `iters` steps); *flops receives the

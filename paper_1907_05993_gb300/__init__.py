@@ -21,12 +21,12 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
+    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_wait_selftest", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
     "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
-ESCRATCH = -5
+ETIMEOUT, ESCRATCH = -4, -5
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -104,6 +104,7 @@ def load(build: bool = False):
         "hrebsd_probe_fp32_fma": (i, [vp, i, C.POINTER(C.c_double), vp]),
         "hrebsd_polar_batch": (i, [vp, vp, i, vp, vp]),
         "hrebsd_tc_selftest": (i, [vp, vp, vp, i, i, vp, vp]),
+        "hrebsd_wait_selftest": (i, [vp, C.c_uint, vp]),
         "hrebsd_bandpass_batch": (i, [vp, vp, i, i, i, C.c_float, C.c_float, vp, vp]),
         "hrebsd_mean_pattern": (i, [vp, vp, i, i, i, vp, vp]),
         "hrebsd_background_batch": (i, [vp, vp, i, i, i, vp, C.c_float, vp, vp]),
@@ -308,6 +309,10 @@ def hrebsd_tc_selftest(ctx, A, B, N, KS, D, stream=None):
     t = _t()
     _chk(load().hrebsd_tc_selftest(ctx, _p(A, t.bfloat16), _p(B, t.bfloat16), N, KS, _p(D, t.float32), _s(stream)),
          "hrebsd_tc_selftest")
+
+
+def hrebsd_wait_selftest(ctx, max_polls, stream=None):
+    _chk(load().hrebsd_wait_selftest(ctx, int(max_polls), _s(stream)), "hrebsd_wait_selftest")
 
 
 def hrebsd_polar_batch(ctx, F, B, R, stream=None):

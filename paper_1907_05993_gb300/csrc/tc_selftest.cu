@@ -1,4 +1,5 @@
-// Check of the tcgen05 building blocks (descriptors, MMA, commit, TMEM loads)
+// Self-tests: the bounded-wait failure path, and the tcgen05 building blocks
+// (descriptors, MMA, commit, TMEM loads)
 // on one GEMM tile: D[128][N] = A[128][K] B[N][K]^T, BF16 operands, FP32
 // accumulation in tensor memory.  The operand area of shared memory is padded
 // well beyond the operands and the whole TMEM range an N field can name is
@@ -65,7 +66,34 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const uint16_t *__rest
     if (warp == 0) hr_tc::tmem_dealloc(tb, kTmemCols);
 }
 
+// Failure-path check of the bounded waits: an mbarrier that nothing arrives at,
+// waited on with the same try-wait loop as the library's kernels but with a
+// caller-given poll limit; when it runs out the kernel raises the context's
+// error flag and returns.
+__global__ void wait_selftest_kernel(uint32_t max_polls, int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        hr_tma::mbar_init(&bar, 1);
+        hr_tma::fence_mbar_init();
+    }
+    __syncthreads();
+    bool done = false;
+    for (uint32_t i = 0; i < max_polls && !done; ++i) done = hr_tma::mbar_try_wait(&bar, 0);
+    if (!__syncthreads_or(done) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 }  // namespace
+
+extern "C" int hrebsd_wait_selftest(hrebsd_ctx *ctx, unsigned max_polls, void *stream)
+{
+    if (!ctx || max_polls < 1 || max_polls > (1u << 22)) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    wait_selftest_kernel<<<1, 32, 0, hr_stream(stream)>>>(max_polls, ctx->d_err);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
 
 extern "C" int hrebsd_tc_selftest(hrebsd_ctx *ctx, const uint16_t *A, const uint16_t *B, int N, int KS, float *D,
                                   void *stream)
