@@ -392,6 +392,13 @@ long long hrebsd_cnn_num_params(hrebsd_ctx *ctx);
 int hrebsd_cnn_init(hrebsd_ctx *ctx, const float *params_host, long long n_params);
 /* Copy parameters and the gradients of the last training step to the host (either may be NULL). */
 int hrebsd_cnn_get_params(hrebsd_ctx *ctx, float *params_host, float *grads_host);
+/* Training checkpoint: the Adam moments (host FP32, hrebsd_cnn_num_params
+ * entries each; get: either may be NULL) and the step count that sets the
+ * bias corrections.  set after hrebsd_cnn_init(params) resumes training
+ * exactly where get left it.  Both synchronise the device.  EINVAL: no
+ * network (get), a NULL moment or a negative step (set). */
+int hrebsd_cnn_get_state(hrebsd_ctx *ctx, float *m_host, float *v_host, int *step);
+int hrebsd_cnn_set_state(hrebsd_ctx *ctx, const float *m_host, const float *v_host, int step);
 /* Inference on x [B][2][64][64] BF16 (channel 0 reference, 1 test) -> field64 [B][2][64][64] FP32. */
 int hrebsd_cnn_infer(hrebsd_ctx *ctx, const uint16_t *x_bf16, int B, float *field64, void *stream);
 /* Inference from preprocessed patterns (as for the registration): the input is

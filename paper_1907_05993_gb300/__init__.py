@@ -21,7 +21,7 @@ __all__ = [
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
     "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
-    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_wait_selftest", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
+    "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_wait_selftest", "hrebsd_cnn_get_state", "hrebsd_cnn_set_state", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
     "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
@@ -118,6 +118,8 @@ def load(build: bool = False):
         "hrebsd_cnn_num_params": (ll, [vp]),
         "hrebsd_cnn_init": (i, [vp, vp, ll]),
         "hrebsd_cnn_get_params": (i, [vp, vp, vp]),
+        "hrebsd_cnn_get_state": (i, [vp, vp, vp, C.POINTER(C.c_int)]),
+        "hrebsd_cnn_set_state": (i, [vp, vp, vp, i]),
         "hrebsd_cnn_infer": (i, [vp, vp, i, vp, vp]),
         "hrebsd_cnn_infer_patterns": (i, [vp, vp, vp, vp, i, i, i, vp, vp]),
         "hrebsd_cnn_train_step": (i, [vp, vp, vp, i, C.c_float, vp, vp]),
@@ -395,6 +397,24 @@ def hrebsd_cnn_get_params(ctx):
     p, g = np.empty(n, np.float32), np.empty(n, np.float32)
     _chk(load().hrebsd_cnn_get_params(ctx, p.ctypes.data, g.ctypes.data), "hrebsd_cnn_get_params")
     return p, g
+
+
+def hrebsd_cnn_get_state(ctx):
+    """(Adam first moment, second moment, step) of the network in the context."""
+    import numpy as np
+    n = hrebsd_cnn_num_params(ctx)
+    m, v, step = np.empty(n, np.float32), np.empty(n, np.float32), C.c_int(0)
+    _chk(load().hrebsd_cnn_get_state(ctx, m.ctypes.data, v.ctypes.data, C.byref(step)), "hrebsd_cnn_get_state")
+    return m, v, step.value
+
+
+def hrebsd_cnn_set_state(ctx, m, v, step):
+    import numpy as np
+    n = hrebsd_cnn_num_params(ctx)
+    m, v = np.ascontiguousarray(m, np.float32), np.ascontiguousarray(v, np.float32)
+    if m.size != n or v.size != n:
+        raise ValueError(f"Adam moments need {n} entries each")
+    _chk(load().hrebsd_cnn_set_state(ctx, m.ctypes.data, v.ctypes.data, int(step)), "hrebsd_cnn_set_state")
 
 
 def hrebsd_cnn_infer(ctx, x_bf16, B, field64, stream=None):

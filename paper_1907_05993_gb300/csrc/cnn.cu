@@ -861,6 +861,30 @@ extern "C" int hrebsd_cnn_get_params(hrebsd_ctx *ctx, float *params_host, float 
     return HREBSD_OK;
 }
 
+extern "C" int hrebsd_cnn_get_state(hrebsd_ctx *ctx, float *m_host, float *v_host, int *step)
+{
+    if (!ctx || !ctx->cnn) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    HR_CHECK(cudaDeviceSynchronize());
+    if (m_host) HR_CHECK(cudaMemcpy(m_host, ctx->cnn->M, ctx->cnn->n_params * 4, cudaMemcpyDeviceToHost));
+    if (v_host) HR_CHECK(cudaMemcpy(v_host, ctx->cnn->V, ctx->cnn->n_params * 4, cudaMemcpyDeviceToHost));
+    if (step) *step = ctx->cnn->step;
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_cnn_set_state(hrebsd_ctx *ctx, const float *m_host, const float *v_host, int step)
+{
+    if (!ctx || !m_host || !v_host || step < 0) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_net(ctx))) return e;
+    HR_CHECK(cudaDeviceSynchronize());
+    HR_CHECK(cudaMemcpy(ctx->cnn->M, m_host, ctx->cnn->n_params * 4, cudaMemcpyHostToDevice));
+    HR_CHECK(cudaMemcpy(ctx->cnn->V, v_host, ctx->cnn->n_params * 4, cudaMemcpyHostToDevice));
+    ctx->cnn->step = step;
+    return HREBSD_OK;
+}
+
 static int infer_common(hrebsd_ctx *ctx, int B, float *field, cudaStream_t st)
 {
     int e = forward(ctx, B, st);

@@ -13,7 +13,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (cnn_params, demons_params, hrebsd_cnn_get_params, hrebsd_cnn_init, hrebsd_cnn_train_step,
+from . import (cnn_params, demons_params, hrebsd_cnn_get_params, hrebsd_cnn_get_state, hrebsd_cnn_init,
+               hrebsd_cnn_set_state, hrebsd_cnn_train_step,
                hrebsd_demons_register_batch, hrebsd_downsample_batch, hrebsd_field_resample, hrebsd_preprocess_batch)
 
 TARGET_CAP = 100                  # iteration cap of every level of the target registration
@@ -114,3 +115,25 @@ def save(ctx, path: str):
 
 def load_model(ctx, path: str):
     hrebsd_cnn_init(ctx, np.load(path))
+
+
+def save_checkpoint(ctx, path: str, **extra):
+    """Weights, Adam moments and step (plus any small arrays in ``extra``, e.g. the epoch) to one
+    .npz, written to a temporary name and renamed, so that an interrupted write leaves the previous
+    checkpoint intact."""
+    import os
+    w, _ = hrebsd_cnn_get_params(ctx)
+    m, v, step = hrebsd_cnn_get_state(ctx)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, params=w, adam_m=m, adam_v=v, step=np.int64(step), **extra)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(ctx, path: str) -> dict:
+    """Restore what save_checkpoint wrote; training continues as if it had not stopped.  Returns the
+    file's arrays (including ``extra``)."""
+    with np.load(path) as z:
+        d = {k: z[k] for k in z.files}
+    hrebsd_cnn_init(ctx, d["params"])
+    hrebsd_cnn_set_state(ctx, d["adam_m"], d["adam_v"], int(d["step"]))
+    return d

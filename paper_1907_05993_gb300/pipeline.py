@@ -206,6 +206,23 @@ class Pipeline:
                 o[name][a:b].copy_(r[name], non_blocking=True)
         return o
 
+    def run_scan(self, refs_host, tests_host, ref_idx_host, out_dir, chunk=10_000, slices=4):
+        """A whole scan from pinned host inputs, resumable: chunks of ``chunk`` points go through
+        ``run_host`` (``slices`` overlapped slices each) and F, R_finite and status of every chunk are
+        written to ``out_dir`` (see scan.run_resumable); calling it again after an interruption
+        computes only the missing chunks.  Returns (results as numpy arrays, chunks computed now)."""
+        from .scan import run_resumable
+        t = self.torch
+        cs = t.cuda.current_stream(self.dev)
+
+        def process(a, b):
+            o = self.run_host(refs_host, tests_host[a:b], ref_idx_host[a:b], chunks=slices)
+            cs.synchronize()
+            return {k: o[k].numpy().copy() for k in ("F", "R_finite", "status")}
+
+        tag = f"{tuple(tests_host.shape)} levels={self.cfg.levels} caps={tuple(self.cfg.max_iters)}"
+        return run_resumable(int(tests_host.shape[0]), int(chunk), out_dir, process, tag)
+
     def strain_stress(self, out, g, ref_idx, tilt_rad, stiffness=NI_STIFFNESS, traction_free=True, stream=None):
         """Post-processing of Eq. 13-16 on the F of ``run``: adds F_S, eps, sigma [B, 9] (FP64) to ``out``.
 
