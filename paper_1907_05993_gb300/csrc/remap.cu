@@ -4,9 +4,9 @@
 // projection of R^T r', r' = (x' - xpc, y' - ypc, Z*): the reference point
 // that Eq. 2 maps onto x' under the pure rotation R.  The value is a Keys
 // (1981) cubic convolution (a = -0.5) over 4x4 reference pixels with
-// replicated borders.  One thread per output pixel; the references (a few
-// grains) are gathered through the read-only path and stay in L2, so HBM
-// traffic is the 4 B written per pixel.
+// replicated borders.  One thread per output pixel, one CTA per output row;
+// the references (a few grains) are gathered through the read-only path and
+// stay in L2, so HBM traffic is the 4 B written per pixel.
 #include "internal.cuh"
 
 namespace {
@@ -22,23 +22,29 @@ __device__ __forceinline__ void keys_weights(float t, float *wt)
     wt[3] = ((a * s3 - 5.0f * a) * s3 + 8.0f * a) * s3 - 4.0f * a;
 }
 
-__global__ void remap_kernel(const float *__restrict__ ref, const int32_t *__restrict__ ref_idx,
-                             const double *__restrict__ Rf, int B, int H, int W, float xpc, float ypc, float zs,
-                             float *__restrict__ out)
+// One CTA per output row (blockIdx.x = pair x H + row, all index arithmetic
+// 32-bit and per CTA), threads along the row; R^T of the pair is read once per
+// CTA and kept in FP32 registers.
+__global__ void __launch_bounds__(256) remap_kernel(const float *__restrict__ ref, const int32_t *__restrict__ ref_idx,
+                                                    const double *__restrict__ Rf, int B, int H, int W, float xpc,
+                                                    float ypc, float zs, float *__restrict__ out)
 {
+    const int b = (int)(blockIdx.x / (unsigned)H), i = (int)(blockIdx.x - (unsigned)b * H);
+    if (b >= B) return;
+    float r[9];
+    const double *R = Rf + (size_t)b * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r[k] = (float)__ldg(R + k);
     const size_t plane = (size_t)H * W;
-    const size_t total = (size_t)B * plane;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int b = (int)(idx / plane);
-        const int rem = (int)(idx - (size_t)b * plane);
-        const int i = rem / W, j = rem - i * W;
-        const double *R = Rf + (size_t)b * 9;
-        const float dx = (float)j + 0.5f - xpc, dy = (float)i + 0.5f - ypc;
+    const float *M = ref + (size_t)__ldg(ref_idx + b) * plane;
+    float *orow = out + (size_t)b * plane + (size_t)i * W;
+    const float dy = (float)i + 0.5f - ypc;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const float dx = (float)j + 0.5f - xpc;
         // v = R^T r'
-        const float v0 = fmaf((float)R[0], dx, fmaf((float)R[3], dy, (float)R[6] * zs));
-        const float v1 = fmaf((float)R[1], dx, fmaf((float)R[4], dy, (float)R[7] * zs));
-        const float v2 = fmaf((float)R[2], dx, fmaf((float)R[5], dy, (float)R[8] * zs));
+        const float v0 = fmaf(r[0], dx, fmaf(r[3], dy, r[6] * zs));
+        const float v1 = fmaf(r[1], dx, fmaf(r[4], dy, r[7] * zs));
+        const float v2 = fmaf(r[2], dx, fmaf(r[5], dy, r[8] * zs));
         const float iv = zs / v2;
         const float x = fmaf(v0, iv, xpc - 0.5f), y = fmaf(v1, iv, ypc - 0.5f);
         const float fx0 = floorf(x), fy0 = floorf(y);
@@ -46,18 +52,19 @@ __global__ void remap_kernel(const float *__restrict__ ref, const int32_t *__res
         float wx[4], wy[4];
         keys_weights(x - fx0, wx);
         keys_weights(y - fy0, wy);
-        const float *M = ref + (size_t)__ldg(ref_idx + b) * plane;
+        int cx[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cx[k] = min(max(x0 - 1 + k, 0), W - 1);
         float acc = 0.0f;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const int yy = min(max(y0 - 1 + m, 0), H - 1);
-            const float *row = M + (size_t)yy * W;
-            float r = 0.0f;
+            const float *row = M + min(max(y0 - 1 + m, 0), H - 1) * W;
+            float rr = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) r = fmaf(wx[k], __ldg(row + min(max(x0 - 1 + k, 0), W - 1)), r);
-            acc = fmaf(wy[m], r, acc);
+            for (int k = 0; k < 4; ++k) rr = fmaf(wx[k], __ldg(row + cx[k]), rr);
+            acc = fmaf(wy[m], rr, acc);
         }
-        out[idx] = acc;
+        orow[j] = acc;
     }
 }
 
@@ -71,11 +78,11 @@ extern "C" int hrebsd_remap(hrebsd_ctx *ctx, const float *ref, const int32_t *re
     if (!ref || !ref_idx || !R_finite || !remapped) return HREBSD_EINVAL;
     int e = hr_set_device(ctx);
     if (e) return e;
-    size_t total = (size_t)B * H * W;
-    int grid = (int)((total + 255) / 256);
-    if (grid > ctx->num_sms * 32) grid = ctx->num_sms * 32;
+    const long long rows = (long long)B * H;
+    if (rows > 0x7fffffffLL || (long long)H * W > 0x7fffffffLL) return HREBSD_EINVAL;
+    const int threads = W >= 256 ? 256 : (W + 31) / 32 * 32;
     hr_prof_begin(ctx, hr_stream(stream));
-    remap_kernel<<<grid, 256, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
+    remap_kernel<<<(unsigned)rows, threads, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
                                                       (float)(g->ystar * H), (float)(g->zstar * W), remapped);
     hr_prof_end(ctx, PROF_REMAP, hr_stream(stream));
     HR_LAUNCHED(ctx);
