@@ -213,12 +213,13 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
 
 /* Tile shapes of the TMA-fed demons iteration (batching; the paper has no
  * counterpart): 0 = 64x32 outputs, 256 threads (2 CTAs per SM), 1 = 32x32
- * (3 per SM), 2 = 64x16 (3 per SM), 3 = 64x32 with 512 threads (2 per SM).
- * Shapes 1-3 exist for the Gaussian radius 3 (sigma = 1); other radii always
+ * (3 per SM), 2 = 64x16 (3 per SM), 3 = 64x32 with 512 threads (2 per SM),
+ * 4 = 64x64 with 512 threads (1 per SM), 5 = 64x64 with 768 threads (1 per SM).
+ * Shapes 1-5 exist for the Gaussian radius 3 (sigma = 1); other radii always
  * use shape 0.  Every shape computes each
  * output pixel with the same operations in the same order, so the field is
  * the same; only the grouping of the per-tile SSD partials changes. */
-#define HREBSD_TILE_VARIANTS 4
+#define HREBSD_TILE_VARIANTS 6
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small

@@ -863,9 +863,9 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, i
 // (and hence the last bits of the level SSD) are grouped differently.  The
 // extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
 // use shape 0.
-constexpr int kTileVariants = 4;
-constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64};
-constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32};
+constexpr int kTileVariants = 6;
+constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 64};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 64};
 constexpr int kMinTX = 32, kMinTY = 16;
 bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }   // smallest tile extents (sizes the SSD partials)
 static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
@@ -944,7 +944,9 @@ int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit
     case 0: return CALL(RAD, 64, 32, 2, 256, 4);                                                                   \
     case 1: if (RAD == 3) return CALL(3, 32, 32, 3, 256, 4); break;                                                \
     case 2: if (RAD == 3) return CALL(3, 64, 16, 3, 256, 4); break;                                                \
-    case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512, 4); break;
+    case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512, 4); break;                                                \
+    case 4: if (RAD == 3) return CALL(3, 64, 64, 1, 512, 4); break;                                                \
+    case 5: if (RAD == 3) return CALL(3, 64, 64, 1, 768, 4); break;
 
 bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w,
                  CUtensorMap *tmS, CUtensorMap *tmF)
