@@ -254,8 +254,11 @@ def run_ours(args, rank, world, local_rank):
     refs, tests, ridx, _ = synth_gpu.make_scan_gpu(spec, pairs)
     torch.cuda.synchronize()
     cfg = PipelineConfig(wl["H"], wl["W"], wl["roi"], wl["S"], wl["levels"], wl["caps"], 1.0, 1.0,
-                         wl["stop_tol"], wl["stop_window"])
+                         wl["stop_tol"], wl["stop_window"], autotune=args.tile_variants is None)
     pipe = Pipeline(cfg, device=local_rank)
+    if args.tile_variants is not None:   # fixed tile shapes per level (finest first), no autotuning
+        for l, v in enumerate(args.tile_variants[:wl["levels"]]):
+            P.hrebsd_set_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l, v)
     stream = torch.cuda.current_stream()
     out = {}
     for _ in range(args.warmup):
@@ -288,10 +291,11 @@ def run_ours(args, rank, world, local_rank):
 
     def shape_name(v):
         return "x".join(map(str, P.TILE_SHAPES[v])) + f"/{P.TILE_THREADS[v]}t"
-    tile_choice = None if tune_ms is None else [
+    tile_choice = [
         {"level": l, "shape": shape_name(P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l)),
-         "ms_per_iteration_by_shape": {shape_name(v): round(float(tune_ms[l, v]), 4)
-                                       for v in range(P.TILE_VARIANTS) if np.isfinite(tune_ms[l, v])}}
+         **({"pinned": True} if tune_ms is None else
+            {"ms_per_iteration_by_shape": {shape_name(v): round(float(tune_ms[l, v]), 4)
+                                           for v in range(P.TILE_VARIANTS) if np.isfinite(tune_ms[l, v])}})}
         for l in range(wl["levels"])]
     iters = out["iters"].cpu().numpy()
     status = out["status"].cpu().numpy()
@@ -734,6 +738,8 @@ def main():
     ap.add_argument("--learned-start", type=int, default=64, choices=(64, 128))
     ap.add_argument("--oracle-pairs", type=int, default=500)
     ap.add_argument("--learned-caps", type=int, nargs=4, default=(25, 25, 10, 0))
+    ap.add_argument("--tile-variants", type=int, nargs=4, default=None,
+                    help="scan workload: demons tile shape per level, finest first (no autotuning)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

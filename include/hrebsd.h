@@ -214,18 +214,21 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
 /* Tile shapes of the TMA-fed demons iteration (batching; the paper has no
  * counterpart): 0 = 64x32 outputs, 256 threads (2 CTAs per SM), 1 = 32x32
  * (3 per SM), 2 = 64x16 (3 per SM), 3 = 64x32 with 512 threads (2 per SM),
- * 4 = 64x64 with 512 threads (1 per SM), 5 = 64x64 with 768 threads (1 per SM).
- * Shapes 1-5 exist for the Gaussian radius 3 (sigma = 1); other radii always
+ * 4 = 64x64 with 768 threads (1 per SM; of 512, 768, 896 and 1024 threads
+ * the fastest on GB300).  Shapes 1-4 exist for the Gaussian radius 3 (sigma = 1); other radii always
  * use shape 0.  Every shape computes each
  * output pixel with the same operations in the same order, so the field is
  * the same; only the grouping of the per-tile SSD partials changes. */
-#define HREBSD_TILE_VARIANTS 6
+#define HREBSD_TILE_VARIANTS 5
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small
  * rotation field (min(B, 2048) pairs; 2 warm-up iterations, then the best of
- * 3 timed batches of 4, CUDA events on `stream`) and keep the fastest for later registrations of
- * that level size in this context.  Synchronises `stream`; uses context
+ * 3 timed batches of 4, CUDA events on `stream`) and keep, for later
+ * registrations of that level size in this context, the shape with the least
+ * time x (1 + 0.01 log2(4096 / tile area)): smaller tiles carry a 1 % handicap
+ * per halving of the area, because the synthetic timing showed a tie where
+ * the 64x64 shape was 4 % faster on scan data.  Synchronises `stream`; uses context
  * workspace.  ms_out (host, nullable): [levels][HREBSD_TILE_VARIANTS]
  * milliseconds per iteration, NaN where a shape is unavailable.  Returns
  * HREBSD_EINVAL for invalid parameters (as hrebsd_demons_register_batch). */

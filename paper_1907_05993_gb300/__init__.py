@@ -271,9 +271,9 @@ def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, s
          "hrebsd_solve_F")
 
 
-TILE_VARIANTS = 6
-TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64), (64, 64))
-TILE_THREADS = (256, 256, 256, 512, 512, 768)
+TILE_VARIANTS = 5
+TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64))
+TILE_THREADS = (256, 256, 256, 512, 768)
 
 
 def hrebsd_autotune(ctx, B, H, W, params, stream=None):

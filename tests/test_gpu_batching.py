@@ -67,8 +67,10 @@ def test_autotune_records_the_fastest_shape(torch, lib):
     ms = lib.hrebsd_autotune(ctx, 64, 256, 256, params)
     assert ms.shape == (4, lib.TILE_VARIANTS)
     assert np.isfinite(ms).all() and (ms > 0).all()
+    area = np.array([w * h for w, h in lib.TILE_SHAPES], dtype=np.float64)
+    score = ms * (1.0 + 0.01 * np.log2(4096.0 / area))      # the documented handicap of small tiles
     for l in range(4):
-        assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == int(np.argmin(ms[l]))
+        assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == int(np.argmin(score[l]))
     # radius 0 (no smoothing): nothing to tune
     ms0 = lib.hrebsd_autotune(ctx, 8, 64, 64, lib.demons_params(2, [5, 5], 1.0, 0.0, 0.0))
     assert np.isnan(ms0).all()
