@@ -4,7 +4,7 @@
  * A plain, slow, single-threaded FP64 CPU restatement of the HR-EBSD
  * demons-remapping method of Zhu, Kaufmann & Vecchio, "Novel Remapping
  * Approach for HR-EBSD based on Demons Registration" (arXiv 1907.05993).
- * It is the judge of the CUDA library: only the tests, the smoke check and
+ * It is what the CUDA library is checked against: only the tests, the smoke check and
  * the benchmark's CPU-baseline leg load it.  It shares no code, header,
  * table or constant with the CUDA path, and the product never calls it.
  *
