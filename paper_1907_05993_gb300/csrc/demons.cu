@@ -451,7 +451,9 @@ __device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, 
     }
 }
 
-template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR>
+// IN_S: the input is s_k (u = G_f * s); false for the first iteration of a
+// level, whose input is the prolonged field u_0 itself.
+template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR, bool IN_S = true>
 __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid_constant__ CUtensorMap tmS,
                                                                              const __grid_constant__ CUtensorMap tmF,
                                                                              IterArgs a)
@@ -529,15 +531,17 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             __syncthreads();
         }
         // ---- u = G_f * s on T + r
-        constexpr int NSX = L::BWP / RUN;
-        for (int it = tid; it < NSX * L::AHP; it += NT) {
-            const int seg = it / L::AHP, row = it - seg * L::AHP;
-            run_x<RAD>(sS + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
-        }
-        __syncthreads();
-        if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
-            hr_tma::fence_proxy_async();
-            issue_S(tile_of<TX_, TY_>(a, next));
+        if constexpr (IN_S) {
+            constexpr int NSX = L::BWP / RUN;
+            for (int it = tid; it < NSX * L::AHP; it += NT) {
+                const int seg = it / L::AHP, row = it - seg * L::AHP;
+                run_x<RAD>(sS + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
+            }
+            __syncthreads();
+            if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
+                hr_tma::fence_proxy_async();
+                issue_S(tile_of<TX_, TY_>(a, next));
+            }
         }
         // ---- (the y pass of G_f runs inside the force stage below, on each
         // thread's own column run; u on T + r is kept in sU for the last stage)
@@ -570,7 +574,13 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 fr[i] = fcol[(i + 1) * G::FWB + 1];
             }
             float2 u[FR];
-            {   // y pass of G_f for rows r0 .. r0 + FR - 1 of column c (same sum order as run_y)
+            if constexpr (!IN_S) {   // u_0 itself: the tile holds it with the same 2r halo as s
+#pragma unroll
+                for (int i = 0; i < FR; ++i) {
+                    u[i] = sS[(r0 + i + RAD) * L::AST + c + RAD];
+                    sU[(r0 + i) * L::UST + c] = u[i];
+                }
+            } else {   // y pass of G_f for rows r0 .. r0 + FR - 1 of column c (same sum order as run_y)
                 static_assert(((L::BH + FR - 1) / FR) * FR <= L::BHP, "force runs stay inside sU");
                 float2 win[FR + 2 * RAD];
 #pragma unroll
@@ -620,8 +630,9 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             fix_cols(sD, L::DST, L::BH, L::BW, x0 - RAD, w);
         }
         __syncthreads();
-        if (tid == 0 && next < work) {   // the test-image tile is consumed: fetch the next one
+        if (tid == 0 && next < work) {   // the test-image tile (and u_0's) is consumed: fetch the next one
             hr_tma::fence_proxy_async();
+            if constexpr (!IN_S) issue_S(tile_of<TX_, TY_>(a, next));
             issue_F(tile_of<TX_, TY_>(a, next));
         }
         // ---- G_u * du: x pass on rows of T + r, columns of T
@@ -818,7 +829,7 @@ int launch_iter(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t 
     return a.in_is_s ? launch_iter_t<RAD, true>(ctx, a, max_items, st) : launch_iter_t<RAD, false>(ctx, a, max_items, st);
 }
 
-template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR>
+template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR, bool IN_S = true>
 int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &tmF, const IterArgs &a, int max_items,
                     cudaStream_t st)
 {
@@ -826,7 +837,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR>;
+        auto k = demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR, IN_S>;
         HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT_, smem));
         if (occ < 1) occ = 1;
@@ -836,7 +847,7 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR><<<grid, NT_, smem, st>>>(tmS, tmF, a);
+    demons_iter_tma_kernel<RAD, TX_, TY_, MINB, NT_, FR, IN_S><<<grid, NT_, smem, st>>>(tmS, tmF, a);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -845,14 +856,15 @@ int launch_iter_tma(hrebsd_ctx *ctx, const CUtensorMap &tmS, const CUtensorMap &
 // Tensor maps of one level for the TMA-fed iteration: the two s buffers
 // (float2 [B][h][w] seen as FP32 [B][h][2w]) and the test images.
 template <int RAD, int TX_, int TY_>
-bool encode_level_maps(const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w, CUtensorMap *tmS,
-                       CUtensorMap *tmF)
+bool encode_level_maps(const float2 *s0, const float2 *s1, const float2 *u0, const float *ftest, int B, int h, int w,
+                       CUtensorMap *tmS, CUtensorMap *tmF)
 {
     using L = Geo<RAD, TX_, TY_>;
     using G = GeoT<RAD, TX_, TY_>;
     const uint64_t row2 = (uint64_t)w * 8, img2 = row2 * h, row1 = (uint64_t)w * 4, img1 = row1 * h;
     if (hr_encode_tmap_3d(&tmS[0], s0, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
     if (hr_encode_tmap_3d(&tmS[1], s1, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
+    if (u0 && hr_encode_tmap_3d(&tmS[2], u0, 2ull * w, h, B, row2, img2, 2 * L::AST, L::AHP, 1)) return false;
     if (hr_encode_tmap_3d(tmF, ftest, w, h, B, row1, img1, G::FWB, G::FH, 1)) return false;
     return true;
 }
@@ -947,10 +959,11 @@ int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit
     case 3: if (RAD == 3) return CALL(3, 64, 32, 2, 512, 4); break;                                                \
     case 4: if (RAD == 3) return CALL(3, 64, 64, 1, 768, 4); break;
 
-bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float *ftest, int B, int h, int w,
-                 CUtensorMap *tmS, CUtensorMap *tmF)
+// tmS: [3] (s0, s1 and, when u0 is given, the level's initial field).
+bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const float2 *u0, const float *ftest, int B,
+                 int h, int w, CUtensorMap *tmS, CUtensorMap *tmF)
 {
-#define HR_ENC(R, X, Y, MB, NT, FR) encode_level_maps<R, X, Y>(s0, s1, ftest, B, h, w, tmS, tmF)
+#define HR_ENC(R, X, Y, MB, NT, FR) encode_level_maps<R, X, Y>(s0, s1, u0, ftest, B, h, w, tmS, tmF)
     switch (rad) {
     case 1: return var == 0 && HR_ENC(1, 64, 32, 2, 256, 4);
     case 2: return var == 0 && HR_ENC(2, 64, 32, 2, 256, 4);
@@ -965,9 +978,18 @@ bool encode_maps(int rad, int var, const float2 *s0, const float2 *s1, const flo
 #undef HR_ENC
 }
 
-int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, int var, const CUtensorMap &tmS, const CUtensorMap &tmF,
+// in_s false (first iteration of a level, input u_0): compiled for radius 3 only.
+int dispatch_iter_tma(hrebsd_ctx *ctx, int rad, int var, bool in_s, const CUtensorMap &tmS, const CUtensorMap &tmF,
                       const IterArgs &a, int max_items, cudaStream_t st)
 {
+    if (!in_s) {
+#define HR_LT0(R, X, Y, MB, NT, FR) launch_iter_tma<R, X, Y, MB, NT, FR, false>(ctx, tmS, tmF, a, max_items, st)
+        if (rad == 3) {
+            switch (var) { HR_TMA_VARIANTS(3, HR_LT0) default: break; }
+        }
+#undef HR_LT0
+        return HREBSD_EINVAL;
+    }
 #define HR_LT(R, X, Y, MB, NT, FR) launch_iter_tma<R, X, Y, MB, NT, FR>(ctx, tmS, tmF, a, max_items, st)
     switch (rad) {
     case 1: if (var == 0) return HR_LT(1, 64, 32, 2, 256, 4); break;
@@ -1131,9 +1153,10 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         const int h = H >> l, w = W >> l;
         const int cap = p->max_iters[l];
         const int var = hr_tuned_variant(ctx, rad, h, w);
-        CUtensorMap tmS[2], tmF;
+        CUtensorMap tmS[3], tmF;
         const bool use_tma = rad > 0 && !ctx->no_tma && cap > 1 &&
-                             encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, tl[l], B, h, w, tmS, &tmF);
+                             encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, (const float2 *)u0, tl[l],
+                                         B, h, w, tmS, &tmF);
         // The launches of one level: list reset, cap x (iteration, control),
         // finalize, prolongation.  Replayed from a cached CUDA graph when possible.
         auto emit = [&](cudaStream_t st) -> int {
@@ -1143,7 +1166,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
             HR_LAUNCHED(ctx);
             for (int k = 0; k < cap; ++k) {
-                const bool tma_k = k > 0 && use_tma;
+                const bool tma_k = use_tma && (k > 0 || rad == 3);
                 const int tx = tma_k ? kVarTX[var] : TX, ty = tma_k ? kVarTY[var] : TY;
                 const int tiles_x = (w + tx - 1) / tx, tiles = tiles_x * ((h + ty - 1) / ty);
                 int *cur = (k & 1) ? list1 : list0, *nxt = (k & 1) ? list0 : list1;
@@ -1166,7 +1189,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 a.taps = taps;
                 a.px_count = hr_prof_pixiters(ctx);
                 a.err = ctx->d_err;
-                if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, tmS[k & 1], tmF, a, B * tiles, st);
+                if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, k > 0, k > 0 ? tmS[k & 1] : tmS[2], tmF, a, B * tiles, st);
                 else e2 = dispatch_iter(ctx, rad, a, B * tiles, st);
                 if (e2) return e2;
                 CtrlArgs c;
@@ -1349,8 +1372,9 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
             int best_v = 0;
             for (int v = 0; v < kTileVariants; ++v) {
                 if (!variant_ok(rad, v) || ctx->no_tma) continue;
-                CUtensorMap tmS[2], tmF;
-                if (!encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, test, Bt, h, w, tmS, &tmF)) continue;
+                CUtensorMap tmS[3], tmF;
+                if (!encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
+                    continue;
                 const int tiles_x = (w + kVarTX[v] - 1) / kVarTX[v], tiles = tiles_x * ((h + kVarTY[v] - 1) / kVarTY[v]);
                 IterArgs a;
                 a.Ftest = test;
@@ -1376,7 +1400,7 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 for (; k < kWarm; ++k) {
                     a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                     a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
-                    int e2 = dispatch_iter_tma(ctx, rad, v, tmS[k & 1], tmF, a, Bt * tiles, st);
+                    int e2 = dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                     if (e2) return e2;
                 }
                 for (int rep = 0; rep < kRounds; ++rep) {
@@ -1384,7 +1408,7 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                     for (int j = 0; j < kBatch; ++j, ++k) {
                         a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                         a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
-                        int e2 = dispatch_iter_tma(ctx, rad, v, tmS[k & 1], tmF, a, Bt * tiles, st);
+                        int e2 = dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                         if (e2) return e2;
                     }
                     HR_CHECK(cudaEventRecord(ev[1], st));

@@ -367,7 +367,9 @@ def test_pipeline_single_pair_workload(torch, lib, oracle):
 # ------------------------------------------------------------------ both iteration paths
 @pytest.mark.parametrize("H,W,levels,caps", [(256, 256, 4, [12] * 4), (96, 80, 2, [10, 10]), (66, 70, 1, [10])])
 def test_tma_and_plain_iteration_paths_agree(torch, lib, oracle, H, W, levels, caps):
-    """The tensor-memory-accelerator path (k > 0) and the plain-load path give the same field.
+    """The tensor-memory-accelerator path (every iteration for radius 3, where the first one of a
+    level reads u_0 through its own tensor map; k > 0 otherwise) and the plain-load path give the
+    same field.
 
     66 x 70 is a shape the tensor maps refuse (row pitch not a multiple of 16 bytes), so it runs
     the plain path in both modes and checks the fallback against the oracle.
