@@ -308,7 +308,7 @@ def run_ours(args, rank, world, local_rank):
     h_R = torch.empty((B, 9), dtype=torch.float64).pin_memory()
     h_st = torch.empty((B,), dtype=torch.int32).pin_memory()
     e_steps = max(1, min(args.steps, 3))
-    # Pipeline.run_host: the batch in E2E_CHUNKS slices, the host -> device copy of slice k + 1 on a
+    # Pipeline.run_host: the batch in E2E_CHUNKS slices of growing size, the host -> device copy of slice k + 1 on a
     # side stream while slice k is processed, results copied back into pinned host tensors.  One
     # untimed pass first (new slice buffers: autotune and per-level graph capture happen there).
     host_out = {"F": h_F, "R_finite": h_R, "status": h_st}
@@ -353,8 +353,8 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(wl, B),
             "e2e": {"value": world * B * e_steps / te, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
-                    "path": f"Pipeline.run_host: pinned host inputs, {E2E_CHUNKS} slices, copy of slice k+1 "
-                            f"overlapping slice k, F/R/status back to pinned host"},
+                    "path": f"Pipeline.run_host: pinned host inputs, {E2E_CHUNKS} slices growing 1:2:4:8, copy of "
+                            f"slice k+1 overlapping slice k, F/R/status back to pinned host"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "kernel": "demons_iter_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,

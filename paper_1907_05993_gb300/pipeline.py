@@ -152,21 +152,37 @@ class Pipeline:
         hrebsd_solve_F(self.ctx, q, self.roi, N, B, H, W, self.geom, Rf, F, status, stream)
         return o
 
-    def run_host(self, refs_host, tests_host, ref_idx_host, chunks=4, out=None):
+    @staticmethod
+    def slice_bounds(B: int, chunks: int, growth: float = 2.0):
+        """Boundaries of ``chunks`` consecutive slices of B items whose sizes grow by ``growth``
+        (1 : 2 : 4 ... by default): the first slice, whose copy nothing hides, is small, and each
+        later copy runs while the (smaller) slice before it is processed.  Every slice has at
+        least one item; returns [0, b1, ..., B]."""
+        k = max(1, min(int(chunks), B))
+        w = [growth ** i for i in range(k)]
+        cuts = [0]
+        for i in range(1, k):
+            c = int(round(B * sum(w[:i]) / sum(w)))
+            cuts.append(min(max(c, cuts[-1] + 1), B - (k - i)))
+        cuts.append(B)
+        return cuts
+
+    def run_host(self, refs_host, tests_host, ref_idx_host, chunks=4, out=None, growth=2.0):
         """Host-resident inputs: refs [R,H,W] and tests [B,H,W] float32, ref_idx [B] int32, in pinned CPU
-        memory.  The batch runs through ``run`` as ``chunks`` consecutive slices on the current stream;
-        the host -> device copy of slice k + 1 runs on a side stream while slice k is processed, and
-        F, R_finite (FP64 [B, 9]) and status ([B]) of every slice are copied into pinned host tensors,
-        returned in a dict (valid once the current stream has synchronised).  Each pair's result is
-        the one ``run`` gives on the whole batch (pairs are independent); the static background,
-        a statistic of the whole batch, needs chunks=1."""
+        memory.  The batch runs through ``run`` as ``chunks`` consecutive slices (sizes growing by
+        ``growth``, see slice_bounds) on the current stream; the host -> device copy of slice k + 1 runs
+        on a side stream while slice k is processed, and F, R_finite (FP64 [B, 9]) and status ([B]) of
+        every slice are copied into pinned host tensors, returned in a dict (valid once the current
+        stream has synchronised).  Each pair's result is the one ``run`` gives on the whole batch (pairs
+        are independent); the static background, a statistic of the whole batch, needs chunks=1."""
         t = self.torch
         if self.cfg.static_background and chunks > 1:
             raise ValueError("the static background is a whole-batch statistic: use chunks=1")
         B, H, W = tests_host.shape
         R = refs_host.shape[0]
-        n = -(-B // max(1, chunks))
-        nk = -(-B // n)
+        cuts = self.slice_bounds(B, chunks, growth)
+        nk = len(cuts) - 1
+        n = max(cuts[i + 1] - cuts[i] for i in range(nk))
         cs = t.cuda.current_stream(self.dev)
         if self._copy_stream is None:
             self._copy_stream = t.cuda.Stream(self.dev)
@@ -184,7 +200,7 @@ class Pipeline:
         freed = [None, None]
 
         def issue_copy(k):
-            sl, a, b = k % 2, k * n, min(B, (k + 1) * n)
+            sl, a, b = k % 2, cuts[k], cuts[k + 1]
             with t.cuda.stream(xs):
                 if freed[sl] is not None:   # the slice two back is done with this staging slot
                     xs.wait_event(freed[sl])
@@ -194,7 +210,7 @@ class Pipeline:
 
         issue_copy(0)
         for k in range(nk):
-            sl, a, b = k % 2, k * n, min(B, (k + 1) * n)
+            sl, a, b = k % 2, cuts[k], cuts[k + 1]
             if k + 1 < nk:
                 issue_copy(k + 1)
             cs.wait_event(copied[sl])

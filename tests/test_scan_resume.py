@@ -48,3 +48,14 @@ def test_other_scan_refused_and_shapes_checked(tmp_path):
         scan.run_resumable(7, 3, d, _process_factory([]))      # other size
     with pytest.raises(ValueError):
         scan.run_resumable(4, 2, str(tmp_path / "bad"), lambda a, b: {"F": np.zeros((1, 9))})
+
+
+def test_slice_bounds_cover_the_batch_with_growing_slices():
+    from paper_1907_05993_gb300.pipeline import Pipeline
+    assert Pipeline.slice_bounds(10_000, 4) == [0, 667, 2000, 4667, 10_000]
+    for B in range(1, 40):
+        for chunks in range(1, 7):
+            cuts = Pipeline.slice_bounds(B, chunks)
+            sizes = np.diff(cuts)
+            assert cuts[0] == 0 and cuts[-1] == B and len(sizes) == min(chunks, B) and (sizes >= 1).all()
+    assert Pipeline.slice_bounds(12, 3, growth=1.0) == [0, 4, 8, 12]
