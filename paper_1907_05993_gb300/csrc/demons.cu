@@ -768,18 +768,20 @@ __global__ void __launch_bounds__(256) demons_finalize_kernel(const float2 *u0, 
 }
 
 // Prolongation (Section 1): fine(x_f) = 2 * bilinear(coarse, (x_f + 0.5)/2 - 0.5), interleaved fields.
-__global__ void prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B, int h, int w)
+// One CTA per fine row (blockIdx.x = pair x 2h + row), threads along the row.
+__global__ void __launch_bounds__(256) prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B,
+                                                      int h, int w)
 {
     const int H = 2 * h, W = 2 * w;
-    const size_t total = (size_t)B * H * W;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        size_t b = idx / ((size_t)H * W);
-        int rem = (int)(idx - b * H * W);
-        int i = rem / W, j = rem - i * W;
-        float x = ((float)j + 0.5f) * 0.5f - 0.5f, y = ((float)i + 0.5f) * 0.5f - 0.5f;
-        float2 v = bilinear2_clamped(uc + b * h * w, h, w, x, y);
-        uf[idx] = make_float2(2.0f * v.x, 2.0f * v.y);
+    const int b = (int)(blockIdx.x / (unsigned)H), i = (int)(blockIdx.x - (unsigned)b * H);
+    if (b >= B) return;
+    const float2 *src = uc + (size_t)b * h * w;
+    float2 *dst = uf + ((size_t)b * H + i) * W;
+    const float y = ((float)i + 0.5f) * 0.5f - 0.5f;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const float x = ((float)j + 0.5f) * 0.5f - 0.5f;
+        const float2 v = bilinear2_clamped(src, h, w, x, y);
+        dst[j] = make_float2(2.0f * v.x, 2.0f * v.y);
     }
 }
 
@@ -1222,11 +1224,11 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                                         iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
                 return e2;
             if (l > 0) {
-                size_t total = (size_t)B * (2 * h) * (2 * w);
-                int grid = (int)((total + 255) / 256);
-                if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+                if ((long long)B * (2 * h) > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
+                const unsigned rows = (unsigned)B * (unsigned)(2 * h);
+                const int threads = 2 * w >= 256 ? 256 : (2 * w + 31) / 32 * 32;
                 hr_prof_begin(ctx, st);
-                prolong_kernel<<<grid, 256, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
+                prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
                 hr_prof_end(ctx, PROF_DEMONS_AUX, st);
                 HR_LAUNCHED(ctx);
             }
