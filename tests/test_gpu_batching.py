@@ -61,6 +61,29 @@ def test_tile_shapes_give_the_same_field(torch, lib, pairs):
         assert np.array_equal(it, out[0][1]) and np.array_equal(st, out[0][2])
 
 
+def test_tile_shapes_agree_on_ragged_tiles(torch, lib, oracle):
+    """96x96 patterns (levels 96, 48, 24): 64x64 and 64x32 tiles run past the image edge, so the
+    border replication of partial tiles is exercised; with fixed iteration counts every shape gives
+    a bit-identical field."""
+    spec = K.ScanSpec(n_pairs=3, H=96, W=96, n_refs=1, mis_lo_deg=0.5, mis_hi_deg=3.0, seed=77)
+    refs = np.stack([oracle.preprocess(K.render_ref(spec, 0).astype(np.float64), True)]).astype(np.float32)
+    tests = np.stack([oracle.preprocess(K.render_test(spec, p).astype(np.float64), True)
+                      for p in range(3)]).astype(np.float32)
+    ridx = np.zeros(3, dtype=np.int32)
+    params = lib.demons_params(3, [15] * 3, 1.0, 1.0, 1.0)
+    out = []
+    for v in range(lib.TILE_VARIANTS):
+        ctx = lib.hrebsd_create(0)
+        for l in range(3):
+            lib.hrebsd_set_tile_variant(ctx, 96 >> l, 96 >> l, v)
+        out.append(_register(torch, lib, ctx, (refs, tests, ridx), params))
+        lib.hrebsd_destroy(ctx)
+    assert np.isfinite(out[0][0]).all() and np.abs(out[0][0]).max() > 0
+    for f, it, st in out[1:]:
+        assert np.array_equal(f, out[0][0])
+        assert np.array_equal(it, out[0][1]) and np.array_equal(st, out[0][2])
+
+
 def test_autotune_records_the_fastest_shape(torch, lib):
     ctx = lib.hrebsd_create(0)
     params = lib.demons_params(4, [100] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
