@@ -499,18 +499,26 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         hr_tma::mbar_arrive_expect_tx(&bar[1], G::F_BYTES);
         hr_tma::load_3d(sF, &tmF, &bar[1], t.x0 - G::FOFF, t.y0 - RAD - 1, t.pair);
     };
+    // The item's tile is decoded once, by thread 0 when it issues the item's copies, and read by
+    // all threads from shared memory after the barrier that opens the item (thread 0 overwrites it
+    // with the next item only after a later barrier of the current one).
+    __shared__ TileRef s_tile;
+    __shared__ int s_ref;
     long long item = blockIdx.x;
+    TileRef tn;   // thread 0: the next item
+    auto publish = [&](const TileRef &t) {
+        s_tile = t;
+        s_ref = __ldg(a.ref_idx + t.pair);
+    };
     if (tid == 0 && item < work) {
-        const TileRef t = tile_of<TX_, TY_>(a, item);
-        issue_S(t);
-        issue_F(t);
+        tn = tile_of<TX_, TY_>(a, item);
+        publish(tn);
+        issue_S(tn);
+        issue_F(tn);
     }
     uint32_t phase = 0;
     for (; item < work; item += gridDim.x) {
-        const TileRef cur = tile_of<TX_, TY_>(a, item);
         const long long next = item + gridDim.x;
-        const int x0 = cur.x0, y0 = cur.y0;
-        const float *M = a.Mref + (size_t)__ldg(a.ref_idx + cur.pair) * plane;
         bool ok = hr_tma::mbar_wait(&bar[0], phase);
         ok = hr_tma::mbar_wait(&bar[1], phase) && ok;
         if (!__syncthreads_and(ok)) {
@@ -518,6 +526,9 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             return;
         }
         phase ^= 1u;
+        const TileRef cur = s_tile;
+        const int x0 = cur.x0, y0 = cur.y0;
+        const float *M = a.Mref + (size_t)s_ref * plane;
         // ---- replicate borders (tiles that reach outside the image only)
         const bool border = x0 - 2 * RAD < 0 || x0 - 2 * RAD + L::AST > w || y0 - 2 * RAD < 0 ||
                             y0 - 2 * RAD + L::AHP > h || x0 - G::FOFF < 0 || x0 - G::FOFF + G::FWB > w ||
@@ -539,8 +550,10 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             }
             __syncthreads();
             if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
+                tn = tile_of<TX_, TY_>(a, next);
+                publish(tn);
                 hr_tma::fence_proxy_async();
-                issue_S(tile_of<TX_, TY_>(a, next));
+                issue_S(tn);
             }
         }
         // ---- (the y pass of G_f runs inside the force stage below, on each
@@ -631,9 +644,13 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         }
         __syncthreads();
         if (tid == 0 && next < work) {   // the test-image tile (and u_0's) is consumed: fetch the next one
+            if constexpr (!IN_S) {
+                tn = tile_of<TX_, TY_>(a, next);
+                publish(tn);
+            }
             hr_tma::fence_proxy_async();
-            if constexpr (!IN_S) issue_S(tile_of<TX_, TY_>(a, next));
-            issue_F(tile_of<TX_, TY_>(a, next));
+            if constexpr (!IN_S) issue_S(tn);
+            issue_F(tn);
         }
         // ---- G_u * du: x pass on rows of T + r, columns of T
         constexpr int NSXD = TX_ / RUN;
