@@ -503,12 +503,16 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
     // all threads from shared memory after the barrier that opens the item (thread 0 overwrites it
     // with the next item only after a later barrier of the current one).
     __shared__ TileRef s_tile;
-    __shared__ int s_ref;
+    __shared__ int s_ref, s_border;
     long long item = blockIdx.x;
     TileRef tn;   // thread 0: the next item
     auto publish = [&](const TileRef &t) {
         s_tile = t;
         s_ref = __ldg(a.ref_idx + t.pair);
+        // tiles whose s or test-image box reaches outside the image get their edges replicated
+        s_border = t.x0 - 2 * RAD < 0 || t.x0 - 2 * RAD + L::AST > w || t.y0 - 2 * RAD < 0 ||
+                   t.y0 - 2 * RAD + L::AHP > h || t.x0 - G::FOFF < 0 || t.x0 - G::FOFF + G::FWB > w ||
+                   t.y0 - RAD - 1 < 0 || t.y0 - RAD - 1 + G::FH > h;
     };
     if (tid == 0 && item < work) {
         tn = tile_of<TX_, TY_>(a, item);
@@ -530,9 +534,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         const int x0 = cur.x0, y0 = cur.y0;
         const float *M = a.Mref + (size_t)s_ref * plane;
         // ---- replicate borders (tiles that reach outside the image only)
-        const bool border = x0 - 2 * RAD < 0 || x0 - 2 * RAD + L::AST > w || y0 - 2 * RAD < 0 ||
-                            y0 - 2 * RAD + L::AHP > h || x0 - G::FOFF < 0 || x0 - G::FOFF + G::FWB > w ||
-                            y0 - RAD - 1 < 0 || y0 - RAD - 1 + G::FH > h;
+        const bool border = s_border != 0;
         if (border) {
             fix_rows(sS, L::AST, L::AHP, L::AST, y0 - 2 * RAD, h);
             fix_rows(sF, G::FWB, G::FH, G::FWB, y0 - RAD - 1, h);
@@ -569,6 +571,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         // below by the replicated in-image values.  Rows of the last group beyond
         // T + r are computed from padding and discarded.
         float ssd = 0.0f;
+        const int rows_in = min(TY_, h - y0);   // rows of T inside the image
         constexpr int NG = (L::BH + FR - 1) / FR;
         constexpr int FC = G::FOFF - RAD;   // test-image column of local column 0
         for (int it = tid; it < NG * L::BW; it += NT) {
@@ -576,7 +579,9 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             const int r0 = FR * g;
             const int vx = x0 - RAD + c, vy0 = y0 - RAD + r0;
             const bool colT = c >= RAD && c < RAD + TX_ && vx < w;
-            const float sx = (vx == 0 || vx == w - 1) ? 1.0f : 0.5f;
+            // one-sided difference (scale 1) in the first and last column; columns outside the
+            // image are computed from replicated data and discarded
+            const float sx = (unsigned)(vx - 1) >= (unsigned)(w - 2) ? 1.0f : 0.5f;
             const float *fcol = sF + r0 * G::FWB + c + FC;   // test image, local rows r0 - 1 .. r0 + FR
             float fv[FR + 2], fl[FR], fr[FR];
 #pragma unroll
@@ -617,8 +622,8 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 const float2 mw = bilinear_pair_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y,
                                                         (float)vx - u[i + 1].x, (float)(vy0 + i + 1) - u[i + 1].y);
                 const int vya = vy0 + i, vyb = vya + 1;
-                const float2 sy2 = make_float2((vya == 0 || vya == h - 1) ? 1.0f : 0.5f,
-                                               (vyb == 0 || vyb == h - 1) ? 1.0f : 0.5f);
+                const float2 sy2 = make_float2((unsigned)(vya - 1) >= (unsigned)(h - 2) ? 1.0f : 0.5f,
+                                               (unsigned)(vyb - 1) >= (unsigned)(h - 2) ? 1.0f : 0.5f);
                 const float2 gx = __fmul2_rn(sx2, __ffma2_rn(make_float2(fl[i], fl[i + 1]), n1,
                                                              make_float2(fr[i], fr[i + 1])));
                 const float2 gy = __fmul2_rn(sy2, __ffma2_rn(make_float2(fv[i], fv[i + 1]), n1,
@@ -627,12 +632,12 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 const float2 den = __ffma2_rn(gx, gx, __ffma2_rn(gy, gy, __fmul2_rn(__fmul2_rn(al2, d), d)));
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const int r = r0 + i + j, vy = vya + j;
+                    const int r = r0 + i + j;
                     const float dj = j ? d.y : d.x, denj = j ? den.y : den.x;
                     const float t = denj > 1e-9f ? __fdividef(dj, denj) : 0.0f;
                     const float2 g = j ? make_float2(gx.y, gy.y) : make_float2(gx.x, gy.x);
                     if (L::BH % FR == 0 || r < L::BH) sD[r * L::DST + c] = __fmul2_rn(make_float2(t, t), g);
-                    if (colT && r >= RAD && r < RAD + TY_ && vy < h) ssd = fmaf(dj, dj, ssd);
+                    if (colT && (unsigned)(r - RAD) < (unsigned)rows_in) ssd = fmaf(dj, dj, ssd);
                 }
             }
         }
@@ -665,13 +670,14 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             const int seg = it / TX_, col = it - seg * TX_;
             float2 acc[RUN];
             run_y<RAD>(sX + seg * RUN * L::XDST + col, L::XDST, tu, acc);
-            const int gx = x0 + col;
+            const int gx = x0 + col, gy0 = y0 + seg * RUN;
+            if (gx < w) {
+                const int nrow = h - gy0;   // rows of this run inside the image (may exceed RUN)
+                float2 *p = dst + (size_t)gy0 * w + gx;
+                const float2 *su = sU + (seg * RUN + RAD) * L::UST + col + RAD;
 #pragma unroll
-            for (int o = 0; o < RUN; ++o) {
-                const int gy = y0 + seg * RUN + o;
-                if (gy < h && gx < w) {
-                    const float2 u = sU[(seg * RUN + o + RAD) * L::UST + col + RAD];
-                    dst[(size_t)gy * w + gx] = __fadd2_rn(u, acc[o]);
+                for (int o = 0; o < RUN; ++o) {
+                    if (o < nrow) p[(size_t)o * w] = __fadd2_rn(su[o * L::UST], acc[o]);
                 }
             }
         }
