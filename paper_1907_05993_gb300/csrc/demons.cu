@@ -179,6 +179,28 @@ __device__ __forceinline__ void run_x(const float2 *in, float2 *out, const float
 }
 
 // Same along a column: in[j * stride], j = 0..RUN + 2r - 1 -> acc[o].
+// run_x on a row whose columns outside [lo, hi] stand for the nearest of them
+// (the window is read column by column through clamped indices; same sums).
+template <int RAD>
+__device__ __forceinline__ void run_x_clamped(const float2 *row, int c0, int lo, int hi, float2 *out,
+                                              const float2 (&t)[2 * RAD + 1])
+{
+    constexpr int NW = RUN + 2 * RAD;
+    float2 win[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) win[j] = row[min(max(c0 + j, lo), hi)];
+    float2 acc[RUN];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o) acc[o] = __fmul2_rn(t[0], win[o]);
+#pragma unroll
+    for (int k = 1; k <= 2 * RAD; ++k)
+#pragma unroll
+        for (int o = 0; o < RUN; ++o) acc[o] = ffma2(t[k], win[o + k], acc[o]);
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+#pragma unroll
+    for (int o = 0; o < RUN; o += 2) out4[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
+}
+
 template <int RAD>
 __device__ __forceinline__ void run_y(const float2 *in, int stride, const float2 (&t)[2 * RAD + 1], float2 (&acc)[RUN])
 {
@@ -641,12 +663,6 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
                 }
             }
         }
-        if (border) {   // du outside the image = du at the clamped position
-            __syncthreads();
-            fix_rows(sD, L::DST, L::BH, L::BW, y0 - RAD, h);
-            __syncthreads();
-            fix_cols(sD, L::DST, L::BH, L::BW, x0 - RAD, w);
-        }
         __syncthreads();
         if (tid == 0 && next < work) {   // the test-image tile (and u_0's) is consumed: fetch the next one
             if constexpr (!IN_S) {
@@ -657,11 +673,25 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             if constexpr (!IN_S) issue_S(tn);
             issue_F(tn);
         }
-        // ---- G_u * du: x pass on rows of T + r, columns of T
+        // ---- G_u * du: x pass on rows of T + r, columns of T.  du outside the image is du at the
+        // clamped position: border tiles read rows and columns through clamped indices
         constexpr int NSXD = TX_ / RUN;
-        for (int it = tid; it < NSXD * L::BH; it += NT) {
-            const int seg = it / L::BH, row = it - seg * L::BH;
-            run_x<RAD>(sD + row * L::DST + seg * RUN, sX + row * L::XDST + seg * RUN, tu);
+        if (!border) {
+            for (int it = tid; it < NSXD * L::BH; it += NT) {
+                const int seg = it / L::BH, row = it - seg * L::BH;
+                run_x<RAD>(sD + row * L::DST + seg * RUN, sX + row * L::XDST + seg * RUN, tu);
+            }
+        } else {
+            const int rlo = max(0, RAD - y0), rhi = L::BH - 1 - max(0, y0 - RAD + L::BH - h);
+            const int clo = max(0, RAD - x0), chi = L::BW - 1 - max(0, x0 - RAD + L::BW - w);
+            for (int it = tid; it < NSXD * L::BH; it += NT) {
+                const int seg = it / L::BH, row = it - seg * L::BH;
+                const int rs = min(max(row, rlo), rhi), c0 = seg * RUN;
+                if (c0 >= clo && c0 + RUN + 2 * RAD - 1 <= chi)
+                    run_x<RAD>(sD + rs * L::DST + c0, sX + row * L::XDST + c0, tu);
+                else
+                    run_x_clamped<RAD>(sD + rs * L::DST, c0, clo, chi, sX + row * L::XDST + c0, tu);
+            }
         }
         __syncthreads();
         // ---- y pass, s_{k+1} = u_k + G_u * du on T
