@@ -473,6 +473,33 @@ __device__ __forceinline__ void fix_cols(T *t, int st, int nr, int nc, int g0c, 
     }
 }
 
+// Replicate edges in one pass: every element of the tile outside the image
+// (rows [g0r, g0r + nr) and columns [g0c, g0c + nc) in image coordinates)
+// takes the value at the nearest in-image row and column.  Sources are
+// in-image elements, which are never written, so no barrier is needed between
+// rows and columns (the result equals fix_rows followed by fix_cols).
+template <typename T>
+__device__ __forceinline__ void fix_frame(T *t, int st, int nr, int nc, int g0r, int g0c, int himg, int wimg)
+{
+    const int top = max(0, -g0r), bot = max(0, g0r + nr - himg);
+    const int left = max(0, -g0c), right = max(0, g0c + nc - wimg);
+    const int rhi = nr - bot - 1, chi = nc - right - 1;
+    const int n1 = (top + bot) * nc, ncol = left + right, n = n1 + (nr - top - bot) * ncol;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        int r, c;
+        if (idx < n1) {
+            const int k = idx / nc;
+            c = idx - k * nc;
+            r = k < top ? k : nr - bot + (k - top);
+        } else {
+            const int q = idx - n1, k = q / ncol, m = q - k * ncol;
+            r = top + k;
+            c = m < left ? m : nc - right + (m - left);
+        }
+        t[r * st + c] = t[min(max(r, top), rhi) * st + min(max(c, left), chi)];
+    }
+}
+
 // IN_S: the input is s_k (u = G_f * s); false for the first iteration of a
 // level, whose input is the prolonged field u_0 itself.
 template <int RAD, int TX_, int TY_, int MINB, int NT_, int FR, bool IN_S = true>
@@ -557,20 +584,36 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         const float *M = a.Mref + (size_t)s_ref * plane;
         // ---- replicate borders (tiles that reach outside the image only)
         const bool border = s_border != 0;
+        // (the test-image tile is read in the force stage: its out-of-image elements are filled
+        // here, before the barrier that ends the x pass; the s tile is read only by the x pass,
+        // which goes through clamped indices on border tiles; u_0 is read directly, so its tile
+        // is filled too, followed by a barrier)
         if (border) {
-            fix_rows(sS, L::AST, L::AHP, L::AST, y0 - 2 * RAD, h);
-            fix_rows(sF, G::FWB, G::FH, G::FWB, y0 - RAD - 1, h);
-            __syncthreads();
-            fix_cols(sS, L::AST, L::AHP, L::AST, x0 - 2 * RAD, w);
-            fix_cols(sF, G::FWB, G::FH, G::FWB, x0 - G::FOFF, w);
-            __syncthreads();
+            fix_frame(sF, G::FWB, G::FH, G::FWB, y0 - RAD - 1, x0 - G::FOFF, h, w);
+            if constexpr (!IN_S) {
+                fix_frame(sS, L::AST, L::AHP, L::AST, y0 - 2 * RAD, x0 - 2 * RAD, h, w);
+                __syncthreads();
+            }
         }
         // ---- u = G_f * s on T + r
         if constexpr (IN_S) {
             constexpr int NSX = L::BWP / RUN;
-            for (int it = tid; it < NSX * L::AHP; it += NT) {
-                const int seg = it / L::AHP, row = it - seg * L::AHP;
-                run_x<RAD>(sS + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
+            if (!border) {
+                for (int it = tid; it < NSX * L::AHP; it += NT) {
+                    const int seg = it / L::AHP, row = it - seg * L::AHP;
+                    run_x<RAD>(sS + row * L::AST + seg * RUN, sX + row * L::XST + seg * RUN, tf);
+                }
+            } else {   // s outside the image = s at the clamped position
+                const int rlo = max(0, 2 * RAD - y0), rhi = L::AHP - 1 - max(0, y0 - 2 * RAD + L::AHP - h);
+                const int clo = max(0, 2 * RAD - x0), chi = L::AST - 1 - max(0, x0 - 2 * RAD + L::AST - w);
+                for (int it = tid; it < NSX * L::AHP; it += NT) {
+                    const int seg = it / L::AHP, row = it - seg * L::AHP;
+                    const int rs = min(max(row, rlo), rhi), c0 = seg * RUN;
+                    if (c0 >= clo && c0 + RUN + 2 * RAD - 1 <= chi)
+                        run_x<RAD>(sS + rs * L::AST + c0, sX + row * L::XST + c0, tf);
+                    else
+                        run_x_clamped<RAD>(sS + rs * L::AST, c0, clo, chi, sX + row * L::XST + c0, tf);
+                }
             }
             __syncthreads();
             if (tid == 0 && next < work) {   // the s tile is consumed: fetch the next one
