@@ -570,6 +570,14 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         issue_F(tn);
     }
     uint32_t phase = 0;
+    // thread 0: the SSD partial of the previous item, summed from red[] after the barrier that
+    // opens the next item (or the one after the loop), so no barrier closes an item
+    int prev_pair = -1, prev_tile = 0;
+    auto write_partial = [&]() {
+        float t = 0.0f;
+        for (int i = 0; i < NT / 32; ++i) t += red[i];
+        a.part[(size_t)prev_pair * a.tiles + prev_tile] = t;
+    };
     for (; item < work; item += gridDim.x) {
         const long long next = item + gridDim.x;
         bool ok = hr_tma::mbar_wait(&bar[0], phase);
@@ -578,6 +586,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             if (tid == 0) atomicExch(a.err, 1);
             return;
         }
+        if (tid == 0 && prev_pair >= 0) write_partial();
         phase ^= 1u;
         const TileRef cur = s_tile;
         const int x0 = cur.x0, y0 = cur.y0;
@@ -756,13 +765,13 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         }
         for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
         if (lane == 0) red[warp] = ssd;
-        __syncthreads();
         if (tid == 0) {
-            float t = 0.0f;
-            for (int i = 0; i < NT / 32; ++i) t += red[i];
-            a.part[(size_t)cur.pair * a.tiles + cur.tile] = t;
+            prev_pair = cur.pair;
+            prev_tile = cur.tile;
         }
     }
+    __syncthreads();
+    if (tid == 0 && prev_pair >= 0) write_partial();
 }
 
 struct CtrlArgs {
