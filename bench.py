@@ -172,13 +172,26 @@ def xcf_roofline(ms, B, wl, fp32_peak_tflops, hbm_peak):
             "algorithmic": f"{flops / B / 1e6:.2f} MFLOP and {nbytes / B / 1e3:.0f} KB per pair"}
 
 
+def code_digest(path):
+    """SHA-256 of a C/CUDA source with its // comments, trailing blanks and empty lines removed: a
+    change of the code (not of its comments) changes it.  The demons sources hold no '//' inside
+    string literals."""
+    lines = []
+    for line in open(path, encoding="utf-8").read().splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def traffic_per_launch(px_per_launch):
-    """DRAM bytes per demons-iteration launch from the committed ncu summary, if it still matches the kernel."""
+    """DRAM bytes per demons-iteration launch from the committed ncu summary, if the kernel's code is
+    still the one that was captured."""
     path = os.path.join(ROOT, "profiles", "demons_iter_traffic.json")
     try:
         d = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_1907_05993_gb300", "csrc", "demons.cu"), "rb").read()
-        if d.get("demons_cu_sha256") != hashlib.sha256(src).hexdigest():
+        src = os.path.join(ROOT, "paper_1907_05993_gb300", "csrc", "demons.cu")
+        if d.get("demons_cu_code_sha256") != code_digest(src):
             return None
         return d["dram_bytes_per_pixel_iter"] * px_per_launch
     except Exception:

@@ -9,7 +9,8 @@
 // the per-pair test pyramid and the field buffers stream from HBM.
 //
 // One demons iteration u_{k+1} = G_f * (u_k + G_u * du(u_k)) is ONE fused
-// kernel launch over every (active pair, 64x32 tile).  The launch stores the
+// kernel launch over every (active pair, tile) (tile shapes 64x64, 64x32,
+// 32x32, 64x16, autotuned per level size).  The launch stores the
 // unsmoothed field s_{k+1} = u_k + G_u * du(u_k) instead of u_{k+1}; the next
 // launch recomputes u_{k+1} = G_f * s_{k+1} on the fly from a tile with a
 // 2r halo (r the Gaussian radius).  This keeps the expensive part (warp +
@@ -20,11 +21,12 @@
 // of RUN + 2r samples per thread in registers (RUN outputs per thread) and
 // use packed FP32x2 FMAs for the two field components.
 //
-// Border handling: every Gaussian pass has replicated borders.  Tiles load s
-// with clamped addresses (so out-of-image halo values are the replicated
-// ones) and evaluate the force at the clamped position of every halo point;
-// with that, every value the passes read at an in-image position is exact, and
-// out-of-image values are never consumed by an in-image output.
+// Border handling: every Gaussian pass has replicated borders.  The passes
+// read s and du at clamped positions (plain path: clamped addresses; TMA
+// path: clamped shared-memory indices on tiles that reach outside the image)
+// and the test image's out-of-image values are those of the nearest in-image
+// pixel; with that, every value the passes read at an in-image position is
+// exact, and out-of-image values are never consumed by an in-image output.
 //
 // Uneven work (a9): pairs stop independently (stop rule on the SSD history).
 // A small control kernel after each iteration compacts the list of active
@@ -417,17 +419,19 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_kernel(IterArgs a
 }
 
 // ---------------------------------------------------------------------------
-// TMA-fed iteration (k > 0, r > 0).  The s tile (T + 2r, padded) and the test
-// image tile (T + r + 1, widened to 16-byte-aligned columns) arrive by bulk
-// tensor copies issued by one thread, so the other threads spend no
-// instructions on loads: the s copy for the next item is issued as soon as
-// the x pass has consumed the current s tile, the test-image copy as soon as
-// the force stage has consumed the current one.  The copy fills out-of-image
-// elements with zeros; border tiles then replicate the edge rows/columns in
-// shared memory (the clamped-address semantics of the plain path).  The
-// force stage works on runs of 4 pixels per thread with the gradient stencil
-// and field read once per run; runs that touch the image border take the
-// per-pixel clamped path.
+// TMA-fed iteration (every iteration for r = 3, k > 0 for other radii; the
+// first iteration of a level reads u_0 instead of s).  The s tile (T + 2r,
+// padded) and the test image tile (T + r + 1, widened to 16-byte-aligned
+// columns) arrive by bulk tensor copies issued by one thread, so the other
+// threads spend no instructions on loads: the s copy for the next item is
+// issued as soon as the x pass has consumed the current s tile, the
+// test-image copy as soon as the force stage has consumed the current one.
+// The copy fills out-of-image elements with zeros; on border tiles the x
+// passes read s and du through clamped indices and the test image's
+// out-of-image elements are filled from the nearest in-image ones (the
+// clamped-address semantics of the plain path).  The force stage works on
+// vertical runs of 4 pixels per thread with the gradient stencil and field
+// read once per run.
 template <int RAD, int TX_, int TY_>
 struct GeoT {
     using L = Geo<RAD, TX_, TY_>;
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         const TileRef cur = s_tile;
         const int x0 = cur.x0, y0 = cur.y0;
         const float *M = a.Mref + (size_t)s_ref * plane;
-        // ---- replicate borders (tiles that reach outside the image only)
+        // ---- tiles that reach outside the image
         const bool border = s_border != 0;
         // (the test-image tile is read in the force stage: its out-of-image elements are filled
         // here, before the barrier that ends the x pass; the s tile is read only by the x pass,
@@ -641,9 +645,9 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
         // accesses conflict-free).  Every run is computed the same way (no
         // divergent border path): the test-image tile has replicated borders, so
         // the central difference becomes the one-sided one at the image edge once
-        // scaled by 1 instead of 1/2; points outside the image are overwritten
-        // below by the replicated in-image values.  Rows of the last group beyond
-        // T + r are computed from padding and discarded.
+        // scaled by 1 instead of 1/2; du at points outside the image is computed
+        // but never read (the x pass of du reads the clamped positions).  Rows of
+        // the last group beyond T + r are computed from padding and discarded.
         float ssd = 0.0f;
         const int rows_in = min(TY_, h - y0);   // rows of T inside the image
         constexpr int NG = (L::BH + FR - 1) / FR;
