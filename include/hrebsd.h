@@ -48,6 +48,8 @@ extern "C" {
 #define HREBSD_ENOMEM -3   /* workspace allocation failed */
 #define HREBSD_ETIMEOUT -4 /* a bounded device-side wait expired */
 #define HREBSD_ESCRATCH -5 /* request larger than the static scratch of hrebsd_demons_register_batch_noalloc */
+#define HREBSD_EIO -6      /* a file could not be opened, read or written */
+#define HREBSD_EFORMAT -7  /* a model file is not one this library wrote for this network */
 
 /* pair_status bits */
 #define HREBSD_PAIR_CAPPED 1      /* some pyramid level stopped at its iteration cap */
@@ -142,6 +144,16 @@ typedef struct {
     int start_level;
 } hrebsd_demons_params;
 
+/* The Gaussian of the field regularisation (Section 1; the workloads smooth
+ * the update and the field with it): radius r = ceil(3 sigma) (at most 6),
+ * taps[0 .. 2r] = exp(-k^2 / 2 sigma^2) normalised, k = -r .. r, in FP32.  The
+ * FP32 taps are chosen so that their exact sum is one (the rounded weights
+ * alone would leave it a few 1e-8 short, a systematic shrink of the field by
+ * that much at every smoothing pass); the smallest outer tap may differ from
+ * its rounded weight by a few units in the last place.  Host only, no GPU.
+ * Returns r (taps[0 .. 2r] written) or HREBSD_EINVAL (null taps, r > 6). */
+int hrebsd_gauss_taps(float sigma, float *taps);
+
 /* a1 -- intensity normalisation (Section 2) with static background
  * correction (Section 3.3): for each of the n patterns in [n][H][W], if
  * `flat` the least-squares quadric c0 + c1 x + c2 y + c3 x^2 + c4 xy + c5 y^2
@@ -188,16 +200,17 @@ int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, const float 
                                  void *stream);
 
 /* Allocation-free variant of hrebsd_demons_register_batch (the paper has no
- * counterpart; it exists for callers that cannot allocate device memory:
- * code recorded into a CUDA graph, where cudaMalloc cannot be captured, and
- * hosts or plugins that fix the device-memory budget or own the allocator).
+ * counterpart).  It exists for callers that cannot allocate device memory:
+ * hosts that fix the device-memory budget before they start, plugins whose
+ * host application owns the allocator, and latency-bound services that may not
+ * allocate (a cudaMalloc can synchronise the device) while serving a request.
  * Same arguments, outputs and results as hrebsd_demons_register_batch, but
  * the workspace is a static device array of HREBSD_NOALLOC_SCRATCH_BYTES
  * (16 MiB) inside this library, held by every process that loads it on each
  * device it uses, until exit; the call never calls cudaMalloc/cudaFree or any
  * allocating routine.  The first call on a device looks the array's device
  * address up (cudaGetSymbolAddress) with that device current: make that first
- * call outside any stream capture.  The whole batch must fit: about
+ * call before any stream capture.  The whole batch must fit: about
  * 8 B x 3 x H x W + 8 B x H x W / 4 + 4 B x H x W / 3 per pair plus small
  * per-pair lists (about 9 pairs of 256 x 256 with 4 levels, or 37 pairs of
  * 128 x 128 with 3 levels);
@@ -273,12 +286,33 @@ int hrebsd_xcf_roi_batch(hrebsd_ctx *ctx, const float *remapped, const float *te
 
 /* a8 -- second-pass deformation gradient (Eq. 3 on the XCF shifts, Eq. 12):
  * r_i = c_i, r'_i = c_i + q_i, F_inf by the same FP64 fit as
- * hrebsd_fit_rotation (det F_inf = 1), F = F_inf R_finite (R_finite may be
- * NULL: F = F_inf).  F [B][9]; pair_status |= FIT_FAILED on a singular fit
- * (may be NULL). */
+ * hrebsd_fit_rotation, F = F_inf R_finite (R_finite may be NULL: F = F_inf).
+ * Eq. 3 fixes F only up to a scale (F and lambda F project every point to the
+ * same place); `normalization` picks it:
+ *   HREBSD_NORM_DET1: det F = 1 (elastic is ignored and may be NULL);
+ *   HREBSD_NORM_TRACTION_FREE: the traction-free condition of Section 2
+ *     (Eq. 16 with sigma_33 = 0 at the free surface): F = lambda F_det1 with
+ *     lambda > 0 such that the stress C_S : 1/2 (F_S F_S^T - I) of
+ *     F_S = T F T^T (the tilt of Eq. 13-14) has a zero 33 component, C_S the
+ *     cubic stiffness (elastic->c11, c12, c44) rotated to the sample frame by
+ *     elastic->g[ref_idx[b]] as in hrebsd_strain_stress.  A pair whose
+ *     condition has no positive solution, or whose ref_idx is outside [0, R),
+ *     gets F = NaN and FIT_FAILED.
+ * F [B][9]; pair_status |= FIT_FAILED on a singular fit (may be NULL).
+ * Errors: EINVAL (sizes, null pointers, unknown normalization, missing elastic
+ * data for TRACTION_FREE). */
+#define HREBSD_NORM_DET1 0
+#define HREBSD_NORM_TRACTION_FREE 1
+typedef struct {
+    double tilt_rad;          /* sample tilt theta of Eq. 13 */
+    double c11, c12, c44;     /* cubic stiffness in crystal axes, Pa (nickel: 276e9, 159e9, 132e9) */
+    const double *g;          /* device [R][9]: passive orientation matrix (sample -> crystal) per reference */
+    const int32_t *ref_idx;   /* device [B], nullable: every pair uses g[0] */
+    int R;
+} hrebsd_elastic;
 int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N, int B, int H, int W,
-                   const hrebsd_geometry *geom, const double *R_finite, double *F, int32_t *pair_status,
-                   void *stream);
+                   const hrebsd_geometry *geom, const double *R_finite, int normalization,
+                   const hrebsd_elastic *elastic, double *F, int32_t *pair_status, void *stream);
 
 /* f2 -- pattern preprocessing for real scans (Section 3.2-3.3).  The paper
  * names the steps without kernels; the readings (FP32, replicated borders):
@@ -403,6 +437,18 @@ int hrebsd_cnn_get_params(hrebsd_ctx *ctx, float *params_host, float *grads_host
  * network (get), a NULL moment or a negative step (set). */
 int hrebsd_cnn_get_state(hrebsd_ctx *ctx, float *m_host, float *v_host, int *step);
 int hrebsd_cnn_set_state(hrebsd_ctx *ctx, const float *m_host, const float *v_host, int step);
+/* Model file (weights, Adam moments and step; the paper has no learned part,
+ * so the format is this library's own: magic "HRCNN001", int64 parameter
+ * count, int64 step, FP32 parameters, first and second moments, and an FNV-1a
+ * hash of all preceding bytes; little-endian).  hrebsd_cnn_save synchronises
+ * the device and writes the network of the context (EINVAL if it has none) to
+ * `path` through a temporary file renamed into place (an interrupted save
+ * leaves an earlier file intact).  hrebsd_cnn_load replaces the context's
+ * network state by the file's, so that training continues exactly where the
+ * saved context stood.  Errors: EIO (open/read/write/rename failed), EFORMAT
+ * (wrong magic, parameter count, size or hash: nothing is loaded). */
+int hrebsd_cnn_save(hrebsd_ctx *ctx, const char *path);
+int hrebsd_cnn_load(hrebsd_ctx *ctx, const char *path);
 /* Inference on x [B][2][64][64] BF16 (channel 0 reference, 1 test) -> field64 [B][2][64][64] FP32. */
 int hrebsd_cnn_infer(hrebsd_ctx *ctx, const uint16_t *x_bf16, int B, float *field64, void *stream);
 /* Inference from preprocessed patterns (as for the registration): the input is

@@ -20,13 +20,13 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
+    "hrebsd_solve_F", "hrebsd_elastic", "elastic_params", "NORM_DET1", "NORM_TRACTION_FREE", "hrebsd_cnn_save", "hrebsd_cnn_load", "hrebsd_gauss_taps", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
     "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_wait_selftest", "hrebsd_cnn_get_state", "hrebsd_cnn_set_state", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
     "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
 
 PAIR_CAPPED, PAIR_NONFINITE, PAIR_FIT_FAILED = 1, 2, 4
-ETIMEOUT, ESCRATCH = -4, -5
+ETIMEOUT, ESCRATCH, EIO, EFORMAT = -4, -5, -6, -7
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lib = None
@@ -41,6 +41,14 @@ class HrebsdError(RuntimeError):
 
 class hrebsd_geometry(C.Structure):
     _fields_ = [("xstar", C.c_double), ("ystar", C.c_double), ("zstar", C.c_double)]
+
+
+class hrebsd_elastic(C.Structure):
+    _fields_ = [("tilt_rad", C.c_double), ("c11", C.c_double), ("c12", C.c_double), ("c44", C.c_double),
+                ("g", C.c_void_p), ("ref_idx", C.c_void_p), ("R", C.c_int)]
+
+
+NORM_DET1, NORM_TRACTION_FREE = 0, 1
 
 
 class hrebsd_profile(C.Structure):
@@ -97,7 +105,8 @@ def load(build: bool = False):
         "hrebsd_fit_rotation": (i, [vp, vp, i, i, i, vp, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
         "hrebsd_remap": (i, [vp, vp, vp, vp, i, i, i, C.POINTER(hrebsd_geometry), vp, vp]),
         "hrebsd_xcf_roi_batch": (i, [vp, vp, vp, i, i, i, vp, i, i, i, vp, vp, vp, vp, vp]),
-        "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, vp, vp, vp]),
+        "hrebsd_solve_F": (i, [vp, vp, vp, i, i, i, i, C.POINTER(hrebsd_geometry), vp, i, C.POINTER(hrebsd_elastic), vp,
+                               vp, vp]),
         "hrebsd_downsample_batch": (i, [vp, vp, i, i, i, i, vp, vp]),
         "hrebsd_field_resample": (i, [vp, vp, i, i, i, vp, i, i, vp]),
         "hrebsd_autotune": (i, [vp, i, i, i, C.POINTER(hrebsd_demons_params), vp, vp]),
@@ -120,6 +129,9 @@ def load(build: bool = False):
         "hrebsd_cnn_get_params": (i, [vp, vp, vp]),
         "hrebsd_cnn_get_state": (i, [vp, vp, vp, C.POINTER(C.c_int)]),
         "hrebsd_cnn_set_state": (i, [vp, vp, vp, i]),
+        "hrebsd_cnn_save": (i, [vp, C.c_char_p]),
+        "hrebsd_gauss_taps": (i, [C.c_float, C.POINTER(C.c_float)]),
+        "hrebsd_cnn_load": (i, [vp, C.c_char_p]),
         "hrebsd_cnn_infer": (i, [vp, vp, i, vp, vp]),
         "hrebsd_cnn_infer_patterns": (i, [vp, vp, vp, vp, i, i, i, vp, vp]),
         "hrebsd_cnn_train_step": (i, [vp, vp, vp, i, C.c_float, vp, vp]),
@@ -264,11 +276,25 @@ def hrebsd_xcf_roi_batch(ctx, remapped, test, B, H, W, roi_xy, N, S, window, q, 
          "hrebsd_xcf_roi_batch")
 
 
-def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, stream=None):
+def hrebsd_solve_F(ctx, q, roi_xy, N, B, H, W, geom, R_finite, F, pair_status, stream=None,
+                   normalization=0, elastic=None):
+    """normalization: NORM_DET1 (default) or NORM_TRACTION_FREE, which needs ``elastic``
+    (an hrebsd_elastic, see ``elastic_params``)."""
     t = _t()
     _chk(load().hrebsd_solve_F(ctx, _p(q, t.float32), _p(roi_xy, t.int32), N, B, H, W, C.byref(geom),
-                               _p(R_finite, t.float64), _p(F, t.float64), _p(pair_status, t.int32), _s(stream)),
+                               _p(R_finite, t.float64), int(normalization),
+                               None if elastic is None else C.byref(elastic), _p(F, t.float64),
+                               _p(pair_status, t.int32), _s(stream)),
          "hrebsd_solve_F")
+
+
+def elastic_params(g, R, tilt_rad, stiffness=None, ref_idx=None):
+    """hrebsd_elastic for the traction-free normalisation: g [R, 9] float64 CUDA orientation matrices,
+    ref_idx [B] int32 CUDA or None.  The struct holds raw device addresses: keep g and ref_idx alive."""
+    t = _t()
+    c11, c12, c44 = NI_STIFFNESS if stiffness is None else stiffness
+    return hrebsd_elastic(float(tilt_rad), float(c11), float(c12), float(c44), _p(g, t.float64),
+                          _p(ref_idx, t.int32), int(R))
 
 
 TILE_VARIANTS = 5
@@ -415,6 +441,25 @@ def hrebsd_cnn_set_state(ctx, m, v, step):
     if m.size != n or v.size != n:
         raise ValueError(f"Adam moments need {n} entries each")
     _chk(load().hrebsd_cnn_set_state(ctx, m.ctypes.data, v.ctypes.data, int(step)), "hrebsd_cnn_set_state")
+
+
+def hrebsd_gauss_taps(sigma):
+    """FP32 taps of the registration's Gaussian (numpy float32 [2r + 1]); host only."""
+    import numpy as np
+    buf = (C.c_float * 13)()
+    r = load().hrebsd_gauss_taps(float(sigma), buf)
+    _chk(min(r, 0), "hrebsd_gauss_taps")
+    return np.array(buf[: 2 * r + 1], dtype=np.float32)
+
+
+def hrebsd_cnn_save(ctx, path):
+    """Write the network's weights, Adam moments and step to ``path`` (the library's model file)."""
+    _chk(load().hrebsd_cnn_save(ctx, os.fsencode(path)), "hrebsd_cnn_save")
+
+
+def hrebsd_cnn_load(ctx, path):
+    """Replace the network state of the context by the model file at ``path``."""
+    _chk(load().hrebsd_cnn_load(ctx, os.fsencode(path)), "hrebsd_cnn_load")
 
 
 def hrebsd_cnn_infer(ctx, x_bf16, B, field64, stream=None):

@@ -8,6 +8,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <vector>
 
@@ -882,6 +883,92 @@ extern "C" int hrebsd_cnn_set_state(hrebsd_ctx *ctx, const float *m_host, const 
     HR_CHECK(cudaMemcpy(ctx->cnn->M, m_host, ctx->cnn->n_params * 4, cudaMemcpyHostToDevice));
     HR_CHECK(cudaMemcpy(ctx->cnn->V, v_host, ctx->cnn->n_params * 4, cudaMemcpyHostToDevice));
     ctx->cnn->step = step;
+    return HREBSD_OK;
+}
+
+// Model file of the learned initialiser (project format, little-endian):
+//   bytes 0-7   magic "HRCNN001"
+//   8-15        int64 number of parameters n
+//   16-23       int64 Adam step count
+//   then        float32 parameters [n], Adam first moments [n], second moments [n]
+//   last 8      uint64 FNV-1a hash of every byte before it
+// The hash makes a truncated or damaged file fail to load instead of loading
+// wrong weights.  The file is written under a temporary name and renamed, so
+// an interrupted save leaves an earlier file of that name intact.
+namespace {
+
+constexpr char kCnnMagic[8] = {'H', 'R', 'C', 'N', 'N', '0', '0', '1'};
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t h)
+{
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+constexpr uint64_t kFnvBasis = 0xcbf29ce484222325ull;
+
+}  // namespace
+
+extern "C" int hrebsd_cnn_save(hrebsd_ctx *ctx, const char *path)
+{
+    if (!ctx || !ctx->cnn || !path || !*path) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e) return e;
+    const hr_cnn_net *n = ctx->cnn;
+    const size_t np = n->n_params, body = 24 + 3 * np * 4;
+    std::vector<unsigned char> buf(body + 8);
+    memcpy(buf.data(), kCnnMagic, 8);
+    const int64_t hdr[2] = {(int64_t)np, (int64_t)n->step};
+    memcpy(buf.data() + 8, hdr, 16);
+    HR_CHECK(cudaDeviceSynchronize());
+    HR_CHECK(cudaMemcpy(buf.data() + 24, n->W, np * 4, cudaMemcpyDeviceToHost));
+    HR_CHECK(cudaMemcpy(buf.data() + 24 + np * 4, n->M, np * 4, cudaMemcpyDeviceToHost));
+    HR_CHECK(cudaMemcpy(buf.data() + 24 + 2 * np * 4, n->V, np * 4, cudaMemcpyDeviceToHost));
+    const uint64_t h = fnv1a(buf.data(), body, kFnvBasis);
+    memcpy(buf.data() + body, &h, 8);
+    std::vector<char> tmp(strlen(path) + 32);
+    snprintf(tmp.data(), tmp.size(), "%s.tmp%ld", path, (long)getpid());
+    FILE *f = fopen(tmp.data(), "wb");
+    if (!f) return HREBSD_EIO;
+    const bool ok = fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok || rename(tmp.data(), path) != 0) {
+        remove(tmp.data());
+        return HREBSD_EIO;
+    }
+    return HREBSD_OK;
+}
+
+extern "C" int hrebsd_cnn_load(hrebsd_ctx *ctx, const char *path)
+{
+    if (!ctx || !path || !*path) return HREBSD_EINVAL;
+    int e = hr_set_device(ctx);
+    if (e || (e = ensure_net(ctx))) return e;
+    hr_cnn_net *n = ctx->cnn;
+    const size_t np = n->n_params, body = 24 + 3 * np * 4;
+    FILE *f = fopen(path, "rb");
+    if (!f) return HREBSD_EIO;
+    std::vector<unsigned char> buf(body + 8);
+    const size_t got = fread(buf.data(), 1, buf.size(), f);
+    const int extra = fgetc(f);   // the file must end here
+    fclose(f);
+    if (got < 24 || memcmp(buf.data(), kCnnMagic, 8) != 0) return HREBSD_EFORMAT;
+    int64_t hdr[2];
+    memcpy(hdr, buf.data() + 8, 16);
+    if (hdr[0] != (int64_t)np || hdr[1] < 0 || hdr[1] > 0x7fffffff) return HREBSD_EFORMAT;
+    if (got != buf.size() || extra != EOF) return HREBSD_EFORMAT;
+    uint64_t h;
+    memcpy(&h, buf.data() + body, 8);
+    if (h != fnv1a(buf.data(), body, kFnvBasis)) return HREBSD_EFORMAT;
+    HR_CHECK(cudaDeviceSynchronize());
+    HR_CHECK(cudaMemcpy(n->W, buf.data() + 24, np * 4, cudaMemcpyHostToDevice));
+    HR_CHECK(cudaMemcpy(n->M, buf.data() + 24 + np * 4, np * 4, cudaMemcpyHostToDevice));
+    HR_CHECK(cudaMemcpy(n->V, buf.data() + 24 + 2 * np * 4, np * 4, cudaMemcpyHostToDevice));
+    n->step = (int)hdr[1];
+    if ((e = refresh_bf16(ctx, 0))) return e;
+    HR_CHECK(cudaDeviceSynchronize());
     return HREBSD_OK;
 }
 

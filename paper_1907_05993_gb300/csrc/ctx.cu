@@ -51,6 +51,17 @@ int hr_gauss_radius(float sigma)
     return r;
 }
 
+// FP32 taps whose exact sum is one.  Rounding each normalised weight to FP32
+// on its own leaves the sum off by a few 1e-8 (1 - 2.8e-8 at sigma = 1); the
+// field smoothing applies the taps twice per iteration, so a registration of
+// a few hundred iterations would scale the whole field by ~1e-5 (a systematic
+// shrink).  Instead the outer taps are rounded to multiples of one quantum q
+// (the unit in the last place of the largest outer tap, or half that of the
+// centre tap if coarser: every such multiple is an FP32 value), so that the
+// centre tap 1 - 2 sum_{k>0} t_k is exactly representable and the taps sum
+// to one exactly.  The outer taps stay within half a quantum (at most half a
+// unit in the last place of the centre tap) of their normalised weights; the
+// centre tap takes up the sum of their rounding errors.
 int hr_gauss_taps(float sigma, int rad, float *taps)
 {
     int r = hr_gauss_radius(sigma);
@@ -60,13 +71,35 @@ int hr_gauss_taps(float sigma, int rad, float *taps)
         taps[rad] = 1.0f;
         return 0;
     }
-    double w[13], s = 0.0;
-    for (int k = -r; k <= r; ++k) {
-        w[k + r] = exp(-(double)(k * k) / (2.0 * (double)sigma * (double)sigma));
-        s += w[k + r];
+    double w[7], s = 0.0;
+    for (int k = -r; k <= r; ++k) s += exp(-(double)(k * k) / (2.0 * (double)sigma * (double)sigma));
+    for (int k = 0; k <= r; ++k) w[k] = exp(-(double)(k * k) / (2.0 * (double)sigma * (double)sigma)) / s;
+    auto ulp = [](double v) {
+        const float f = (float)v;
+        return (double)nextafterf(f, 2.0f * f + 1.0f) - (double)f;
+    };
+    double q = fmax(ulp(w[1]), 0.5 * ulp(w[0]));
+    float t[7];
+    for (int attempt = 0; attempt < 8; ++attempt, q *= 2.0) {
+        double S = 0.0;   // exact: every term is a multiple of q below 1
+        for (int k = 1; k <= r; ++k) {
+            t[k] = (float)(q * nearbyint(w[k] / q));
+            S += (double)t[k];
+        }
+        const double c = 1.0 - 2.0 * S;
+        t[0] = (float)c;
+        if ((double)t[0] == c) break;
     }
-    for (int k = -r; k <= r; ++k) taps[rad + k] = (float)(w[k + r] / s);
+    for (int k = -r; k <= r; ++k) taps[rad + k] = t[k < 0 ? -k : k];
     return r;
+}
+
+extern "C" int hrebsd_gauss_taps(float sigma, float *taps)
+{
+    if (!taps) return HREBSD_EINVAL;
+    const int r = hr_gauss_radius(sigma);
+    if (r > 6) return HREBSD_EINVAL;
+    return hr_gauss_taps(sigma, r, taps) < 0 ? HREBSD_EINVAL : r;
 }
 
 // Set by kernels whose bounded wait on an asynchronous copy gave up.
@@ -217,6 +250,8 @@ const char *hrebsd_status_string(int status)
     case HREBSD_ENOMEM: return "out of device memory";
     case HREBSD_ETIMEOUT: return "bounded device wait expired";
     case HREBSD_ESCRATCH: return "request exceeds the static scratch array of the allocation-free entry point";
+    case HREBSD_EIO: return "file could not be opened, read or written";
+    case HREBSD_EFORMAT: return "not a model file of this network (wrong header, size or checksum)";
     default: return "unknown status";
     }
 }

@@ -35,6 +35,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.cuh"
 #include "tma.cuh"
 
@@ -989,8 +991,15 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float2 *u0, con
 constexpr int kTileVariants = 5;
 constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64};
 constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64};
-constexpr int kMinTX = 32, kMinTY = 16;
-bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }   // smallest tile extents (sizes the SSD partials)
+constexpr int kMinTX = 32, kMinTY = 16;   // smallest tile extents (size the per-tile SSD partials)
+bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }
+constexpr bool min_extents_ok()
+{
+    for (int v = 0; v < kTileVariants; ++v)
+        if (kVarTX[v] < kMinTX || kVarTY[v] < kMinTY) return false;
+    return TX >= kMinTX && TY >= kMinTY;
+}
+static_assert(min_extents_ok(), "kMinTX/kMinTY must not exceed any tile shape (the SSD partials are sized by them)");
 static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
 
 int hr_tuned_variant(const hrebsd_ctx *ctx, int rad, int h, int w)
@@ -1584,35 +1593,39 @@ extern "C" int hrebsd_demons_register_batch(hrebsd_ctx *ctx, const float *ref, c
 }
 
 // ---------------------------------------------------------------------------
-// Allocation-free registration.  Some callers cannot call cudaMalloc: code
-// that runs inside a CUDA graph capture (allocation is not a capturable
-// operation and would break the capture), hosts that enforce a fixed
-// device-memory budget set up before launch, and plugins whose host
-// application owns the allocator.  For them the workspace of the registration
-// lives in one static device array of HREBSD_NOALLOC_SCRATCH_BYTES, which
-// every process that loads this library holds on each device it uses until
-// exit.  All calls share it and it keeps the previous call's contents: every
-// slot is written before it is read (the initial field is zeroed explicitly),
-// so nothing leaks from one call into the next, but calls that overlap on the
-// GPU (different streams, or different host threads) race on the array and
-// must be serialised by the caller.
+// Allocation-free registration.  Some callers cannot call cudaMalloc: hosts
+// that enforce a fixed device-memory budget set up before they start, plugins
+// whose host application owns the allocator, and latency-bound services where
+// an allocation (which may synchronise the device) in the middle of a request
+// is not allowed.  For them the workspace of the registration lives in one
+// static device array of HREBSD_NOALLOC_SCRATCH_BYTES, which every process that
+// loads this library holds on each device it uses until exit.  All calls share
+// it and it keeps the previous call's contents: every slot is written before it
+// is read (the initial field is zeroed or copied in explicitly), so nothing
+// leaks from one call into the next, but calls that overlap on the GPU
+// (different streams, or different host threads) race on the array and must be
+// serialised by the caller.
 namespace {
 
 __device__ __align__(256) unsigned char hr_noalloc_scratch[HREBSD_NOALLOC_SCRATCH_BYTES];
 
 // Device address of the array on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device address).
+// device (host code cannot use the symbol itself as a device address).  The
+// cache entries are atomics: two host threads making the first call on a
+// device at the same time both look the address up and store the same value.
 int noalloc_scratch_address(int device, unsigned char **out)
 {
-    static unsigned char *addr[256] = {};
+    static std::atomic<unsigned char *> addr[256];
     if (device < 0 || device >= 256) return HREBSD_EINVAL;
-    if (!addr[device]) {
+    unsigned char *a = addr[device].load(std::memory_order_acquire);
+    if (!a) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, hr_noalloc_scratch);
         if (e != cudaSuccess) return hr_cuda_error(e, "cudaGetSymbolAddress(hr_noalloc_scratch)", __FILE__, __LINE__);
-        addr[device] = static_cast<unsigned char *>(p);
+        a = static_cast<unsigned char *>(p);
+        addr[device].store(a, std::memory_order_release);
     }
-    *out = addr[device];
+    *out = a;
     return HREBSD_OK;
 }
 

@@ -336,19 +336,24 @@ extern "C" int hrebsd_fit_rotation(hrebsd_ctx *ctx, const float *field, int B, i
 }
 
 extern "C" int hrebsd_solve_F(hrebsd_ctx *ctx, const float *q, const int32_t *roi_xy, int N, int B, int H, int W,
-                              const hrebsd_geometry *g, const double *R_finite, double *F, int32_t *pair_status,
-                              void *stream)
+                              const hrebsd_geometry *g, const double *R_finite, int normalization,
+                              const hrebsd_elastic *elastic, double *F, int32_t *pair_status, void *stream)
 {
     if (!ctx || !g || B < 0 || H < 2 || W < 2 || N < 4 || N > kMaxRoi) return HREBSD_EINVAL;
+    if (normalization != HREBSD_NORM_DET1 && normalization != HREBSD_NORM_TRACTION_FREE) return HREBSD_EINVAL;
+    if (normalization == HREBSD_NORM_TRACTION_FREE && (!elastic || !elastic->g || elastic->R < 1))
+        return HREBSD_EINVAL;
     if (B == 0) return HREBSD_OK;
     if (!q || !roi_xy || !F) return HREBSD_EINVAL;
     int e = hr_set_device(ctx);
     if (e) return e;
-    hr_prof_begin(ctx, hr_stream(stream));
-    solve_F_kernel<<<(B + 63) / 64, 64, 0, hr_stream(stream)>>>(q, roi_xy, N, B, g->xstar * W, g->ystar * H,
-                                                                g->zstar * W, R_finite, F, pair_status);
-    hr_prof_end(ctx, PROF_SOLVE, hr_stream(stream));
+    cudaStream_t st = hr_stream(stream);
+    hr_prof_begin(ctx, st);
+    solve_F_kernel<<<(B + 63) / 64, 64, 0, st>>>(q, roi_xy, N, B, g->xstar * W, g->ystar * H, g->zstar * W, R_finite,
+                                                 F, pair_status);
+    hr_prof_end(ctx, PROF_SOLVE, st);
     HR_LAUNCHED(ctx);
+    if (normalization == HREBSD_NORM_TRACTION_FREE) return hr_launch_traction_scale(ctx, F, elastic, B, pair_status, st);
     return HREBSD_OK;
 }
 

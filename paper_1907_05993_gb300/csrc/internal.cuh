@@ -85,8 +85,12 @@ struct hrebsd_ctx {
 // Bracket a launch with events when tracing is on.
 void hr_prof_begin(hrebsd_ctx *ctx, cudaStream_t st);
 void hr_prof_end(hrebsd_ctx *ctx, int cls, cudaStream_t st);
-// Device counter of demons pixel-iterations (NULL when tracing is off).
-static inline unsigned long long *hr_prof_pixiters(hrebsd_ctx *ctx) { return ctx->prof_on ? ctx->d_pixiters : nullptr; }
+// Device counter of demons pixel-iterations (NULL when tracing is off, and
+// inside a call that is kept out of the trace).
+static inline unsigned long long *hr_prof_pixiters(hrebsd_ctx *ctx)
+{
+    return ctx->prof_on && !ctx->no_events ? ctx->d_pixiters : nullptr;
+}
 
 // Make sure workspace slot `slot` holds at least `bytes`; returns the pointer
 // through *out.  Allocation is synchronous (cudaMalloc) and happens only on
@@ -101,3 +105,8 @@ static inline cudaStream_t hr_stream(void *s) { return reinterpret_cast<cudaStre
 // zeros to radius `rad`.  Returns the natural radius, or -1 if > 6.
 int hr_gauss_taps(float sigma, int rad, float *taps);
 int hr_gauss_radius(float sigma);
+
+// Traction-free rescaling of second-pass deformation gradients in place
+// (strain.cu; used by hrebsd_solve_F with HREBSD_NORM_TRACTION_FREE).
+int hr_launch_traction_scale(hrebsd_ctx *ctx, double *F, const hrebsd_elastic *el, int B, int32_t *status,
+                             cudaStream_t st);

@@ -29,6 +29,72 @@ __device__ __forceinline__ void vpair(int k, int &i, int &j)
     j = J[k];
 }
 
+// C_S = M C M^T (Voigt, 6x6): the cubic stiffness rotated from crystal to
+// sample axes, M the Bond matrix of a = g^T (crystal -> sample), gr = g of the
+// pair's reference (sample -> crystal).
+__device__ void stiffness_sample(const double *gr, double c11, double c12, double c44, double *CS)
+{
+    double a[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) a[i * 3 + j] = gr[j * 3 + i];
+    double M[36], C[36], MC[36];
+    for (int I = 0; I < 6; ++I) {
+        int i, j;
+        vpair(I, i, j);
+        for (int P = 0; P < 6; ++P) {
+            int p, q;
+            vpair(P, p, q);
+            M[I * 6 + P] = p == q ? a[i * 3 + p] * a[j * 3 + p]
+                                  : a[i * 3 + p] * a[j * 3 + q] + a[i * 3 + q] * a[j * 3 + p];
+            C[I * 6 + P] = (I < 3 && P < 3) ? (I == P ? c11 : c12) : (I == P ? c44 : 0.0);
+        }
+    }
+    for (int I = 0; I < 6; ++I)
+        for (int P = 0; P < 6; ++P) {
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += M[I * 6 + k] * C[k * 6 + P];
+            MC[I * 6 + P] = s;
+        }
+    for (int I = 0; I < 6; ++I)
+        for (int P = 0; P < 6; ++P) {
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += MC[I * 6 + k] * M[P * 6 + k];
+            CS[I * 6 + P] = s;
+        }
+}
+
+// Eq. 13-14: F_S = T F T^T
+__device__ void tilt_to_sample(const double *F, double ct, double st, double *Fs)
+{
+    const double T[9] = {ct, st, 0.0, -st, ct, 0.0, 0.0, 0.0, 1.0};
+    const double Tt[9] = {ct, -st, 0.0, st, ct, 0.0, 0.0, 0.0, 1.0};
+    double tmp[9];
+    mat3_mul(T, F, tmp);
+    mat3_mul(tmp, Tt, Fs);
+}
+
+// A = 1/2 F_S F_S^T
+__device__ void half_ffT(const double *Fs, double *A)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            A[i * 3 + j] = 0.5 * (Fs[i * 3] * Fs[j * 3] + Fs[i * 3 + 1] * Fs[j * 3 + 1] + Fs[i * 3 + 2] * Fs[j * 3 + 2]);
+}
+
+// Traction-free scale (Eq. 16, sigma_33 = 0): lambda^2 with
+// sigma_33(lambda^2 A - I/2) = 0, A = 1/2 F_S F_S^T.
+__device__ double traction_lam2(const double *A, const double *CS)
+{
+    double sa = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        int i, j;
+        vpair(k, i, j);
+        sa += CS[2 * 6 + k] * (k < 3 ? A[i * 3 + j] : 2.0 * A[i * 3 + j]);
+    }
+    const double sb = 0.5 * (CS[12] + CS[13] + CS[14]);
+    return sb / sa;
+}
+
 __global__ void strain_stress_kernel(const double *__restrict__ F, const int32_t *__restrict__ ref_idx,
                                      const double *__restrict__ g, int R, int B, double ct, double st, double c11,
                                      double c12, double c44, int traction_free, double *F_S, double *eps,
@@ -41,56 +107,14 @@ __global__ void strain_stress_kernel(const double *__restrict__ F, const int32_t
     if (r < 0 || r >= R) {
         for (int k = 0; k < 9; ++k) Fs[k] = E[k] = S[k] = nan("");
     } else {
-        // Eq. 13-14
-        const double T[9] = {ct, st, 0.0, -st, ct, 0.0, 0.0, 0.0, 1.0};
-        const double Tt[9] = {ct, -st, 0.0, st, ct, 0.0, 0.0, 0.0, 1.0};
-        double tmp[9];
-        mat3_mul(T, F + (size_t)b * 9, tmp);
-        mat3_mul(tmp, Tt, Fs);
-        // C_S = M C M^T, M: Bond matrix of a = g^T (crystal -> sample)
-        const double *gr = g + (size_t)r * 9;
-        double a[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) a[i * 3 + j] = gr[j * 3 + i];
-        double M[36], C[36], MC[36], CS[36];
-        for (int I = 0; I < 6; ++I) {
-            int i, j;
-            vpair(I, i, j);
-            for (int P = 0; P < 6; ++P) {
-                int p, q;
-                vpair(P, p, q);
-                M[I * 6 + P] = p == q ? a[i * 3 + p] * a[j * 3 + p]
-                                      : a[i * 3 + p] * a[j * 3 + q] + a[i * 3 + q] * a[j * 3 + p];
-                C[I * 6 + P] = (I < 3 && P < 3) ? (I == P ? c11 : c12) : (I == P ? c44 : 0.0);
-            }
-        }
-        for (int I = 0; I < 6; ++I)
-            for (int P = 0; P < 6; ++P) {
-                double s = 0.0;
-                for (int k = 0; k < 6; ++k) s += M[I * 6 + k] * C[k * 6 + P];
-                MC[I * 6 + P] = s;
-            }
-        for (int I = 0; I < 6; ++I)
-            for (int P = 0; P < 6; ++P) {
-                double s = 0.0;
-                for (int k = 0; k < 6; ++k) s += MC[I * 6 + k] * M[P * 6 + k];
-                CS[I * 6 + P] = s;
-            }
+        tilt_to_sample(F + (size_t)b * 9, ct, st, Fs);
+        double CS[36];
+        stiffness_sample(g + (size_t)r * 9, c11, c12, c44, CS);
         // engineering Voigt strain of 1/2 F_S F_S^T
         double A[9];
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                A[i * 3 + j] = 0.5 * (Fs[i * 3] * Fs[j * 3] + Fs[i * 3 + 1] * Fs[j * 3 + 1] + Fs[i * 3 + 2] * Fs[j * 3 + 2]);
+        half_ffT(Fs, A);
         if (traction_free) {
-            // sigma_33(lambda^2 A - I/2) = 0
-            double sa = 0.0;
-            for (int k = 0; k < 6; ++k) {
-                int i, j;
-                vpair(k, i, j);
-                sa += CS[2 * 6 + k] * (k < 3 ? A[i * 3 + j] : 2.0 * A[i * 3 + j]);
-            }
-            const double sb = 0.5 * (CS[12] + CS[13] + CS[14]);
-            const double lam2 = sb / sa;
+            const double lam2 = traction_lam2(A, CS);
             const double lam = sqrt(lam2);
             for (int k = 0; k < 9; ++k) {
                 Fs[k] *= lam;
@@ -122,6 +146,33 @@ __global__ void strain_stress_kernel(const double *__restrict__ F, const int32_t
     }
 }
 
+// Traction-free scale of the second-pass F (hrebsd_solve_F): F <- lambda F in
+// place (the scale commutes with the tilt, so lambda of F_S scales F itself).
+__global__ void traction_scale_kernel(double *__restrict__ F, const int32_t *__restrict__ ref_idx,
+                                      const double *__restrict__ g, int R, int B, double ct, double st, double c11,
+                                      double c12, double c44, int32_t *status)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double *Fb = F + (size_t)b * 9;
+    const int r = ref_idx ? ref_idx[b] : 0;
+    double lam = nan("");
+    if (r >= 0 && r < R) {
+        double Fs[9], A[9], CS[36];
+        tilt_to_sample(Fb, ct, st, Fs);
+        stiffness_sample(g + (size_t)r * 9, c11, c12, c44, CS);
+        half_ffT(Fs, A);
+        const double lam2 = traction_lam2(A, CS);
+        if (lam2 > 0.0 && isfinite(lam2)) lam = sqrt(lam2);
+    }
+    if (!(lam > 0.0)) {
+        if (status) status[b] |= HREBSD_PAIR_FIT_FAILED;
+        for (int k = 0; k < 9; ++k) Fb[k] = nan("");
+        return;
+    }
+    for (int k = 0; k < 9; ++k) Fb[k] *= lam;
+}
+
 }  // namespace
 
 extern "C" int hrebsd_strain_stress(hrebsd_ctx *ctx, const double *F, const int32_t *ref_idx, const double *g, int R,
@@ -138,6 +189,17 @@ extern "C" int hrebsd_strain_stress(hrebsd_ctx *ctx, const double *F, const int3
                                                                         sin(tilt_rad), c11, c12, c44, traction_free,
                                                                         F_S, eps, sigma);
     hr_prof_end(ctx, PROF_SOLVE, hr_stream(stream));
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+int hr_launch_traction_scale(hrebsd_ctx *ctx, double *F, const hrebsd_elastic *el, int B, int32_t *status,
+                             cudaStream_t st)
+{
+    hr_prof_begin(ctx, st);
+    traction_scale_kernel<<<(B + 127) / 128, 128, 0, st>>>(F, el->ref_idx, el->g, el->R, B, cos(el->tilt_rad),
+                                                           sin(el->tilt_rad), el->c11, el->c12, el->c44, status);
+    hr_prof_end(ctx, PROF_SOLVE, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
 }

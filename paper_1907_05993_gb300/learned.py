@@ -13,8 +13,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (cnn_params, demons_params, hrebsd_cnn_get_params, hrebsd_cnn_get_state, hrebsd_cnn_init,
-               hrebsd_cnn_set_state, hrebsd_cnn_train_step,
+from . import (cnn_params, demons_params, hrebsd_cnn_get_params, hrebsd_cnn_init, hrebsd_cnn_load,
+               hrebsd_cnn_save, hrebsd_cnn_train_step,
                hrebsd_demons_register_batch, hrebsd_downsample_batch, hrebsd_field_resample, hrebsd_preprocess_batch)
 
 TARGET_CAP = 100                  # iteration cap of every level of the target registration
@@ -109,31 +109,35 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def save(ctx, path: str):
-    w, _ = hrebsd_cnn_get_params(ctx)
-    np.save(path, w)
+    """The model file of the library (weights, Adam moments, step): hrebsd_cnn_save."""
+    hrebsd_cnn_save(ctx, path)
 
 
 def load_model(ctx, path: str):
-    hrebsd_cnn_init(ctx, np.load(path))
+    """Load a model file written by ``save`` or ``save_checkpoint`` (hrebsd_cnn_load)."""
+    hrebsd_cnn_load(ctx, path)
 
 
 def save_checkpoint(ctx, path: str, **extra):
-    """Weights, Adam moments and step (plus any small arrays in ``extra``, e.g. the epoch) to one
-    .npz, written to a temporary name and renamed, so that an interrupted write leaves the previous
-    checkpoint intact."""
+    """Training checkpoint: the network state in the library's model file at ``path``
+    (hrebsd_cnn_save, written under a temporary name and renamed), plus any small arrays in
+    ``extra`` (e.g. the epoch) in ``path + ".extra.npz"``, written the same way and first, so that a
+    model file never pairs with the extras of a later save."""
     import os
-    w, _ = hrebsd_cnn_get_params(ctx)
-    m, v, step = hrebsd_cnn_get_state(ctx)
-    tmp = path + ".tmp.npz"
-    np.savez(tmp, params=w, adam_m=m, adam_v=v, step=np.int64(step), **extra)
-    os.replace(tmp, path)
+    tmp = path + ".extra.tmp.npz"
+    np.savez(tmp, **extra)
+    os.replace(tmp, path + ".extra.npz")
+    hrebsd_cnn_save(ctx, path)
 
 
 def load_checkpoint(ctx, path: str) -> dict:
     """Restore what save_checkpoint wrote; training continues as if it had not stopped.  Returns the
-    file's arrays (including ``extra``)."""
-    with np.load(path) as z:
-        d = {k: z[k] for k in z.files}
-    hrebsd_cnn_init(ctx, d["params"])
-    hrebsd_cnn_set_state(ctx, d["adam_m"], d["adam_v"], int(d["step"]))
+    extras and the restored parameter vector (key "params")."""
+    import os
+    hrebsd_cnn_load(ctx, path)
+    d = {}
+    if os.path.exists(path + ".extra.npz"):
+        with np.load(path + ".extra.npz") as z:
+            d = {k: z[k] for k in z.files}
+    d["params"] = hrebsd_cnn_get_params(ctx)[0]
     return d

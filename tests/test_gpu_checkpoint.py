@@ -1,5 +1,6 @@
 """Checkpoint/resume on the GPU: the learned initialiser's training state (weights, Adam moments,
-step) restored into a new context continues training as the uninterrupted run does; a scan
+step), written by hrebsd_cnn_save and restored by hrebsd_cnn_load into a new context, continues
+training as the uninterrupted run does, and damaged model files are refused; a scan
 resumed after losing a chunk recomputes only that chunk and gives the same results."""
 import os
 
@@ -19,7 +20,7 @@ def test_training_checkpoint_resumes(tmp_path):
     x = torch.from_numpy(rng.normal(size=(16, 2, 64, 64)).astype(np.float32)).cuda().to(torch.bfloat16)
     tgt = torch.from_numpy(rng.normal(0, 0.5, (16, 2, 64, 64)).astype(np.float32)).cuda()
     loss = torch.zeros(1, device="cuda")
-    path = str(tmp_path / "ckpt.npz")
+    path = str(tmp_path / "ckpt.hrcnn")
     ctxs = [P.hrebsd_create(0) for _ in range(3)]
     try:
         a = ctxs[0]
@@ -47,6 +48,19 @@ def test_training_checkpoint_resumes(tmp_path):
         # gradients are summed with float atomics, so the runs agree to rounding, not bit for bit
         assert np.abs(wa - wb).max() <= 0.02 * np.abs(wa - wc).max()
         assert np.abs(wa - wc).max() > 1e-4
+        # the model file is checked before anything is loaded
+        raw = open(path, "rb").read()
+        for bad in (raw[:-9], raw[:100] + bytes([raw[100] ^ 1]) + raw[101:], b"HRCNN002" + raw[8:]):
+            with open(path + ".bad", "wb") as fh:
+                fh.write(bad)
+            before = P.hrebsd_cnn_get_params(c)[0]
+            with pytest.raises(P.HrebsdError) as err:
+                P.hrebsd_cnn_load(c, path + ".bad")
+            assert err.value.status == P.EFORMAT
+            assert np.array_equal(P.hrebsd_cnn_get_params(c)[0], before)
+        with pytest.raises(P.HrebsdError) as err:
+            P.hrebsd_cnn_load(c, str(tmp_path / "missing.hrcnn"))
+        assert err.value.status == P.EIO
     finally:
         for ctx in ctxs:
             P.hrebsd_destroy(ctx)

@@ -312,6 +312,46 @@ def test_solve_F_parity(torch, lib, ctx, oracle):
         assert np.abs(F[b] - oracle.solve_F(q[b], roi, H, W, geom, Rs[b])).max() < 1e-10
 
 
+def test_solve_F_traction_free_parity(torch, lib, ctx, oracle):
+    """hrebsd_solve_F with the traction-free normalisation (Section 2, Eq. 16, sigma_33 = 0) against the
+    oracle's det-1 solve rescaled by oracle/strain.py's traction-free lambda, for several references,
+    tilts and an out-of-range reference index (NaN + FIT_FAILED)."""
+    from oracle import strain as S
+    H = W = 256
+    geom = K.Geometry()
+    roi = K.roi_grid(H, W, 64, False)
+    rng = np.random.default_rng(15)
+    B, R = 6, 3
+    q = f32(rng.normal(0, 0.4, (B, len(roi), 2)))
+    Rs = np.stack([K.axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, 12))) for _ in range(B)])
+    gs = np.stack([K.random_rotation(99, r) for r in range(R)])
+    ridx = np.array([0, 1, 2, 1, 0, 7], np.int32)   # the last index is outside [0, R)
+    g = lib.hrebsd_geometry(geom.xstar, geom.ystar, geom.zstar)
+    for tilt in (0.0, np.radians(70.0)):
+        F = torch.empty((B, 9), dtype=torch.float64, device="cuda")
+        st = torch.zeros((B,), dtype=torch.int32, device="cuda")
+        d_g, d_idx = cuda(torch, gs.reshape(R, 9)), cuda(torch, ridx)
+        el = lib.elastic_params(d_g, R, tilt, None, d_idx)
+        lib.hrebsd_solve_F(ctx, cuda(torch, q, torch.float32), cuda(torch, roi), len(roi), B, H, W, g,
+                           cuda(torch, Rs.reshape(B, 9)), F, st, normalization=lib.NORM_TRACTION_FREE, elastic=el)
+        F, st = F.cpu().numpy().reshape(B, 3, 3), st.cpu().numpy()
+        for b in range(B - 1):
+            F1 = oracle.solve_F(q[b], roi, H, W, geom, Rs[b])
+            C_S = S.rotate_stiffness(S.cubic_stiffness(*S.NI_C), gs[ridx[b]])
+            lam = S.traction_free_scale(S.to_sample(F1, tilt), C_S)
+            assert abs(lam - 1.0) > 1e-9   # the normalisation does something
+            assert np.abs(F[b] - lam * F1).max() < 1e-10
+            # the result is traction free: sigma_33 of the sample-frame strain vanishes
+            sig = S.stress(C_S, S.strain(S.to_sample(F[b], tilt)))
+            assert abs(sig[2, 2]) < 1e-6 * np.abs(sig).max() + 1.0
+            assert st[b] == 0
+        assert np.isnan(F[B - 1]).all() and (st[B - 1] & lib.PAIR_FIT_FAILED)
+    with pytest.raises(lib.HrebsdError):   # traction free without elastic data
+        lib.hrebsd_solve_F(ctx, cuda(torch, q, torch.float32), cuda(torch, roi), len(roi), B, H, W, g, None,
+                           torch.empty((B, 9), dtype=torch.float64, device="cuda"), None,
+                           normalization=lib.NORM_TRACTION_FREE)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_batch_and_bad_args(torch, lib, ctx):
     p = lib.demons_params(2, [5, 5])

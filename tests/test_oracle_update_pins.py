@@ -1,0 +1,119 @@
+"""Pins of the oracle's demons update, XCF tie flag and sub-pixel bias against independent library
+restatements (scipy / numpy), covering the configurations the other pins leave at their defaults.
+
+- One demons iteration (Eq. 1 with the workloads' regularisation) is, step by step:
+  d = M(x - u) - F, du = d grad F / (|grad F|^2 + alpha^2 d^2), u <- G_f * (u + G_u * du).  Here the
+  warp is scipy's linear map_coordinates (edge mode: the clamped bilinear sample), the gradient
+  numpy's (central inside, one-sided at the borders), and the Gaussians scipy's correlate1d with
+  replicated edges.  Distinct sigma_update and sigma_field and alpha != 1 make a swapped role, a
+  wrong smoothing order or alpha instead of alpha^2 fail.
+- The XCF near-tie flag: a surface with two equal maxima is flagged, one with a clear maximum is not.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from synth import kikuchi as K
+
+
+def gauss(sigma):
+    r = math.ceil(3 * sigma)
+    k = np.arange(-r, r + 1)
+    w = np.exp(-k * k / (2 * sigma * sigma))
+    return w / w.sum()
+
+
+def smooth(img, sigma):
+    if sigma <= 0:
+        return img.copy()
+    w = gauss(sigma)
+    return ndimage.correlate1d(ndimage.correlate1d(img, w, axis=1, mode="nearest"), w, axis=0, mode="nearest")
+
+
+def force(F, M, u, alpha):
+    H, W = F.shape
+    Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+    mw = ndimage.map_coordinates(M, [Y - u[1], X - u[0]], order=1, mode="nearest")
+    gy, gx = np.gradient(F)
+    d = mw - F
+    den = gx * gx + gy * gy + alpha * alpha * d * d
+    t = np.where(den > 1e-9, d / np.where(den > 1e-9, den, 1.0), 0.0)
+    return np.stack([t * gx, t * gy]), float(np.sum(d * d))
+
+
+def pair(H=40, W=48, seed=3):
+    spec = K.ScanSpec(n_pairs=1, H=H, W=W, n_refs=1, mis_lo_deg=1.0, mis_hi_deg=3.0, seed=seed)
+    import oracle
+    M = oracle.preprocess(K.render_ref(spec, 0).astype(np.float64))
+    F = oracle.preprocess(K.render_test(spec, 0).astype(np.float64))
+    rng = np.random.default_rng(seed)
+    u = np.stack([smooth(rng.normal(0, 1.5, (H, W)), 2.0) for _ in range(2)])
+    return F, M, u
+
+
+@pytest.mark.parametrize("alpha", [0.5, 2.0])
+def test_force_matches_library_composition(oracle, alpha):
+    F, M, u = pair()
+    du, ssd = oracle.demons_force(F, M, u, alpha)
+    e_du, e_ssd = force(F, M, u, alpha)
+    assert np.abs(du - e_du).max() < 1e-12 and abs(ssd - e_ssd) < 1e-9 * e_ssd
+    # alpha (not alpha^2) in the denominator would differ
+    wrong, _ = force(F, M, u, math.sqrt(alpha))
+    assert np.abs(du - wrong).max() > 1e-3
+
+
+@pytest.mark.parametrize("sigma_up,sigma_f,alpha", [(0.0, 1.0, 1.0), (1.6, 1.0, 0.5), (0.7, 2.0, 2.0)])
+def test_one_update_is_smoothed_sum(oracle, sigma_up, sigma_f, alpha):
+    F, M, u = pair()
+    got, k, trace = oracle.demons_level(F, M, u, alpha, sigma_up, sigma_f, 1, 0, 0.0, 1)
+    assert k == 1
+    du, ssd = force(F, M, u, alpha)
+    exp = np.stack([smooth(u[c] + smooth(du[c], sigma_up), sigma_f) for c in range(2)])
+    assert np.abs(got - exp).max() < 1e-12
+    assert abs(trace[0] - ssd) < 1e-9 * ssd
+    # the other readings are measurably different: swapped roles, smoothing before the sum
+    swapped = np.stack([smooth(u[c] + smooth(du[c], sigma_f), sigma_up) for c in range(2)])
+    other_order = np.stack([smooth(u[c], sigma_f) + smooth(du[c], sigma_up) for c in range(2)])
+    assert np.abs(got - swapped).max() > 1e-4
+    assert np.abs(got - other_order).max() > 1e-4
+
+
+def test_two_updates_chain(oracle):
+    F, M, u = pair(seed=8)
+    got, k, _ = oracle.demons_level(F, M, u, 2.0, 1.6, 1.0, 2, 0, 0.0, 2)
+    exp = u
+    for _ in range(2):
+        du, _ = force(F, M, exp, 2.0)
+        exp = np.stack([smooth(exp[c] + smooth(du[c], 1.6), 1.0) for c in range(2)])
+    assert k == 2 and np.abs(got - exp).max() < 1e-12
+
+
+def periodic_pair(S, a, b, wb, seed=0):
+    """ref = one period R0 of size S tiled over 2S x 2S; test = R0 shifted by a plus wb x R0 shifted by b
+    (circular, the same tiling), so that inside an S x S ROI aligned with the period the circular
+    cross-correlation (window off) has the values c(a) and c(b) of a two-peak surface."""
+    rng = np.random.default_rng(seed)
+    R0 = ndimage.gaussian_filter(rng.normal(size=(S, S)), 1.0, mode="wrap")
+    T0 = np.roll(R0, a, axis=(0, 1)) + wb * np.roll(R0, b, axis=(0, 1))
+    return np.tile(R0, (2, 2)), np.tile(T0, (2, 2))
+
+
+def test_near_tie_flag(oracle):
+    S = 32
+    roi = np.array([[S // 2 + S // 2, S // 2 + S // 2]], np.int32)   # ROI = rows/cols [S/2, 3S/2): one period
+    # equal weights: c(a) = c(b) up to rounding (the autocorrelation is symmetric) -> near tie
+    ref, test = periodic_pair(S, (3, -5), (-6, 4), 1.0)
+    q, peak, ph, tie = oracle.xcf_roi(ref, test, roi, S, window=False)
+    assert tie[0]
+    # the peak is one of the two maxima
+    assert tuple(peak[0]) in {(-5, 3), (4, -6)}
+    # a clearly weaker second copy: a unique maximum at shift a, no tie
+    ref, test = periodic_pair(S, (3, -5), (-6, 4), 0.8)
+    q, peak, ph, tie = oracle.xcf_roi(ref, test, roi, S, window=False)
+    assert not tie[0] and tuple(peak[0]) == (-5, 3)
+    # brute-force surface: the two equal-weight maxima are equal to 1e-12 relative
+    ref, test = periodic_pair(S, (3, -5), (-6, 4), 1.0)
+    c, _, _ = oracle.xcf_surface(ref, test, S // 2, S // 2, S, window=False)
+    assert abs(c[3 % S, -5 % S] - c[-6 % S, 4 % S]) < 1e-12 * abs(c).max()
