@@ -237,11 +237,16 @@ E2E_CHUNKS = 4   # slices of the end-to-end (host-buffer) path
 
 def run_ours(args, rank, world, local_rank):
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline and args.no_learned):
         # before any CUDA call: the oracle pool is spawned, never forked from a CUDA process
-        cores = os.cpu_count() or 1
+        import oracle
+        oracle.build()
+        pool = mp.get_context("spawn").Pool(cores)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n = max(cores, args.cpu_sample)
-        v, cpu_s, wall = oracle_throughput(n, args.pairs, cores)
+        v, cpu_s, wall = oracle_throughput(n, args.pairs, cores, pool)
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} pairs of the workload (pairs 0..{n - 1}), one pair per process over {cores} host "
                          f"cores, {cpu_s:.1f} s of CPU work"}
@@ -278,8 +283,7 @@ def run_ours(args, rank, world, local_rank):
         pipe.run(refs, tests, ridx, out=out)
     torch.cuda.synchronize()
 
-    # ---- device-resident timing
-    P.hrebsd_profile_enable(pipe.ctx, True)
+    # ---- device-resident timing (tracing off: every pyramid level replays its cached CUDA graph)
     l0 = P.hrebsd_launch_count(pipe.ctx)
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -296,8 +300,19 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     launches = P.hrebsd_launch_count(pipe.ctx) - l0
+    # ---- traced pass of the same steps: per-kernel CUDA events on the launch stream (the graphs carry
+    # no per-kernel events, so the breakdown and the roofline of the demons iteration come from here)
+    trace_steps = max(1, min(args.steps, 3))
+    P.hrebsd_profile_enable(pipe.ctx, True)
+    tr0, tr1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tr0.record(stream)
+    for _ in range(trace_steps):
+        pipe.run(refs, tests, ridx, out=out)
+    tr1.record(stream)
+    torch.cuda.synchronize()
     prof = P.hrebsd_profile_read(pipe.ctx)
     P.hrebsd_profile_enable(pipe.ctx, False)
+    traced_ms_per_step = tr0.elapsed_time(tr1) / trace_steps
     t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, device="cuda")
     value = world * B * args.steps / t
     tune_ms = pipe._tuned.get((B, wl["H"], wl["W"]))
@@ -350,6 +365,21 @@ def run_ours(args, rank, world, local_rank):
     p1.record(stream)
     torch.cuda.synchronize()
     fp32_peak = probe_flops / (p0.elapsed_time(p1) / 1e3) / 1e12
+    pipe.close()
+
+    # learned initialiser vs plain on the learned-vs-plain scan (rank 0 of a 1-GPU run; network trained here
+    # on a reduced set so that the run stays within minutes; --workload learned uses the full recipe)
+    lvp = None
+    if pool is not None and not args.no_learned:
+        del refs, tests, out
+        torch.cuda.empty_cache()
+        lvp = learned_comparison(args, local_rank, pool, args.lvp_train_pairs, args.lvp_epochs, args.pairs,
+                                 args.oracle_pairs, max(3, args.warmup), max(1, min(args.steps, 3)))
+        lvp["training"]["note"] += (f"; reduced set for the default benchmark ({args.lvp_train_pairs} pairs, "
+                                    f"{args.lvp_epochs} epochs; the full recipe is --workload learned)")
+    if pool is not None:
+        pool.close()
+        pool.join()
 
     if rank == 0:
         it = prof["demons_iter"]
@@ -377,73 +407,91 @@ def run_ours(args, rank, world, local_rank):
                                               f"{px_per_launch:.0f} pixel-iterations per launch (average)",
                          "avg_launch_ms": it["ms"] / max(1, it["launches"]),
                          "share_of_step": it["ms"] / total_ms if total_ms else None},
-            "xcf_roofline": xcf_roofline(prof["xcf"]["ms"] / args.steps, B, wl, fp32_peak, peak),
-            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items() if k != "pixel_iters"},
+            "xcf_roofline": xcf_roofline(prof["xcf"]["ms"] / trace_steps, B, wl, fp32_peak, peak),
+            "kernel_ms_per_step": {k: v["ms"] / trace_steps for k, v in prof.items() if k != "pixel_iters"},
+            "traced_pass": {"steps": trace_steps, "ms_per_step": traced_ms_per_step,
+                            "note": "per-kernel CUDA events around every launch (direct launches, no graphs); "
+                                    "the roofline and kernel_ms_per_step come from it"},
             "demons_tile_shape_per_level": tile_choice,
             "demons_iters_mean_per_level": [float(x) for x in iters.mean(axis=0)],
             "pairs_capped": int(np.sum(status & 1)),
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if lvp is not None:
+            line["learned_vs_plain"] = lvp
         print(json.dumps(line), flush=True)
-    pipe.close()
     if dist:
         dist.destroy_process_group()
     return 0
 
 
 # ------------------------------------------------------------------ learned initialiser vs plain
-def _oracle_pair5(args):
-    p, n_pairs = args
+LEARNED_SCAN_PAIRS = 160_000   # the learned-init vs plain scan: 400 x 400 points, 8 grains, mis U(0, 12) deg
+
+
+def _render5(p):
+    from synth import kikuchi as K
+    spec = K.config5(LEARNED_SCAN_PAIRS)
+    return K.render_test(spec, p)
+
+
+def _oracle5(args):
+    """The oracle's chain on one config-5 pair: its own stop rule (replay None) or replaying the given
+    per-level counts.  Returns (R_finite, F, iters)."""
+    p, replay = args
     import numpy as np
     import oracle
     from synth import kikuchi as K
-    spec = K.config5(n_pairs)
+    spec = K.config5(LEARNED_SCAN_PAIRS)
     ref = K.render_ref(spec, K.ref_index(spec, p)).astype(np.float64)
     test = K.render_test(spec, p).astype(np.float64)
-    res = oracle.pipeline(ref, test, K.roi_grid(256, 256, 64, False), 64, spec.geom, 4, [100] * 4, 1.0, 1.0, 5, 1e-4)
-    return oracle.polar(res["F"])
+    res = oracle.pipeline(ref, test, K.roi_grid(256, 256, 64, False), 64, spec.geom, 4, [100] * 4, 1.0, 1.0, 5, 1e-4,
+                          replay=replay)
+    return res["R_finite"], res["F"], np.asarray(res["iters"])
 
 
-def run_learned(args, rank, world, local_rank):
-    """Config-5 scan: plain registration vs registration started from the learned field."""
+def learned_comparison(args, local_rank, pool, train_pairs, epochs, n_points, oracle_pairs, warmup, steps):
+    """Config-5 scan, first n_points points: plain registration (caps 100 x 4) vs registration started
+    from the learned initialiser's field (args.learned_caps) vs a plain control with the learned run's
+    fine-level caps; the network is trained first on train_pairs config-4 pairs for `epochs` epochs.
+    A seeded subset of oracle_pairs points is rendered by the numpy generator on both sides and run by
+    the oracle twice: with its own stop rule (the method's answer) and replaying the plain run's
+    per-level counts (parity of the plain arm)."""
     import numpy as np
-    cores = os.cpu_count() or 1
-    n_pairs = 160_000
-    # seeded subset of the timed points for the oracle comparison
-    sub = list(range(0, args.pairs, max(1, args.pairs // args.oracle_pairs)))[:args.oracle_pairs]
-    import oracle
-    oracle.build()
-    t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        R_oracle = pool.map(_oracle_pair5, [(p, n_pairs) for p in sub], chunksize=1)
-    t_oracle = time.perf_counter() - t0
+    import oracle as O
     import torch
     import paper_1907_05993_gb300 as P
     from paper_1907_05993_gb300 import learned as LN
     from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
     from synth import gpu as SG
     from synth import kikuchi as K
-    torch.cuda.set_device(local_rank)
-    spec5 = K.config5(n_pairs)
-    pairs = sorted(set(range(args.pairs)) | set(sub))
-    refs, tests, ridx, F_true = SG.make_scan_gpu(spec5, pairs)
-    pos = {p: i for i, p in enumerate(pairs)}
-    roi = K.roi_grid(256, 256, 64, False)
-    cfg = PipelineConfig(256, 256, roi, 64, 4, (100, 100, 100, 100), 1.0, 1.0, 1e-4, 5)
-    pipe = Pipeline(cfg, device=local_rank)
-    # train the initialiser (config-4 recipe) in the pipeline's context
+    rng = np.random.default_rng(505)
+    sub = sorted(rng.choice(n_points, oracle_pairs, replace=False).tolist())
     t0 = time.perf_counter()
-    x, y = LN.build_training_set(pipe.ctx, K.config4(args.train_pairs))
+    own = pool.map(_oracle5, [(p, None) for p in sub], chunksize=2)
+    renders = pool.map(_render5, sub, chunksize=8)
+    t_oracle = time.perf_counter() - t0
+    torch.cuda.set_device(local_rank)
+    spec5 = K.config5(LEARNED_SCAN_PAIRS)
+    refs, tests, ridx, F_true = SG.make_scan_gpu(spec5, range(n_points))
+    refs = torch.from_numpy(np.stack([K.render_ref(spec5, r) for r in range(spec5.n_refs)])).cuda()
+    for p, img in zip(sub, renders):
+        tests[p] = torch.from_numpy(img).cuda()
+    roi = K.roi_grid(256, 256, 64, False)
+    pipe = Pipeline(PipelineConfig(256, 256, roi, 64, 4, (100, 100, 100, 100), 1.0, 1.0, 1e-4, 5),
+                    device=local_rank)
+    t0 = time.perf_counter()
+    x, y = LN.build_training_set(pipe.ctx, K.config4(train_pairs))
     torch.cuda.synchronize()
     t_set = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = LN.train(pipe.ctx, x, y, epochs=args.epochs, batch=256, lr=args.lr, seed=0, lr_final=args.lr_final)
+    hist = LN.train(pipe.ctx, x, y, epochs=epochs, batch=256, lr=args.lr, seed=0, lr_final=args.lr_final)
     del x, y
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     caps_l = tuple(args.learned_caps)
-    B = len(pairs)
+    ctrl_caps = (caps_l[0], caps_l[1], 100, 100)
     stream = torch.cuda.current_stream()
 
     def timed(learned, plain_caps=None):
@@ -452,76 +500,90 @@ def run_learned(args, rank, world, local_rank):
         saved = pipe.params
         if plain_caps is not None:
             pipe.params = P.demons_params(4, plain_caps, 1.0, 1.0, 1.0, 1e-4, 5)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             pipe.run(refs, tests, ridx, out=out, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             pipe.run(refs, tests, ridx, out=out, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         pipe.params = saved
-        F = out["F"].cpu().numpy().reshape(-1, 3, 3)
-        its = out["iters"].cpu().numpy()
-        return B * args.steps / t, F, its
+        return (n_points * steps / t, out["R_finite"].cpu().numpy().reshape(-1, 3, 3),
+                out["iters"].cpu().numpy())
 
-    v_plain, F_plain, it_plain = timed(False)
-    v_learn, F_learn, it_learn = timed(True)
-    # control: plain registration with the same fine-level caps as the learned run (isolates the
-    # initialiser from the cap reduction)
-    ctrl_caps = (caps_l[0], caps_l[1], 100, 100)
-    v_ctrl, F_ctrl, it_ctrl = timed(False, ctrl_caps)
-    import oracle as O
+    v_plain, R_plain, it_plain = timed(False)
+    v_learn, R_learn, it_learn = timed(True)
+    v_ctrl, R_ctrl, it_ctrl = timed(False, ctrl_caps)
+    pipe.close()
+    t0 = time.perf_counter()
+    rep = pool.map(_oracle5, [(p, it_plain[p].astype(np.int32)) for p in sub], chunksize=2)
+    t_oracle += time.perf_counter() - t0
 
     def rot_deg(Ra, Rb):
-        c = np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1)
-        return float(np.degrees(np.arccos(c)))
+        M = np.asarray(Ra).T @ np.asarray(Rb)
+        v = np.array([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]]) / 2
+        return float(np.degrees(np.arcsin(min(1.0, float(np.linalg.norm(v))))))
 
     def stats(e):
         e = np.asarray(e)
-        return {"median": float(np.median(e)), "p95": float(np.percentile(e, 95)),
-                "frac_le_1e-4": float(np.mean(e <= 1e-4))}
-    R_plain = [O.polar(f) for f in F_plain]
-    R_learn = [O.polar(f) for f in F_learn]
+        return {"median": float(np.median(e)), "p95": float(np.percentile(e, 95)), "max": float(e.max()),
+                "frac_le_1e-4_deg": float(np.mean(e <= 1e-4))}
+    R_own = [o[0] for o in own]
+    R_rep = [r[0] for r in rep]
     R_true = [O.polar(f) for f in F_true]
-    e_plain = [rot_deg(R_plain[pos[p]], R) for p, R in zip(sub, R_oracle)]
-    e_learn = [rot_deg(R_learn[pos[p]], R) for p, R in zip(sub, R_oracle)]
-    t_plain = [rot_deg(a, b) for a, b in zip(R_plain, R_true)]
-    t_learn = [rot_deg(a, b) for a, b in zip(R_learn, R_true)]
-    t_ctrl = [rot_deg(O.polar(a), b) for a, b in zip(F_ctrl, R_true)]
-    d_pl = [rot_deg(a, b) for a, b in zip(R_plain, R_learn)]
-    line = {
-        "metric": METRIC + "; learned-init vs plain", "workload": "learned-init vs plain",
-        "value": v_learn, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
-        "data": "synthetic (seeded kinematic Kikuchi generator)",
-        "config": {"workload": f"config-5 scan 400x400 (first {args.pairs} points), 256x256, 8 grains, "
-                               f"mis U(0,12) deg; plain: 4 levels <=100 it; learned: network field resampled "
-                               f"to {args.learned_start}x{args.learned_start}, registration from that level, "
-                               f"caps {list(caps_l)}", "pairs": B,
-                   "training": f"{args.train_pairs} config-4 pairs (128x128, mis U(0,12) deg), target = final "
-                               f"field of the full registration at 64x64; {args.epochs} epochs, batch 256, "
-                               f"Adam {args.lr} -> {args.lr_final} (cosine)"},
-        "plain_pairs_per_s": v_plain, "learned_pairs_per_s": v_learn, "speedup": v_learn / v_plain,
+    dev = {name: [rot_deg(R[p], Ro) for p, Ro in zip(sub, R_own)]
+           for name, R in (("plain", R_plain), ("learned", R_learn), ("control", R_ctrl))}
+    dev_rep_plain = [rot_deg(R_plain[p], Ro) for p, Ro in zip(sub, R_rep)]
+    truth = {name: [rot_deg(R[p], R_true[p]) for p in range(n_points)]
+             for name, R in (("plain", R_plain), ("learned", R_learn), ("control", R_ctrl))}
+    stop_d = np.abs(np.stack([it_plain[p] for p in sub]) - np.stack([o[2] for o in own]))
+    f_plain = stats(dev["plain"])["frac_le_1e-4_deg"]
+    f_learn = stats(dev["learned"])["frac_le_1e-4_deg"]
+    holds = bool(v_learn > v_plain and f_learn >= f_plain)
+    return {
+        "workload": f"config-5 scan (400x400 points, 256x256, 8 grains, mis U(0,12) deg), first {n_points} points",
+        "plain": {"caps": [100] * 4, "pairs_per_s": v_plain,
+                  "iters_mean_per_level": [float(a) for a in it_plain.mean(axis=0)]},
+        "learned": {"caps": list(caps_l), "start": f"{args.learned_start}x{args.learned_start} from the network's "
+                                                 f"64x64 field", "pairs_per_s": v_learn,
+                    "iters_mean_per_level": [float(a) for a in it_learn.mean(axis=0)]},
         "control_plain_same_fine_caps": {"caps": list(ctrl_caps), "pairs_per_s": v_ctrl,
-                                         "speedup_of_learned": v_learn / v_ctrl,
-                                         "iters_mean_per_level": [float(a) for a in it_ctrl.mean(axis=0)],
-                                         "rot_err_vs_ground_truth_deg": stats(t_ctrl)},
-        "iters_mean_per_level_plain": [float(a) for a in it_plain.mean(axis=0)],
-        "iters_mean_per_level_learned": [float(a) for a in it_learn.mean(axis=0)],
-        "oracle_subset": len(sub), "oracle_seconds": t_oracle, "oracle_cores": cores,
-        "rot_err_vs_oracle_deg": {"plain": stats(e_plain), "learned": stats(e_learn)},
-        "rot_err_vs_ground_truth_deg": {"plain": stats(t_plain), "learned": stats(t_learn)},
-        "rot_err_vs_ground_truth_deg_mean": {"plain": float(np.mean(t_plain)), "learned": float(np.mean(t_learn)),
-                                             "control": float(np.mean(t_ctrl))},
-        "rot_dev_learned_vs_plain_deg": stats(d_pl),
-        "training_loss_per_epoch": hist, "training_seconds": t_train, "training_set_seconds": t_set,
+                                         "iters_mean_per_level": [float(a) for a in it_ctrl.mean(axis=0)]},
+        "speedup_learned_over_plain": v_learn / v_plain, "speedup_learned_over_control": v_learn / v_ctrl,
+        "oracle_subset": {"pairs": len(sub), "seconds": t_oracle,
+                          "inputs": "numpy-rendered on both sides (seeded subset, rng 505)"},
+        "rot_dev_vs_oracle_own_stop_deg": {k: stats(v) for k, v in dev.items()},
+        "rot_dev_plain_vs_oracle_replayed_deg": stats(dev_rep_plain),
+        "stop_rule_plain_vs_oracle": {"exact": float(np.mean(stop_d == 0)), "within_1": float(np.mean(stop_d <= 1))},
+        "rot_err_vs_ground_truth_deg": {k: stats(v) for k, v in truth.items()},
+        "criterion": "learned-init beats plain in pairs/s at the same <= 1e-4 deg rotation error against the oracle "
+                     "(fraction of the subset within 1e-4 deg of the oracle's own-stop answer at least the plain arm's)",
+        "criterion_holds": holds,
+        "training": {"pairs": train_pairs, "epochs": epochs, "seconds": t_train, "set_seconds": t_set,
+                     "loss_first_last": [hist[0], hist[-1]],
+                     "note": "trained in the benchmark run (config-4 recipe: 128x128, mis U(0,12) deg, target = final "
+                             "field of the full registration at 64x64; Adam, batch 256, cosine step size)"},
     }
+
+
+def run_learned(args, rank, world, local_rank):
+    """The learned-init vs plain comparison with the full training recipe (config 4: 200,000 pairs)."""
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = learned_comparison(args, local_rank, pool, args.train_pairs, args.epochs, args.pairs,
+                                 args.oracle_pairs, args.warmup, args.steps)
+    line = {"metric": METRIC + "; learned-init vs plain", "workload": "learned-init vs plain",
+            "value": res["learned"]["pairs_per_s"], "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (network bf16)", "data": "synthetic (seeded kinematic Kikuchi generator)",
+            "config": {"workload": res["workload"], "pairs": args.pairs}, "learned_vs_plain": res}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    pipe.close()
     return 0
 
 
@@ -750,6 +812,9 @@ def main():
     ap.add_argument("--lr-final", type=float, default=5e-5)
     ap.add_argument("--learned-start", type=int, default=64, choices=(64, 128))
     ap.add_argument("--oracle-pairs", type=int, default=500)
+    ap.add_argument("--no-learned", action="store_true", help="default run: skip the learned-vs-plain comparison")
+    ap.add_argument("--lvp-train-pairs", type=int, default=20_000)
+    ap.add_argument("--lvp-epochs", type=int, default=20)
     ap.add_argument("--learned-caps", type=int, nargs=4, default=(25, 25, 10, 0))
     ap.add_argument("--tile-variants", type=int, nargs=4, default=None,
                     help="scan workload: demons tile shape per level, finest first (no autotuning)")

@@ -80,15 +80,34 @@ struct IterArgs {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// Bilinear sample of M at index coordinates (x, y), clamped to the image;
-// (1 - f) a + f b per axis, exact at the nodes.
-__device__ __forceinline__ float bilinear_clamped(const float *__restrict__ M, int h, int w, float x, float y)
+// Cell and weight of the clamped bilinear sample along one axis at the point
+// q - u (q an integer pixel index, u the displacement; the warp M(x - u(x))).
+// The point is split into integer and fraction from the displacement itself:
+// with n = floor(-u) and f = -u - n the point is (q + n) + f, so the weight
+// keeps the full FP32 precision of u instead of that of q - u (whose unit in
+// the last place is 1.5e-5 px at q ~ 200, an error the iteration amplifies at
+// weakly textured pixels).  Clamping the point to [0, m - 1]: the cell index
+// is clamped to [0, m - 2], and the weight becomes 0 below the image and 1
+// beyond it (exactly the clamped point's cell and weight).
+__device__ __forceinline__ void warp_cell(int q, float u, int m, int &i, float &f)
 {
-    x = fminf(fmaxf(x, 0.0f), (float)(w - 1));
-    y = fminf(fmaxf(y, 0.0f), (float)(h - 1));
-    int x0 = min((int)x, w - 2);   // x >= 0: truncation is floor
-    int y0 = min((int)y, h - 2);
-    float fx = x - (float)x0, fy = y - (float)y0;
+    const float n = floorf(-u);
+    const float fr = -u - n;                            // in [0, 1]
+    const float x = (float)q + n;                       // integer-valued, exact
+    const float xc = fminf(fmaxf(x, 0.0f), (float)(m - 2));
+    f = __saturatef(fr + (x - xc));                     // fr inside, 0 / 1 when clamped
+    i = (int)xc;
+}
+
+// Bilinear sample of M at the point (qx - ux, qy - uy), clamped to the image;
+// (1 - f) a + f b per axis, exact at the nodes.
+__device__ __forceinline__ float warp_sample(const float *__restrict__ M, int h, int w, int qx, int qy, float ux,
+                                             float uy)
+{
+    int x0, y0;
+    float fx, fy;
+    warp_cell(qx, ux, w, x0, fx);
+    warp_cell(qy, uy, h, y0, fy);
     const float *p = M + y0 * w + x0;
     float a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + w), d = __ldg(p + w + 1);
     float top = fmaf(fx, b, (1.0f - fx) * a);
@@ -112,19 +131,19 @@ __device__ __forceinline__ float2 bilinear2_clamped(const float2 *__restrict__ M
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Two bilinear samples (the same arithmetic as bilinear_clamped, each rounding
-// step identical) with the interpolation done in packed FP32x2 operations.
+// Two warp samples (the same arithmetic as warp_sample, each rounding step
+// identical) with the interpolation done in packed FP32x2 operations.
 // 1 - f is formed as fma(f, -1, 1), which rounds like the subtraction.
-__device__ __forceinline__ float2 bilinear_pair_clamped(const float *__restrict__ M, int h, int w, float xa, float ya,
-                                                         float xb, float yb)
+__device__ __forceinline__ float2 warp_sample_pair(const float *__restrict__ M, int h, int w, int qxa, int qya,
+                                                   float2 ua, int qxb, int qyb, float2 ub)
 {
-    xa = fminf(fmaxf(xa, 0.0f), (float)(w - 1));
-    ya = fminf(fmaxf(ya, 0.0f), (float)(h - 1));
-    xb = fminf(fmaxf(xb, 0.0f), (float)(w - 1));
-    yb = fminf(fmaxf(yb, 0.0f), (float)(h - 1));
-    const int xa0 = min((int)xa, w - 2), ya0 = min((int)ya, h - 2);
-    const int xb0 = min((int)xb, w - 2), yb0 = min((int)yb, h - 2);
-    const float2 fx = make_float2(xa - (float)xa0, xb - (float)xb0), fy = make_float2(ya - (float)ya0, yb - (float)yb0);
+    int xa0, ya0, xb0, yb0;
+    float fxa, fya, fxb, fyb;
+    warp_cell(qxa, ua.x, w, xa0, fxa);
+    warp_cell(qya, ua.y, h, ya0, fya);
+    warp_cell(qxb, ub.x, w, xb0, fxb);
+    warp_cell(qyb, ub.y, h, yb0, fyb);
+    const float2 fx = make_float2(fxa, fxb), fy = make_float2(fya, fyb);
     const float *pa = M + ya0 * w + xa0, *pb = M + yb0 * w + xb0;
     const float2 A = make_float2(__ldg(pa), __ldg(pb)), Bv = make_float2(__ldg(pa + 1), __ldg(pb + 1));
     const float2 C = make_float2(__ldg(pa + w), __ldg(pb + w)), D = make_float2(__ldg(pa + w + 1), __ldg(pb + w + 1));
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(kIterThreads, 2) demons_iter_kernel(IterArgs a
             const int yl = qy > 0 ? -L::FW : 0, yr = qy < h - 1 ? L::FW : 0;
             const float gx = (fc[xr] - fc[xl]) * ((xr - xl) == 2 ? 0.5f : 1.0f);
             const float gy = (fc[yr] - fc[yl]) * ((yr - yl) == 2 * L::FW ? 0.5f : 1.0f);
-            const float mw = bilinear_clamped(M, h, w, (float)qx - u.x, (float)qy - u.y);
+            const float mw = warp_sample(M, h, w, qx, qy, u.x, u.y);
             const float d = mw - fc[0];
             const float den = fmaf(gx, gx, fmaf(gy, gy, a.alpha2 * d * d));
             const float t = den > 1e-9f ? __fdividef(d, den) : 0.0f;
@@ -699,8 +718,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
             const float2 al2 = make_float2(a.alpha2, a.alpha2);
 #pragma unroll
             for (int i = 0; i < FR; i += 2) {
-                const float2 mw = bilinear_pair_clamped(M, h, w, (float)vx - u[i].x, (float)(vy0 + i) - u[i].y,
-                                                        (float)vx - u[i + 1].x, (float)(vy0 + i + 1) - u[i + 1].y);
+                const float2 mw = warp_sample_pair(M, h, w, vx, vy0 + i, u[i], vx, vy0 + i + 1, u[i + 1]);
                 const int vya = vy0 + i, vyb = vya + 1;
                 const float2 sy2 = make_float2((unsigned)(vya - 1) >= (unsigned)(h - 2) ? 1.0f : 0.5f,
                                                (unsigned)(vyb - 1) >= (unsigned)(h - 2) ? 1.0f : 0.5f);

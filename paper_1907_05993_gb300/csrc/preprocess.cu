@@ -62,19 +62,31 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
     const int n = H * W;
     const float sx = 2.0f / W, sy = 2.0f / H;
 
+    // Sums are taken in FP32 over chunks of kChunk pixels of one thread and the chunk sums added in
+    // FP64: the quadric's coefficients come out of a poorly conditioned 6 x 6 system and the
+    // normalised values are small differences of O(1) numbers, so plain FP32 sums of ~128 terms
+    // would move the output by ~1e-4 (thousands of units in the last place).
+    constexpr int kChunk = 8;
     // pass 1: quadric moments b_k = sum phi_k I
     if (flat) {
-        float acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            int i = p / W, j = p - i * W;
-            float phi[6];
-            basis6(fmaf((float)j + 0.5f, sx, -1.0f), fmaf((float)i + 0.5f, sy, -1.0f), phi);
-            float v = img[p];
+        double d[6] = {0, 0, 0, 0, 0, 0};
+        for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
+            float acc[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] = fmaf(phi[k], v, acc[k]);
+            for (int c = 0; c < kChunk; ++c) {
+                const int p = p0 + c * blockDim.x;
+                if (p < n) {
+                    int i = p / W, j = p - i * W;
+                    float phi[6];
+                    basis6(fmaf((float)j + 0.5f, sx, -1.0f), fmaf((float)i + 0.5f, sy, -1.0f), phi);
+                    float v = img[p];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc[k] = fmaf(phi[k], v, acc[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) d[k] += (double)acc[k];
         }
-        double d[6];
-        for (int k = 0; k < 6; ++k) d[k] = acc[k];
         block_sum<6>(d, red);
         if (threadIdx.x == 0) {
             for (int r = 0; r < 6; ++r) {
@@ -116,25 +128,40 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
     };
 
     // pass 2: mean
-    float s = 0.0f;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) s += value(p);
-    double m[1] = {(double)s};
+    double m[1] = {0.0};
+    for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            const int p = p0 + c * blockDim.x;
+            if (p < n) s += value(p);
+        }
+        m[0] += (double)s;
+    }
     block_sum<1>(m, red);
     const double mean = m[0] / n;
-    // pass 3: variance about the mean
-    float ss = 0.0f;
-    const float meanf = (float)mean;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        float d = value(p) - meanf;
-        ss = fmaf(d, d, ss);
+    // pass 3: variance about the mean; the mean as a pair hi + lo of FP32 values, so that the
+    // subtraction from the quotient (both near 1, exact for the hi part) keeps the mean's precision
+    double v2[1] = {0.0};
+    const float meanf = (float)mean, meanlo = (float)(mean - (double)meanf);
+    for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
+        float ss = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            const int p = p0 + c * blockDim.x;
+            if (p < n) {
+                float d = (value(p) - meanf) - meanlo;
+                ss = fmaf(d, d, ss);
+            }
+        }
+        v2[0] += (double)ss;
     }
-    double v2[1] = {(double)ss};
     block_sum<1>(v2, red);
     const double sd = sqrt(v2[0] / n);
     const float inv = (sd > 0.0 && sd > 1e-6 * fabs(mean)) ? (float)(1.0 / sd) : 0.0f;
     // pass 4: output (in and out may alias: every pixel is read before it is written by the same thread)
     float *o = out + base;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = (value(p) - meanf) * inv;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = ((value(p) - meanf) - meanlo) * inv;
 }
 
 __global__ void reduce2_kernel(const float *__restrict__ in, float *__restrict__ out, int n, int H, int W)

@@ -28,14 +28,17 @@ def test_large_pattern_pair_against_oracle(oracle):
     torch.cuda.synchronize()
     exp = oracle.pipeline(refs[0].astype(np.float64), tests[0].astype(np.float64), roi, 128, spec.geom, 7, caps)
     field = out["field"].cpu().numpy()[0]
-    d = np.abs(field - exp["field"])
     # the field bar scales with the pixel pitch: 1e-3 px at 256 px across is 4e-3 px at 1024
-    bar = 1e-3 * 1024 / 256
-    assert np.mean(d <= bar) >= 0.99, (np.mean(d <= 1e-3), np.mean(d <= bar), d.max())
+    import fp32_sensitivity as FS
+    pre = max(FS.preprocess_ulps(out["test_pre"].cpu().numpy()[0], exp["ptest"]),
+              FS.preprocess_ulps(out["ref_pre"].cpu().numpy()[0], exp["pref"]))
+    members = FS.perturbed_fields(oracle, exp["pref"], exp["ptest"], 7, caps, input_ulps=pre)
+    fo = FS.assert_field_parity(field, exp["field"], members, tol=1e-3 * 1024 / 256, what="1024x1024")
+    print(f"1024x1024: preprocessing {pre:.1f} FP32 units, {fo}")
     Rg = out["R_finite"].cpu().numpy()[0].reshape(3, 3)
     assert rot_err(Rg, exp["R_finite"]) <= 1e-5
     Fg = out["F"].cpu().numpy()[0].reshape(3, 3)
-    assert np.abs(Fg - exp["F"]).max() <= 1e-6 or rot_err(Fg, exp["F"]) <= 1e-5
+    assert np.abs(Fg - exp["F"]).max() <= 1e-6
     tie = out["near_tie"].cpu().numpy()[0].astype(bool) | exp["near_tie"]
-    assert np.mean(np.all(out["peak"].cpu().numpy()[0][~tie] == exp["peak"][~tie], axis=1)) >= 0.96
+    assert np.array_equal(out["peak"].cpu().numpy()[0][~tie], exp["peak"][~tie])
     pipe.close()

@@ -77,35 +77,82 @@ def test_learned_start_reaches_plain_rotation(trained):
     pipe.close()
 
 
+def _render_pair4(p):
+    spec = K.config4(200_000)
+    return K.render_ref(spec, K.ref_index(spec, p)), K.render_test(spec, p)
+
+
+def _oracle_pre4(p):
+    import oracle
+    ref, test = _render_pair4(p)
+    return oracle.preprocess(ref.astype(np.float64), True), oracle.preprocess(test.astype(np.float64), True)
+
+
+TARGET_TOL = 5e-4   # 1e-3 px of the 128x128 field, in the 64x64 pixels of the target
+
+
+def _target_check(args):
+    """Oracle target of one pair (its registration replaying the library's counts, box-averaged to 64x64
+    in 64x64-pixel units) against the library's; returns the largest deviation."""
+    p, it, got = args
+    import oracle
+    pr, pt = _oracle_pre4(p)
+    fo, _ = oracle.demons_register(pr, pt, 3, [100] * 3, 1.0, 1.0, 1.0, 5, 1e-4, replay=it)
+    exp = np.stack([oracle.reduce2(fo[c]) / 2 for c in range(2)])
+    return float(np.abs(got - exp).max())
+
+
+def _field_check(args):
+    """The field bar of tests/fp32_sensitivity.py on the 128x128 field of one pair (eight FP32 executions of
+    the oracle: the pairs checked here are the worst of the sample, selected for their deviation)."""
+    p, it, field, gref, gtest = args
+    import oracle
+    import fp32_sensitivity as FS
+    pr, pt = _oracle_pre4(p)
+    pre = max(FS.preprocess_ulps(gref, pr), FS.preprocess_ulps(gtest, pt))
+    exp = FS.perturbed_register(oracle, pr, pt, 3, it, seed=-1)
+    members = FS.perturbed_fields(oracle, pr, pt, 3, it, members=8, seed0=77 + p, input_ulps=pre)
+    return FS.assert_field_parity(field, exp, members, what=f"training pair {p}")
+
+
 def test_training_targets_spot_checked_against_oracle(oracle):
-    """Training targets (the final field of the full registration, box-averaged to 64x64 in
-    64x64-pixel units) from the library path, against the oracle's registration of the same
-    numpy-rendered training pairs replayed with the library's per-level iteration counts."""
+    """Training targets (the final field of the full registration, box-averaged to 64x64 in 64x64-pixel
+    units) from the library path on a seeded 1 % sample of the 200,000 training pairs, against the
+    oracle's registration of the same numpy-rendered pairs replaying the library's per-level iteration
+    counts.  A target within 5e-4 everywhere passes; otherwise the pair's 128x128 field must meet the
+    field bar of tests/fp32_sensitivity.py (no wider than the oracle's own FP32 sensitivity)."""
+    import multiprocessing as mp
     import torch
     import paper_1907_05993_gb300 as P
-    spec = K.config4(200_000)
-    pairs = [3, 70_001, 150_007]
-    ctx = P.hrebsd_create(0)
-    prm = P.demons_params(3, [100] * 3, 1.0, 1.0, 1.0, 1e-4, 5)
-    for p in pairs:
-        ref = K.render_ref(spec, K.ref_index(spec, p))
-        test = K.render_test(spec, p)
-        r_d, t_d = torch.from_numpy(ref[None]).cuda(), torch.from_numpy(test[None]).cuda()
-        P.hrebsd_preprocess_batch(ctx, r_d, 1, 128, 128, 1, r_d)
-        P.hrebsd_preprocess_batch(ctx, t_d, 1, 128, 128, 1, t_d)
-        field = torch.empty((1, 2, 128, 128), device="cuda")
-        iters = torch.empty((1, 3), dtype=torch.int32, device="cuda")
-        status = torch.empty((1,), dtype=torch.int32, device="cuda")
-        P.hrebsd_demons_register_batch(ctx, r_d, t_d, torch.zeros(1, dtype=torch.int32, device="cuda"), 1, 1, 128,
-                                       128, prm, None, field, iters, status)
-        target = torch.empty((1, 2, 64, 64), device="cuda")
-        P.hrebsd_field_resample(ctx, field, 1, 128, 128, target, 64, 64)
-        torch.cuda.synchronize()
-        it = iters.cpu().numpy()[0]
-        pr = oracle.preprocess(ref.astype(np.float64), True)
-        pt = oracle.preprocess(test.astype(np.float64), True)
-        fo, _ = oracle.demons_register(pr, pt, 3, [100] * 3, 1.0, 1.0, 1.0, 5, 1e-4, replay=it)
-        exp = np.stack([oracle.reduce2(fo[c]) / 2 for c in range(2)])
-        d = np.abs(target.cpu().numpy()[0] - exp)
-        assert np.mean(d <= 1e-3) >= 0.99 and d.max() <= 0.05, (p, d.max(), np.mean(d <= 1e-3))
-    P.hrebsd_destroy(ctx)
+    rng = np.random.default_rng(4040)
+    pairs = sorted(rng.choice(200_000, 2_000, replace=False).tolist())
+    n = len(pairs)
+    with mp.get_context("spawn").Pool(16) as pool:
+        renders = pool.map(_render_pair4, pairs, chunksize=25)
+        ctx = P.hrebsd_create(0)
+        try:
+            refs = torch.from_numpy(np.stack([r for r, _ in renders])).cuda()
+            tests = torch.from_numpy(np.stack([t for _, t in renders])).cuda()
+            P.hrebsd_preprocess_batch(ctx, refs, n, 128, 128, 1, refs)
+            P.hrebsd_preprocess_batch(ctx, tests, n, 128, 128, 1, tests)
+            prm = P.demons_params(3, [100] * 3, 1.0, 1.0, 1.0, 1e-4, 5)
+            field = torch.empty((n, 2, 128, 128), device="cuda")
+            iters = torch.empty((n, 3), dtype=torch.int32, device="cuda")
+            status = torch.empty((n,), dtype=torch.int32, device="cuda")
+            ridx = torch.arange(n, dtype=torch.int32, device="cuda")
+            P.hrebsd_demons_register_batch(ctx, refs, tests, ridx, n, n, 128, 128, prm, None, field, iters, status)
+            target = torch.empty((n, 2, 64, 64), device="cuda")
+            P.hrebsd_field_resample(ctx, field, n, 128, 128, target, 64, 64)
+            torch.cuda.synchronize()
+            it = iters.cpu().numpy()
+            tg = target.cpu().numpy().astype(np.float64)
+            dev = pool.map(_target_check, [(p, it[i], tg[i]) for i, p in enumerate(pairs)], chunksize=8)
+            loose = [i for i, d in enumerate(dev) if d > TARGET_TOL]
+            checks = pool.map(_field_check, [(pairs[i], it[i], field[i].cpu().numpy().astype(np.float64),
+                                              refs[i].cpu().numpy(), tests[i].cpu().numpy()) for i in loose],
+                              chunksize=1)
+        finally:
+            P.hrebsd_destroy(ctx)
+    print(f"training targets: {n - len(loose)}/{n} within {TARGET_TOL} everywhere (worst {max(dev):.2e}); "
+          f"{len(loose)} checked by the field bar of tests/fp32_sensitivity.py")
+    assert len(loose) <= 0.05 * n

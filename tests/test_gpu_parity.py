@@ -3,19 +3,19 @@
 Per-kernel tests feed both sides identical inputs (produced by the generator
 or by the oracle, rounded to FP32) and compare element by element.  End-to-end
 tests give both sides the same raw patterns and let each run its own chain.
-Tolerances (per pair): displacement field max |d| <= 1e-3 px, rotation
-<= 1e-5 rad, deformation-gradient components <= 1e-6, integer XCF peaks
-bit-exact (ROIs flagged as near ties on either side are excluded and counted).
+Tolerances (per pair): rotation <= 1e-5 rad, deformation-gradient components
+<= 1e-6, integer XCF peaks bit-exact (ROIs flagged as near ties on either side
+are excluded and counted), and the displacement field per pixel (below).
 
-The demons iteration amplifies rounding: perturbing the oracle's own FP64
-inputs by one FP32 unit roundoff moves its field by up to ~1e-2 px after 50
-iterations per level (near the pattern border and in weakly textured
-regions), so an FP32 field cannot match an FP64 one everywhere at long runs.
-The field bar is therefore read as: |d| <= 1e-3 px on >= 99.9 % of the pixels
-for runs of <= 10 iterations per level (the rest are isolated pixels where the
-oracle's own FP32-rounding sensitivity exceeds 1e-4 px), and on >= 99 % of
-the pixels plus the rotation fitted from the field within 1e-5 rad for
-full-length runs (and for runs without any smoothing, which are unstable).
+The field bar.  Runs of at most 10 iterations per level are held to 1e-3 px
+at every pixel.  Longer runs reach the regime where the demons iteration
+amplifies small differences at a few pixels (where the test-image gradient and
+the residual are both near zero): there the field is held to the oracle's own
+sensitivity, measured by running the oracle again with every stored
+intermediate rounded to FP32 (seeded stochastic rounding, four executions;
+tests/fp32_sensitivity.py): at the 99 %, 99.9 %, 99.99 % quantiles and the
+maximum the deviation is at most 1e-3 px or 3x what those FP32 executions of
+the oracle show, and so is the fraction of pixels beyond 1e-3 px.
 """
 import math
 
@@ -68,19 +68,18 @@ def f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
-def assert_field_parity(got, exp, caps, oracle=None, roi=None, geom=None, stable=True):
-    d = np.abs(got - exp)
-    if max(caps) <= 10 and stable:
-        # isolated ill-conditioned pixels aside (where the oracle itself moves by
-        # >1e-4 px under an FP32 rounding of its inputs), the bar holds everywhere
-        assert np.mean(d > FIELD_TOL) <= 1e-3, (d.max(), np.mean(d > FIELD_TOL))
-        assert np.percentile(d, 99.9) <= FIELD_TOL
-        return
-    assert np.percentile(d, 99) <= FIELD_TOL, np.percentile(d, 99)
-    if oracle is not None:
-        _, Rg = oracle.fit_rotation(got, roi, geom)
-        _, Re = oracle.fit_rotation(exp, roi, geom)
-        assert rot_err(Rg, Re) <= ROT_TOL
+def field_parity(oracle, got, ref, test, levels, iters, exp=None, what="", **kw):
+    """The field bar of the module docstring; exp (optional) is the unperturbed oracle field (computed
+    here otherwise).  Returns the measured quantiles."""
+    import fp32_sensitivity as FS
+    if exp is None:
+        exp = FS.perturbed_register(oracle, ref, test, levels, iters, seed=-1, **kw)
+    # short smoothed runs stay out of the unstable regime; without smoothing the iteration is unstable
+    strict = max(int(i) for i in iters) <= 10 and kw.get("sigma_f", 1.0) > 0
+    members = None if strict else FS.perturbed_fields(oracle, ref, test, levels, iters, **kw)
+    out = FS.assert_field_parity(got, exp, members, FIELD_TOL, what, strict=strict)
+    print(f"{what}: {out}")
+    return out
 
 
 # ------------------------------------------------------------------ a1
@@ -91,9 +90,14 @@ def test_preprocess_parity(torch, lib, ctx, oracle, H, W, flat):
     out = torch.empty((3, H, W), dtype=torch.float32, device="cuda")
     lib.hrebsd_preprocess_batch(ctx, cuda(torch, raw), 3, H, W, flat, out)
     got = out.cpu().numpy()
+    worst = 0.0
     for i in range(3):
         exp = oracle.preprocess(raw[i].astype(np.float64), bool(flat))
-        assert np.abs(got[i] - exp).max() < 2e-4
+        # in units of the FP32 spacing at the value's magnitude (at least that of 1.0)
+        ulps = np.abs(got[i] - exp) / np.spacing(np.maximum(np.abs(exp), 1.0).astype(np.float32))
+        worst = max(worst, float(ulps.max()))
+    print(f"preprocess {H}x{W} flat={flat}: worst {worst:.1f} FP32 units")
+    assert worst <= 32
 
 
 def test_preprocess_constant_and_inplace(torch, lib, ctx):
@@ -123,30 +127,38 @@ def _gpu_register(torch, lib, ctx, refs, tests, ridx, params, init=None):
     return field.cpu().numpy().astype(np.float64), iters.cpu().numpy(), status.cpu().numpy()
 
 
-@pytest.mark.parametrize("H,W,levels,caps,sigma", [
-    (64, 64, 1, [10], 1.0),             # single level
-    (96, 80, 2, [10, 10], 1.0),         # ragged tiles (80 is not a multiple of the tile width)
-    (256, 256, 4, [10] * 4, 1.0),       # the batched-scan geometry, short run
-    (128, 128, 3, [50, 50, 50], 1.0),   # the single-pair workload, full length
-    (256, 256, 4, [40] * 4, 1.0),       # the batched-scan geometry, long run
-    (64, 64, 2, [10, 10], 0.0),         # no smoothing (the paper's own setting)
-    (64, 64, 2, [10, 10], 1.6),         # radius 5
+@pytest.mark.parametrize("H,W,levels,caps,su,sf,alpha", [
+    (64, 64, 1, [30], 1.0, 1.0, 1.0),              # single level
+    (96, 80, 2, [20, 20], 1.0, 1.0, 1.0),          # ragged tiles (80 is not a multiple of the tile width)
+    (256, 256, 4, [15] * 4, 1.0, 1.0, 1.0),        # the batched-scan geometry, short run
+    (128, 128, 3, [50, 50, 50], 1.0, 1.0, 1.0),    # the single-pair workload, full length
+    (256, 256, 4, [40] * 4, 1.0, 1.0, 1.0),        # the batched-scan geometry, long run
+    (64, 64, 2, [10, 10], 0.0, 0.0, 1.0),          # no smoothing (the paper's own setting)
+    (64, 64, 2, [20, 20], 1.6, 1.6, 1.0),          # radius 5
+    (128, 128, 3, [20] * 3, 0.0, 1.0, 1.0),        # update not smoothed, field smoothed
+    (128, 128, 3, [20] * 3, 1.6, 1.0, 0.5),        # distinct sigmas (radius 5 and 3), alpha 0.5
+    (128, 128, 2, [20, 20], 1.0, 1.6, 2.0),        # the other way round, alpha 2
 ])
-def test_demons_fixed_iterations_parity(torch, lib, ctx, oracle, H, W, levels, caps, sigma):
+def test_demons_fixed_iterations_parity(torch, lib, ctx, oracle, H, W, levels, caps, su, sf, alpha):
     spec = K.ScanSpec(n_pairs=3, H=H, W=W, n_refs=2, mis_lo_deg=0.5, mis_hi_deg=2.5, seed=21)
     pairs = [_pre_pair(oracle, spec, p) for p in range(3)]
     refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
     tests = np.stack([t for _, t in pairs])
     ridx = np.array([K.ref_index(spec, p) for p in range(3)])
-    params = lib.demons_params(levels, caps, 1.0, sigma, sigma, 0.0, 0)
+    params = lib.demons_params(levels, caps, alpha, su, sf, 0.0, 0)
     field, iters, status = _gpu_register(torch, lib, ctx, refs, tests, ridx, params)
     S = 32 if H <= 128 else 64
     roi = K.roi_grid(H, W, S, H <= 128) if H in (128, 256) else None
     for b in range(3):
-        exp, it = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, 1.0, sigma, sigma)
+        exp, it = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, alpha, su, sf)
         assert list(iters[b]) == list(it) == list(caps)
-        assert_field_parity(field[b], exp, caps, oracle if roi is not None else None, roi, spec.geom,
-                            stable=sigma > 0)
+        field_parity(oracle, field[b], refs[ridx[b]], tests[b], levels, caps, exp=exp,
+                     what=f"{H}x{W} {caps} su={su} sf={sf} alpha={alpha} pair {b}",
+                     alpha=alpha, sigma_up=su, sigma_f=sf)
+        if roi is not None and max(caps) >= 40:   # and the rotation the fit reads from the field
+            _, Rg = oracle.fit_rotation(field[b], roi, spec.geom)
+            _, Re = oracle.fit_rotation(exp, roi, spec.geom)
+            assert rot_err(Rg, Re) <= ROT_TOL
     assert np.all((status & lib.PAIR_CAPPED) != 0)
 
 
@@ -169,26 +181,27 @@ def test_init_field_and_start_level(torch, lib, ctx, oracle):
     for b in range(2):
         exp, it = oracle.demons_register(refs[0], tests[b], 3, [8, 8, 8], 1.0, 1.0, 1.0, start_level=1, init=init[b])
         assert list(iters[b]) == [8, 8, 0] == list(it)
-        assert_field_parity(field[b], exp, [8, 8])
+        field_parity(oracle, field[b], refs[0], tests[b], 3, [8, 8, 0], exp=exp, what=f"init field pair {b}",
+                     init=init[b], start_level=1)
 
 
 def test_stop_rule_agreement(torch, lib, ctx, oracle):
-    """Each side decides its own stop; counts agree within +-1 on >= 90 % of (pair, level)."""
+    """Each side decides its own stop: per-level counts agree within +-1 on >= 90 % of (pair, level);
+    with the oracle replaying the library's counts every pair meets the field bar."""
     spec = K.ScanSpec(n_pairs=8, H=64, W=64, n_refs=2, seed=33, mis_lo_deg=0, mis_hi_deg=4)
     refs = np.stack([f32(oracle.preprocess(K.render_ref(spec, r).astype(np.float64))) for r in range(2)])
     tests = np.stack([_pre_pair(oracle, spec, p)[1] for p in range(8)])
     ridx = np.array([K.ref_index(spec, p) for p in range(8)])
     params = lib.demons_params(3, [60, 60, 60], 1.0, 1.0, 1.0, 1e-4, 5)
     field, iters, status = _gpu_register(torch, lib, ctx, refs, tests, ridx, params)
-    close, same, total = 0, 0, 0
+    close, total = 0, 0
     for b in range(8):
-        exp, it = oracle.demons_register(refs[ridx[b]], tests[b], 3, [60] * 3, 1.0, 1.0, 1.0, 5, 1e-4)
+        _, it = oracle.demons_register(refs[ridx[b]], tests[b], 3, [60] * 3, 1.0, 1.0, 1.0, 5, 1e-4)
         close += int(np.sum(np.abs(np.asarray(it) - iters[b]) <= 1))
         total += 3
-        if list(it) == list(iters[b]):
-            same += 1
-            assert_field_parity(field[b], exp, list(it))
-    assert close >= 0.9 * total and same >= 1
+        field_parity(oracle, field[b], refs[ridx[b]], tests[b], 3, iters[b], what=f"stop rule pair {b}")
+    print(f"stop rule: {close}/{total} (pair, level) within +-1")
+    assert close >= 0.9 * total
 
 
 # ------------------------------------------------------------------ a5 (same field on both sides)
@@ -385,8 +398,11 @@ def test_pipeline_single_pair_workload(torch, lib, oracle):
     torch.cuda.synchronize()
     exp = oracle.pipeline(refs[0].astype(np.float64), tests[0].astype(np.float64), roi, 32, spec.geom, 3, [50] * 3)
     field = out["field"].cpu().numpy()[0]
-    assert_field_parity(field, exp["field"], [50, 50, 50])
-    assert np.abs(field - exp["field"])[:, 16:-16, 16:-16].max() <= FIELD_TOL
+    import fp32_sensitivity as FS
+    pre = max(FS.preprocess_ulps(out["test_pre"].cpu().numpy()[0], exp["ptest"]),
+              FS.preprocess_ulps(out["ref_pre"].cpu().numpy()[0], exp["pref"]))
+    field_parity(oracle, field, exp["pref"], exp["ptest"], 3, [50] * 3, exp=exp["field"], what="single pair",
+                 input_ulps=pre)
     Rg = out["R_finite"].cpu().numpy().reshape(3, 3)
     assert rot_err(Rg, exp["R_finite"]) <= ROT_TOL
     Fg = out["F"].cpu().numpy().reshape(3, 3)
@@ -431,7 +447,7 @@ def test_tma_and_plain_iteration_paths_agree(torch, lib, oracle, H, W, levels, c
     assert np.abs(f0 - f1).max() <= 1e-5
     for b in range(3):
         exp, _ = oracle.demons_register(refs[ridx[b]], tests[b], levels, caps, 1.0, 1.0, 1.0)
-        assert_field_parity(f0[b], exp, caps)
+        field_parity(oracle, f0[b], refs[ridx[b]], tests[b], levels, caps, exp=exp, what=f"{H}x{W} pair {b}")
 
 
 # ------------------------------------------------------------------ strain / stress (Eq. 13-16)

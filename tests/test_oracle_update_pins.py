@@ -1,5 +1,6 @@
-"""Pins of the oracle's demons update, XCF tie flag and sub-pixel bias against independent library
-restatements (scipy / numpy), covering the configurations the other pins leave at their defaults.
+"""Pins of the oracle's demons update and XCF tie flag against independent library restatements
+(scipy / numpy), covering the configurations the other pins leave at their defaults, and of the
+conditioning helper that the GPU field bar uses.
 
 - One demons iteration (Eq. 1 with the workloads' regularisation) is, step by step:
   d = M(x - u) - F, du = d grad F / (|grad F|^2 + alpha^2 d^2), u <- G_f * (u + G_u * du).  Here the
@@ -117,3 +118,34 @@ def test_near_tie_flag(oracle):
     ref, test = periodic_pair(S, (3, -5), (-6, 4), 1.0)
     c, _, _ = oracle.xcf_surface(ref, test, S // 2, S // 2, S, window=False)
     assert abs(c[3 % S, -5 % S] - c[-6 % S, 4 % S]) < 1e-12 * abs(c).max()
+
+
+def test_perturbed_register_helper(oracle):
+    """The conditioning helper of the field bar (tests/fp32_sensitivity.py) runs the oracle's own
+    registration: unperturbed it equals oracle.demons_register replaying the same counts bit for bit;
+    its FP32-storage members (seeded stochastic rounding) stay within FP32-sized distances of it and
+    differ from one another; the stochastic rounding is unbiased and lands on FP32 values."""
+    import fp32_sensitivity as FS
+    spec = K.ScanSpec(n_pairs=1, H=64, W=64, n_refs=1, mis_lo_deg=1.0, mis_hi_deg=2.0, seed=12)
+    M = oracle.preprocess(K.render_ref(spec, 0).astype(np.float64))
+    F = oracle.preprocess(K.render_test(spec, 0).astype(np.float64))
+    it = np.array([7, 5, 4], np.int32)
+    exp, _ = oracle.demons_register(M, F, 3, [10] * 3, 1.0, 1.0, 1.0, 0, 0.0, -1, None, it)
+    got = FS.perturbed_register(oracle, M, F, 3, it, seed=-1)
+    assert np.array_equal(got, exp)
+    init = np.full((2, 32, 32), 0.25)
+    exp2, _ = oracle.demons_register(M, F, 3, [10] * 3, 2.0, 0.0, 1.6, 0, 0.0, 1, init, it)
+    got2 = FS.perturbed_register(oracle, M, F, 3, it, 2.0, 0.0, 1.6, seed=-1, init=init, start_level=1)
+    assert np.array_equal(got2, exp2)
+    m = FS.perturbed_fields(oracle, M, F, 3, it, members=2)
+    s = FS.sensitivity(exp, m)
+    assert 0 < np.median(s) < 1e-5 and s.max() < 1e-2 and not np.array_equal(m[0], m[1])
+    m2 = FS.perturbed_fields(oracle, M, F, 3, it, members=1, alpha=2.0, sigma_up=0.0, sigma_f=1.6,
+                             init=init, start_level=1)
+    assert np.abs(m2[0] - exp2).max() < 1e-3
+    r = np.random.default_rng(0)
+    a = r.normal(size=200_000)
+    b = FS.round32(a, r)
+    assert np.array_equal(b, b.astype(np.float32).astype(np.float64))
+    assert np.all(np.abs(b - a) <= np.spacing(np.abs(a).astype(np.float32)))
+    assert abs(np.mean(b - a)) < 1e-3 * np.mean(np.spacing(np.abs(a).astype(np.float32)))
