@@ -51,6 +51,7 @@ def _load():
         "oracle_demons_force": (d, [_D, _D, _D, _D, _D, i, i, d, _D]),
         "oracle_demons_level": (i, [_D, _D, i, i, _D, d, d, d, i, i, d, i, C.c_void_p]),
         "oracle_prolong": (None, [_D, i, i, _D]),
+        "oracle_prolong_to": (None, [_D, i, i, i, i, _D]),
         "oracle_demons_register": (i, [_D, _D, i, i, i, _I, d, d, d, i, d, i, C.c_void_p, C.c_void_p, _D, _I]),
         "oracle_fit_F": (i, [_D, _D, i, d, d, d, _D]),
         "oracle_polar": (None, [_D, _D]),
@@ -161,11 +162,15 @@ def demons_level(Fimg, M, u0, alpha, sigma_up, sigma_f, cap, window=0, tol=0.0, 
     return u, k, trace[:min(k + 1, cap)]
 
 
-def prolong(uc):
+def prolong(uc, H=None, W=None):
+    """Field of the next finer level: 2h x 2w, or the stored size H x W of that level (one more row or
+    column where the size did not halve)."""
     a = _d(uc)
     _, h, w = a.shape
-    out = np.empty((2, 2 * h, 2 * w))
-    _load().oracle_prolong(a, h, w, out)
+    H = 2 * h if H is None else int(H)
+    W = 2 * w if W is None else int(W)
+    out = np.empty((2, H, W))
+    _load().oracle_prolong_to(a, h, w, H, W, out)
     return out
 
 

@@ -79,7 +79,9 @@ void oracle_preprocess(const double *in, int H, int W, int flat, double *out)
 }
 
 /* Multi-resolution pyramid (Section 1, multi-resolution demons): one level
- * down is the 2x2 box mean. */
+ * down is the 2x2 box mean.  Reading for sizes that do not halve (the paper's
+ * 1244 x 1024 patterns with 7 levels): the coarser level is floor(H/2) x
+ * floor(W/2), so an odd last row or column takes no part in the mean. */
 void oracle_reduce2(const double *in, int H, int W, double *out)
 {
     int h = H / 2, w = W / 2;
@@ -227,16 +229,20 @@ int oracle_demons_level(const double *Fimg, const double *M, int H, int W, doubl
 /* ------------------------------------------------------------------ a4 */
 /* Field prolongation to the next finer level (Section 1: the coarse field
  * is the input of the finer level): bilinear at x_c = (x_f + 0.5)/2 - 0.5,
- * replicated edges, values doubled. */
-void oracle_prolong(const double *uc, int h, int w, double *uf)
+ * replicated edges, values doubled.  The finer level is the stored size H x W
+ * of that level, 2h x 2w or one more where the size did not halve (the
+ * extra last row or column samples past the coarse edge, i.e. the clamped
+ * edge value). */
+void oracle_prolong_to(const double *uc, int h, int w, int H, int W, double *uf)
 {
-    int H = 2 * h, W = 2 * w;
     for (int c = 0; c < 2; ++c)
         for (int i = 0; i < H; ++i)
             for (int j = 0; j < W; ++j)
                 uf[(size_t)c * H * W + i * W + j] =
                     2.0 * oracle_bilinear(uc + (size_t)c * h * w, h, w, (j + 0.5) * 0.5 - 0.5, (i + 0.5) * 0.5 - 0.5);
 }
+
+void oracle_prolong(const double *uc, int h, int w, double *uf) { oracle_prolong_to(uc, h, w, 2 * h, 2 * w, uf); }
 
 /* Multi-resolution demons registration of one pair (a2-a4) on preprocessed
  * patterns (oracle_preprocess).  ref = moving image M, test = fixed image F
@@ -274,8 +280,9 @@ int oracle_demons_register(const double *ref, const double *test, int H, int W, 
         iters_out[l] = oracle_demons_level(Fp[l], Mp[l], h, w, u, alpha, sigma_up, sigma_f, caps[l], window,
                                            tol, replay ? replay[l] : -1, NULL);
         if (l > 0) {
-            double *uf = (double *)malloc(sizeof(double) * 8 * (size_t)h * w);
-            oracle_prolong(u, h, w, uf);
+            int Hf = H >> (l - 1), Wf = W >> (l - 1);
+            double *uf = (double *)malloc(sizeof(double) * 2 * (size_t)Hf * Wf);
+            oracle_prolong_to(u, h, w, Hf, Wf, uf);
             free(u);
             u = uf;
         }

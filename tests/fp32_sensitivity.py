@@ -88,7 +88,7 @@ def perturbed_register(oracle, ref, test, levels, iters, alpha=1.0, sigma_up=1.0
             u, k, _ = oracle.demons_level(Fp[l], Mp[l], u, alpha, sigma_up, sigma_f, max(n, 1), 0, 0.0, n)
             assert k == n
         if l > 0:
-            u = r(oracle.prolong(u))
+            u = r(oracle.prolong(u, *Fp[l - 1].shape))
     return u
 
 

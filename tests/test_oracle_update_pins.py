@@ -149,3 +149,34 @@ def test_perturbed_register_helper(oracle):
     assert np.array_equal(b, b.astype(np.float32).astype(np.float64))
     assert np.all(np.abs(b - a) <= np.spacing(np.abs(a).astype(np.float32)))
     assert abs(np.mean(b - a)) < 1e-3 * np.mean(np.spacing(np.abs(a).astype(np.float32)))
+
+
+def test_pyramid_for_sizes_that_do_not_halve(oracle):
+    """Reading for the paper's 1244 x 1024 patterns: a level is floor(H/2) x floor(W/2) (an odd last row
+    or column takes no part in the 2 x 2 box mean) and the prolongation fills the stored finer size, its
+    extra last row/column taking the clamped edge value."""
+    x = np.random.default_rng(3).normal(size=(13, 19))
+    assert np.allclose(oracle.reduce2(x), x[:12, :18].reshape(6, 2, 9, 2).mean(axis=(1, 3)), atol=1e-14)
+    Yc, Xc = np.mgrid[0:6, 0:9].astype(float)
+    uc = np.stack([0.3 * Xc + 0.2, -0.1 * Yc + 0.4])
+    uf = oracle.prolong(uc, 13, 19)
+    assert uf.shape == (2, 13, 19)
+    assert np.array_equal(uf[:, :12, :18], oracle.prolong(uc))
+    Yf, Xf = np.mgrid[0:13, 0:19].astype(float)
+    # interior of a linear field: 2 a ((x_f + 0.5)/2 - 0.5) + 2 b
+    assert np.allclose(uf[0][:, 1:17], 0.3 * (Xf[:, 1:17] - 0.5) + 0.4, atol=1e-13)
+    # the last column (x_c = 8.75 beyond the coarse edge 8) and the one before it (x_c = 8.25) clamp to 8
+    assert np.allclose(uf[0][:, 17], 2 * (0.3 * 8 + 0.2)) and np.allclose(uf[0][:, 18], 2 * (0.3 * 8 + 0.2))
+    assert np.allclose(uf[1][12], 2 * (-0.1 * 5 + 0.4))
+    # a registration on 100 x 92 patterns (levels 100x92, 50x46, 25x23) recovers a sub-pixel shift
+    H, W, t = 100, 92, (0.6, -0.35)
+    Y, X = np.mgrid[0:H, 0:W].astype(float)
+
+    def img(dx, dy):
+        return (np.sin(0.31 * (X - dx) + 0.2 * (Y - dy)) + np.cos(0.17 * (X - dx) - 0.27 * (Y - dy))
+                + 0.5 * np.sin(0.05 * ((X - dx) ** 2 + (Y - dy) ** 2) / 10))
+    ref, test = oracle.normalize(img(0, 0)), oracle.normalize(img(*t))
+    field, iters = oracle.demons_register(ref, test, 3, [60] * 3, 1.0, 1.0, 1.0)
+    assert field.shape == (2, H, W)
+    inner = (slice(None), slice(15, -15), slice(15, -15))
+    assert abs(field[inner][0].mean() - t[0]) < 0.02 and abs(field[inner][1].mean() - t[1]) < 0.02
