@@ -318,6 +318,8 @@ def run_ours(args, rank, world, local_rank):
     tune_ms = pipe._tuned.get((B, wl["H"], wl["W"]))
 
     def shape_name(v):
+        if v == 5:
+            return "row sweep/w threads"
         return "x".join(map(str, P.TILE_SHAPES[v])) + f"/{P.TILE_THREADS[v]}t"
     tile_choice = [
         {"level": l, "shape": shape_name(P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l)),
@@ -756,8 +758,9 @@ def run_cnn(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ large patterns (f4)
 def run_large(args, rank, world, local_rank):
-    """1024 x 1024 patterns (the paper's 1244 x 1024 simulations cut to a width the 7-level pyramid
-    divides), 7 levels x 20 iterations (the paper's Inconel settings), 25 ROIs of 128 x 128."""
+    """Patterns at the paper's scale (Section 3.1): 1244 x 1024, 7 pyramid levels (widths 1244, 622, 311,
+    155, 77, 38, 19), 20 iterations per level (the paper's Inconel settings), 100 ROIs of 256 x 256 on a
+    10 x 10 grid."""
     import numpy as np
     import torch
     from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
@@ -765,11 +768,12 @@ def run_large(args, rank, world, local_rank):
     from synth import kikuchi as K
     torch.cuda.set_device(local_rank)
     n = args.large_pairs
-    spec = K.ScanSpec(n_pairs=n, H=1024, W=1024, n_refs=4, mis_lo_deg=0.0, mis_hi_deg=6.0, strain=5e-4,
+    H, W = 1024, 1244
+    spec = K.ScanSpec(n_pairs=n, H=H, W=W, n_refs=4, mis_lo_deg=0.0, mis_hi_deg=6.0, strain=5e-4,
                       strain_mode="sigma", counts=500.0, seed=6)
     refs, tests, ridx, _ = SG.make_scan_gpu(spec)
-    roi = K.roi_grid(1024, 1024, 128, False)
-    pipe = Pipeline(PipelineConfig(1024, 1024, roi, 128, 7, (20,) * 7))
+    roi = K.roi_grid_n(H, W, 256, 10)
+    pipe = Pipeline(PipelineConfig(H, W, roi, 256, 7, (20,) * 7))
     out = {}
     for _ in range(args.warmup):
         pipe.run(refs, tests, ridx, out=out)
@@ -784,8 +788,8 @@ def run_large(args, rank, world, local_rank):
     line = {"metric": "pattern pairs/s (demons+XCF), large patterns", "workload": "large", "value": n * args.steps / t,
             "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "data": "synthetic (seeded kinematic Kikuchi generator)", "dtype": "f32",
-            "config": {"workload": f"{n} pairs of 1024x1024, 4 references, mis U(0,6) deg, 7 levels x 20 iterations, "
-                                   f"25 ROIs 128x128", "ms_per_pair": 1e3 * t / (n * args.steps)}}
+            "config": {"workload": f"{n} pairs of 1244x1024, 4 references, mis U(0,6) deg, 7 levels x 20 iterations, "
+                                   f"100 ROIs 256x256", "ms_per_pair": 1e3 * t / (n * args.steps)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     pipe.close()
@@ -804,7 +808,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=("scan", "learned", "compare", "large", "single", "cnn"),
                     default="scan")
-    ap.add_argument("--large-pairs", type=int, default=512)
+    ap.add_argument("--large-pairs", type=int, default=256)
     ap.add_argument("--compare-orientations", type=int, default=16)
     ap.add_argument("--train-pairs", type=int, default=200_000)
     ap.add_argument("--epochs", type=int, default=30)

@@ -125,8 +125,10 @@ typedef struct {
 } hrebsd_geometry;
 
 /* Demons parameters.  levels: pyramid levels (1..8; level 0 is the full
- * size, level l is (H >> l) x (W >> l), both must stay >= 8 and H, W must be
- * divisible by 2^(levels-1)).  max_iters[l]: iteration cap of level l
+ * size, level l is (H >> l) x (W >> l), i.e. each level floor(h/2) x
+ * floor(w/2) of the one above (an odd last row or column takes no part in
+ * the 2x2 box mean, and the prolongation fills the finer level's stored
+ * size); the coarsest must stay >= 8 x 8).  max_iters[l]: iteration cap of level l
  * (0..4096).  alpha: force weight of Eq. 1 (du = d grad F / (|grad F|^2 +
  * alpha^2 d^2)).  sigma_update, sigma_field: Gaussian smoothing of the update
  * and of the field (radius ceil(3 sigma) <= 6; 0 = none).  stop_window w and
@@ -159,8 +161,11 @@ int hrebsd_gauss_taps(float sigma, float *taps);
  * `flat` the least-squares quadric c0 + c1 x + c2 y + c3 x^2 + c4 xy + c5 y^2
  * (x, y in [-1, 1] at pixel centres) is divided out, then the pattern is
  * brought to zero mean and unit standard deviation (a constant pattern
- * becomes all zeros).  in and out may alias.  Errors: EINVAL (n < 0, H or
- * W < 2, null pointers with n > 0). */
+ * becomes all zeros).  The quadric and the quotient are evaluated in
+ * double-FP32 precision (hi + lo), so the FP32 output is within a few units
+ * in the last place of the exact result.  in and out may alias.  Errors:
+ * EINVAL (n < 0, H or W < 2, H or W > 1536 with `flat`, null pointers with
+ * n > 0). */
 int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, int H, int W, int flat, float *out,
                             void *stream);
 
@@ -224,15 +229,19 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
                                          const hrebsd_demons_params *params, const float *init_field, float *field,
                                          int32_t *iters, int32_t *pair_status, void *stream);
 
-/* Tile shapes of the TMA-fed demons iteration (batching; the paper has no
+/* Tile shapes of the demons iteration (batching; the paper has no
  * counterpart): 0 = 64x32 outputs, 256 threads (2 CTAs per SM), 1 = 32x32
  * (3 per SM), 2 = 64x16 (3 per SM), 3 = 64x32 with 512 threads (2 per SM),
  * 4 = 64x64 with 768 threads (1 per SM; of 512, 768, 896 and 1024 threads
- * the fastest on GB300).  Shapes 1-4 exist for the Gaussian radius 3 (sigma = 1); other radii always
- * use shape 0.  Every shape computes each
- * output pixel with the same operations in the same order, so the field is
- * the same; only the grouping of the per-tile SSD partials changes. */
-#define HREBSD_TILE_VARIANTS 5
+ * the fastest on GB300), all fed by tensor-memory-accelerator tile copies;
+ * 5 = the row sweep: one CTA of w threads per pair walks down whole rows of
+ * the level with the separable y passes in per-column register windows (no
+ * halo rows; levels 64, 128 or 256 pixels wide; other levels fall back to
+ * shape 4).  Shapes 1-5 exist for the Gaussian radius 3 (sigma = 1); other
+ * radii always use shape 0.  Every shape computes each output pixel with the
+ * same operations in the same order, so the field is the same; only the
+ * grouping of the per-tile SSD partials changes. */
+#define HREBSD_TILE_VARIANTS 6
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small

@@ -798,6 +798,8 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
     if (tid == 0 && prev_pair >= 0) write_partial();
 }
 
+#include "demons_strip.cuh"
+
 struct CtrlArgs {
     const float *part;       // [B][tiles]
     double *hist;            // [B][hist_stride]
@@ -897,11 +899,12 @@ __global__ void __launch_bounds__(256) demons_finalize_kernel(const float2 *u0, 
 }
 
 // Prolongation (Section 1): fine(x_f) = 2 * bilinear(coarse, (x_f + 0.5)/2 - 0.5), interleaved fields.
-// One CTA per fine row (blockIdx.x = pair x 2h + row), threads along the row.
+// The fine level is H x W, 2h x 2w or one more row/column where the size did not halve (the extra row or
+// column samples past the coarse edge: the clamped edge value).  One CTA per fine row (blockIdx.x =
+// pair x H + row), threads along the row.
 __global__ void __launch_bounds__(256) prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B,
-                                                      int h, int w)
+                                                      int h, int w, int H, int W)
 {
-    const int H = 2 * h, W = 2 * w;
     const int b = (int)(blockIdx.x / (unsigned)H), i = (int)(blockIdx.x - (unsigned)b * H);
     if (b >= B) return;
     const float2 *src = uc + (size_t)b * h * w;
@@ -1006,9 +1009,10 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float2 *u0, con
 // (and hence the last bits of the level SSD) are grouped differently.  The
 // extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
 // use shape 0.
-constexpr int kTileVariants = 5;
-constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64};
-constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64};
+constexpr int kTileVariants = 6;
+constexpr int kStripVariant = 5;   // the row sweep (demons_strip.cuh): one CTA per pair, whole rows
+constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 256};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 256};
 constexpr int kMinTX = 32, kMinTY = 16;   // smallest tile extents (size the per-tile SSD partials)
 bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }
 constexpr bool min_extents_ok()
@@ -1019,6 +1023,44 @@ constexpr bool min_extents_ok()
 }
 static_assert(min_extents_ok(), "kMinTX/kMinTY must not exceed any tile shape (the SSD partials are sized by them)");
 static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
+
+// The row sweep covers levels 64, 128 or 256 pixels wide at the Gaussian radius 3 (its register
+// windows are 2r + 1 = 7 rows, the rows of one step).
+bool strip_ok(int rad, int w) { return rad == 3 && (w == 64 || w == 128 || w == 256); }
+
+template <int NT, bool IN_S>
+int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t st)
+{
+    using G = strip::Geo<3, NT>;
+    static int configured_dev = -1;
+    static int occ = 0;
+    auto k = strip::demons_strip_kernel<3, NT, IN_S>;
+    if (configured_dev != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, G::BYTES));
+        if (occ < 1) occ = 1;
+        configured_dev = ctx->device;
+    }
+    int grid = ctx->num_sms * occ;
+    if (grid > max_items) grid = max_items;
+    if (grid < 1) grid = 1;
+    hr_prof_begin(ctx, st);
+    k<<<grid, NT, G::BYTES, st>>>(a);
+    hr_prof_end(ctx, PROF_ITER, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// a.tiles must be 1 (one SSD partial per pair); a.in is s_k, or u_0 when !in_s.
+int launch_strip(hrebsd_ctx *ctx, bool in_s, const IterArgs &a, int max_items, cudaStream_t st)
+{
+    switch (a.w) {
+    case 64: return in_s ? launch_strip_t<64, true>(ctx, a, max_items, st) : launch_strip_t<64, false>(ctx, a, max_items, st);
+    case 128: return in_s ? launch_strip_t<128, true>(ctx, a, max_items, st) : launch_strip_t<128, false>(ctx, a, max_items, st);
+    case 256: return in_s ? launch_strip_t<256, true>(ctx, a, max_items, st) : launch_strip_t<256, false>(ctx, a, max_items, st);
+    default: return HREBSD_EINVAL;
+    }
+}
 
 int hr_tuned_variant(const hrebsd_ctx *ctx, int rad, int h, int w)
 {
@@ -1290,9 +1332,11 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
     for (int l = start; l >= 0; --l) {
         const int h = H >> l, w = W >> l;
         const int cap = p->max_iters[l];
-        const int var = hr_tuned_variant(ctx, rad, h, w);
+        int var = hr_tuned_variant(ctx, rad, h, w);
+        const bool use_strip = var == kStripVariant && strip_ok(rad, w) && !ctx->no_tma;
+        if (var == kStripVariant && !use_strip) var = 4;   // the row sweep does not cover this level: 64x64 tiles
         CUtensorMap tmS[3], tmF;
-        const bool use_tma = rad > 0 && !ctx->no_tma && cap > 1 &&
+        const bool use_tma = !use_strip && rad > 0 && !ctx->no_tma && cap > 1 &&
                              encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, (const float2 *)u0, tl[l],
                                          B, h, w, tmS, &tmF);
         // The launches of one level: list reset, cap x (iteration, control),
@@ -1304,9 +1348,10 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
             HR_LAUNCHED(ctx);
             for (int k = 0; k < cap; ++k) {
-                const bool tma_k = use_tma && (k > 0 || rad == 3);
+                const bool tma_k = !use_strip && use_tma && (k > 0 || rad == 3);
                 const int tx = tma_k ? kVarTX[var] : TX, ty = tma_k ? kVarTY[var] : TY;
-                const int tiles_x = (w + tx - 1) / tx, tiles = tiles_x * ((h + ty - 1) / ty);
+                const int tiles_x = use_strip ? 1 : (w + tx - 1) / tx;
+                const int tiles = use_strip ? 1 : tiles_x * ((h + ty - 1) / ty);
                 int *cur = (k & 1) ? list1 : list0, *nxt = (k & 1) ? list0 : list1;
                 IterArgs a;
                 a.Ftest = tl[l];
@@ -1327,7 +1372,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 a.taps = taps;
                 a.px_count = hr_prof_pixiters(ctx);
                 a.err = ctx->d_err;
-                if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, k > 0, k > 0 ? tmS[k & 1] : tmS[2], tmF, a, B * tiles, st);
+                if (use_strip) e2 = launch_strip(ctx, k > 0, a, B, st);
+                else if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, k > 0, k > 0 ? tmS[k & 1] : tmS[2], tmF, a, B * tiles, st);
                 else e2 = dispatch_iter(ctx, rad, a, B * tiles, st);
                 if (e2) return e2;
                 CtrlArgs c;
@@ -1360,11 +1406,12 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                                         iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
                 return e2;
             if (l > 0) {
-                if ((long long)B * (2 * h) > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
-                const unsigned rows = (unsigned)B * (unsigned)(2 * h);
-                const int threads = 2 * w >= 256 ? 256 : (2 * w + 31) / 32 * 32;
+                const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
+                if ((long long)B * Hf > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
+                const unsigned rows = (unsigned)B * (unsigned)Hf;
+                const int threads = Wf >= 256 ? 256 : (Wf + 31) / 32 * 32;
                 hr_prof_begin(ctx, st);
-                prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w);
+                prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
                 hr_prof_end(ctx, PROF_DEMONS_AUX, st);
                 HR_LAUNCHED(ctx);
             }
@@ -1380,7 +1427,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                             ctx->d_err};
         static_assert(sizeof(kp) / sizeof(kp[0]) <= sizeof(key.p) / sizeof(key.p[0]), "graph key");
         for (size_t i = 0; i < sizeof(kp) / sizeof(kp[0]); ++i) key.p[i] = kp[i];
-        const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window};
+        const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window, (int)use_strip};
         for (size_t i = 0; i < sizeof(ki) / sizeof(ki[0]); ++i) key.i[i] = ki[i];
         key.f[0] = p->alpha;
         key.f[1] = p->stop_tol;
@@ -1398,7 +1445,7 @@ int check_register_args(hrebsd_ctx *ctx, const float *ref, const float *test, co
     if (!ctx || !p || B < 0 || R < 1) return HREBSD_EINVAL;
     if (p->levels < 1 || p->levels > 8) return HREBSD_EINVAL;
     const int L = p->levels;
-    if (H % (1 << (L - 1)) || W % (1 << (L - 1))) return HREBSD_EINVAL;
+    // level l is (H >> l) x (W >> l): floor halving, sizes that do not halve included
     if ((H >> (L - 1)) < 8 || (W >> (L - 1)) < 8) return HREBSD_EINVAL;
     for (int l = 0; l < L; ++l)
         if (p->max_iters[l] < 0 || p->max_iters[l] > 4096) return HREBSD_EINVAL;
@@ -1510,10 +1557,13 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
             int best_v = 0;
             for (int v = 0; v < kTileVariants; ++v) {
                 if (!variant_ok(rad, v) || ctx->no_tma) continue;
+                const bool sv = v == kStripVariant;
+                if (sv && !strip_ok(rad, w)) continue;
                 CUtensorMap tmS[3], tmF;
-                if (!encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
+                if (!sv && !encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
                     continue;
-                const int tiles_x = (w + kVarTX[v] - 1) / kVarTX[v], tiles = tiles_x * ((h + kVarTY[v] - 1) / kVarTY[v]);
+                const int tiles_x = sv ? 1 : (w + kVarTX[v] - 1) / kVarTX[v];
+                const int tiles = sv ? 1 : tiles_x * ((h + kVarTY[v] - 1) / kVarTY[v]);
                 IterArgs a;
                 a.Ftest = test;
                 a.Mref = ref;
@@ -1538,7 +1588,8 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 for (; k < kWarm; ++k) {
                     a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                     a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
-                    int e2 = dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
+                    int e2 = sv ? launch_strip(ctx, true, a, Bt, st)
+                                : dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                     if (e2) return e2;
                 }
                 for (int rep = 0; rep < kRounds; ++rep) {
@@ -1546,7 +1597,8 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                     for (int j = 0; j < kBatch; ++j, ++k) {
                         a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                         a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
-                        int e2 = dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
+                        int e2 = sv ? launch_strip(ctx, true, a, Bt, st)
+                                    : dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                         if (e2) return e2;
                     }
                     HR_CHECK(cudaEventRecord(ev[1], st));
@@ -1561,7 +1613,7 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 // synthetic patterns (small, smooth displacements; every pair active) timed the
                 // 64x32 and 64x64 shapes as a tie at 256x256 where the 64x64 one was 4 % faster
                 // on the batched scan; a clearly faster small tile still wins.
-                const float score = ms * (1.0f + 0.01f * log2f(4096.0f / (float)(kVarTX[v] * kVarTY[v])));
+                const float score = ms * (1.0f + 0.01f * fmaxf(0.0f, log2f(4096.0f / (float)(kVarTX[v] * kVarTY[v]))));
                 if (best_v == 0 && best == 0.0f) {
                     best = score;
                     best_v = v;

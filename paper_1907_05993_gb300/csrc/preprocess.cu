@@ -51,23 +51,73 @@ __device__ void block_sum(double (&v)[NV], double *red /* [32][NV] */)
     __syncthreads();
 }
 
+// Unevaluated sums hi + lo of two FP32 values ("float-float", ~48 bits): the
+// background quadric and the quotient pattern / quadric are evaluated in this
+// precision, because the normalised output is a difference of two numbers near
+// one divided by a standard deviation near 0.1, so plain FP32 would carry a
+// smooth error pattern of ~10 units in the last place of the output.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_from_double(double v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+// exact sum of two floats (Knuth's two-sum)
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);   // exact error of the product
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return two_sum(p, e);
+}
+
+// coordinate (2 k + 1 - n) / n in [-1, 1] of pixel k of n as hi + lo
+__device__ __forceinline__ ff pixel_coord(int k, int n)
+{
+    const float num = (float)(2 * k + 1 - n), den = (float)n;   // exact integers
+    const float h = __fdiv_rn(num, den);
+    const float l = __fdiv_rn(__fmaf_rn(-h, den, num), den);   // the residual num - h n is exact
+    return {h, l};
+}
+
+constexpr int kMaxDim = 1536;   // largest H and W of the background fit (per-row and per-column terms in shared memory)
+
 __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__restrict__ in, float *out, int H,
                                                                  int W, int flat, QuadricInverse qi)
 {
     __shared__ double red[32 * 6];
-    __shared__ float coef[6];
+    __shared__ double coef[6];
+    __shared__ float2 rowA[kMaxDim], rowB[kMaxDim];   // per row: c0 + c2 y + c5 y^2 and c1 + c4 y (hi, lo)
+    __shared__ float2 colX[kMaxDim];                  // per column: x (hi, lo)
     __shared__ int ok_flag;
     const size_t base = (size_t)blockIdx.x * H * W;
     const float *img = in + base;
     const int n = H * W;
-    const float sx = 2.0f / W, sy = 2.0f / H;
 
     // Sums are taken in FP32 over chunks of kChunk pixels of one thread and the chunk sums added in
-    // FP64: the quadric's coefficients come out of a poorly conditioned 6 x 6 system and the
-    // normalised values are small differences of O(1) numbers, so plain FP32 sums of ~128 terms
-    // would move the output by ~1e-4 (thousands of units in the last place).
+    // FP64: the quadric's coefficients come out of a poorly conditioned 6 x 6 system, and plain FP32
+    // sums of ~128 terms would move the output by ~1e-4.
     constexpr int kChunk = 8;
-    // pass 1: quadric moments b_k = sum phi_k I
+    // pass 1: quadric moments b_k = sum phi_k I (basis at the correctly rounded pixel coordinates)
     if (flat) {
         double d[6] = {0, 0, 0, 0, 0, 0};
         for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
@@ -76,10 +126,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
             for (int c = 0; c < kChunk; ++c) {
                 const int p = p0 + c * blockDim.x;
                 if (p < n) {
-                    int i = p / W, j = p - i * W;
+                    const int i = p / W, j = p - i * W;
                     float phi[6];
-                    basis6(fmaf((float)j + 0.5f, sx, -1.0f), fmaf((float)i + 0.5f, sy, -1.0f), phi);
-                    float v = img[p];
+                    basis6(__fdiv_rn((float)(2 * j + 1 - W), (float)W), __fdiv_rn((float)(2 * i + 1 - H), (float)H), phi);
+                    const float v = img[p];
 #pragma unroll
                     for (int k = 0; k < 6; ++k) acc[k] = fmaf(phi[k], v, acc[k]);
                 }
@@ -92,65 +142,86 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
             for (int r = 0; r < 6; ++r) {
                 double c = 0.0;
                 for (int k = 0; k < 6; ++k) c += qi.ginv[r * 6 + k] * d[k];
-                coef[r] = (float)c;
+                coef[r] = c;
             }
             ok_flag = 1;
         }
         __syncthreads();
+        // per-row parts of the quadric in FP64, kept as hi + lo
+        for (int i = threadIdx.x; i < H; i += blockDim.x) {
+            const double y = (2.0 * i + 1.0 - H) / H;
+            const ff A = ff_from_double(coef[0] + y * (coef[2] + y * coef[5]));
+            const ff Bc = ff_from_double(coef[1] + y * coef[4]);
+            rowA[i] = make_float2(A.hi, A.lo);
+            rowB[i] = make_float2(Bc.hi, Bc.lo);
+        }
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            const ff x = pixel_coord(j, W);
+            colX[j] = make_float2(x.hi, x.lo);
+        }
+        __syncthreads();
+    }
+    const ff C = flat ? ff_from_double(coef[3]) : ff{0.0f, 0.0f};
+
+    // the quadric at pixel p as hi + lo: A(y) + x (B(y) + x c3)
+    auto fit_at = [&](int p) -> ff {
+        const int i = p / W, j = p - i * W;
+        const ff x = {colX[j].x, colX[j].y};
+        const ff A = {rowA[i].x, rowA[i].y}, Bc = {rowB[i].x, rowB[i].y};
+        return ff_add(A, ff_mul(x, ff_add(Bc, ff_mul(x, C))));
+    };
+    if (flat) {
         // the division is skipped when the fitted surface is not positive everywhere
         int bad = 0;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            int i = p / W, j = p - i * W;
-            float phi[6];
-            basis6(fmaf((float)j + 0.5f, sx, -1.0f), fmaf((float)i + 0.5f, sy, -1.0f), phi);
-            float fit = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fit = fmaf(coef[k], phi[k], fit);
-            bad |= !(fit > 0.0f);
-        }
+        for (int p = threadIdx.x; p < n; p += blockDim.x) bad |= !(fit_at(p).hi > 0.0f);
         if (__syncthreads_or(bad) && threadIdx.x == 0) ok_flag = 0;
         __syncthreads();
     }
     const bool use_fit = flat && ok_flag;
 
-    auto value = [&](int p) -> float {
-        float v = img[p];
-        if (use_fit) {
-            int i = p / W, j = p - i * W;
-            float phi[6];
-            basis6(fmaf((float)j + 0.5f, sx, -1.0f), fmaf((float)i + 0.5f, sy, -1.0f), phi);
-            float fit = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fit = fmaf(coef[k], phi[k], fit);
-            v = v / fit;
-        }
-        return v;
+    // the pattern divided by the quadric, as hi + lo
+    auto value = [&](int p) -> ff {
+        const float v = img[p];
+        if (!use_fit) return {v, 0.0f};
+        const ff f = fit_at(p);
+        const float q = __fdiv_rn(v, f.hi);
+        float r = __fmaf_rn(-q, f.hi, v);   // exact remainder of the correctly rounded quotient
+        r = __fmaf_rn(-q, f.lo, r);
+        return two_sum(q, __fdiv_rn(r, f.hi));
     };
 
     // pass 2: mean
     double m[1] = {0.0};
     for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
-        float s = 0.0f;
+        float sh = 0.0f, sl = 0.0f;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             const int p = p0 + c * blockDim.x;
-            if (p < n) s += value(p);
+            if (p < n) {
+                const ff q = value(p);
+                sh += q.hi;
+                sl += q.lo;
+            }
         }
-        m[0] += (double)s;
+        m[0] += (double)sh + (double)sl;
     }
     block_sum<1>(m, red);
     const double mean = m[0] / n;
-    // pass 3: variance about the mean; the mean as a pair hi + lo of FP32 values, so that the
-    // subtraction from the quotient (both near 1, exact for the hi part) keeps the mean's precision
+    const ff mu = ff_from_double(mean);
+    // the quotient minus the mean, in FP32 at the end (both parts subtracted before the sum)
+    auto centred = [&](int p) -> float {
+        const ff q = value(p);
+        return __fadd_rn(__fsub_rn(q.hi, mu.hi), __fsub_rn(q.lo, mu.lo));
+    };
+    // pass 3: variance about the mean
     double v2[1] = {0.0};
-    const float meanf = (float)mean, meanlo = (float)(mean - (double)meanf);
     for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
         float ss = 0.0f;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             const int p = p0 + c * blockDim.x;
             if (p < n) {
-                float d = (value(p) - meanf) - meanlo;
+                const float d = centred(p);
                 ss = fmaf(d, d, ss);
             }
         }
@@ -161,9 +232,13 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
     const float inv = (sd > 0.0 && sd > 1e-6 * fabs(mean)) ? (float)(1.0 / sd) : 0.0f;
     // pass 4: output (in and out may alias: every pixel is read before it is written by the same thread)
     float *o = out + base;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = ((value(p) - meanf) - meanlo) * inv;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = centred(p) * inv;
 }
 
+// One pyramid level down: the 2x2 box mean, floor(H/2) x floor(W/2) (an odd
+// last row or column takes no part).  VEC: H and W even, so every pair of
+// neighbours starts on an 8-byte boundary and is read as one float2.
+template <bool VEC>
 __global__ void reduce2_kernel(const float *__restrict__ in, float *__restrict__ out, int n, int H, int W)
 {
     const int h = H >> 1, w = W >> 1;
@@ -173,8 +248,14 @@ __global__ void reduce2_kernel(const float *__restrict__ in, float *__restrict__
         int rem = (int)(idx - img * h * w);
         int i = rem / w, j = rem - i * w;
         const float *p = in + img * H * W + (size_t)(2 * i) * W + 2 * j;
-        float2 a = *reinterpret_cast<const float2 *>(p);
-        float2 b = *reinterpret_cast<const float2 *>(p + W);
+        float2 a, b;
+        if (VEC) {
+            a = *reinterpret_cast<const float2 *>(p);
+            b = *reinterpret_cast<const float2 *>(p + W);
+        } else {
+            a = make_float2(p[0], p[1]);
+            b = make_float2(p[W], p[W + 1]);
+        }
         out[idx] = 0.25f * ((a.x + a.y) + (b.x + b.y));
     }
 }
@@ -227,7 +308,10 @@ int hr_launch_reduce2(hrebsd_ctx *ctx, const float *in, float *out, int n, int H
     int cap = ctx->num_sms * 16;
     if (blocks > cap) blocks = cap;
     hr_prof_begin(ctx, st);
-    reduce2_kernel<<<blocks, 256, 0, st>>>(in, out, n, H, W);
+    if (H % 2 == 0 && W % 2 == 0 && ((uintptr_t)in & 7) == 0)
+        reduce2_kernel<true><<<blocks, 256, 0, st>>>(in, out, n, H, W);
+    else
+        reduce2_kernel<false><<<blocks, 256, 0, st>>>(in, out, n, H, W);
     hr_prof_end(ctx, PROF_DEMONS_AUX, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
@@ -241,6 +325,7 @@ extern "C" int hrebsd_preprocess_batch(hrebsd_ctx *ctx, const float *in, int n, 
     if (!in || !out) return HREBSD_EINVAL;
     int st = hr_set_device(ctx);
     if (st) return st;
+    if (flat && (H > kMaxDim || W > kMaxDim)) return HREBSD_EINVAL;
     QuadricInverse qi;
     if (flat && quadric_inverse(H, W, &qi)) return HREBSD_EINVAL;
     if (!flat)

@@ -20,7 +20,8 @@ noise of +-`input_ulps` FP32 units, the size of the FP32 preprocessing error (``
 measures it on the patterns at hand; test_preprocess_parity holds it within 32 units).  ``assert_field_parity`` then holds the deviation d(x) = |got - oracle| to the distribution
 of the members' own deviations from the oracle: at the quantiles 99 %, 99.9 %, 99.99 % and the
 maximum, d is at most max(1e-3 px, 3 x the largest member's value of that quantile), and the
-fraction of pixels with d > 1e-3 px is at most 3 x the largest member's fraction + 1e-4 (the tail
+fraction of pixels with d > 1e-3 px is at most 3 x the largest member's fraction plus the larger of 1e-4 and
+four pixels (the tail
 of a chaotic response is heavy: the members' own maxima differ by up to 10x).  In words: the FP32
 field is no further from the FP64 oracle than the FP64 oracle is from itself under FP32-sized
 perturbations, at every level of the distribution up to the worst pixel.  ``strict`` holds every
@@ -127,5 +128,6 @@ def assert_field_parity(got, exp, members=None, tol=FIELD_TOL, what="", strict=F
         assert g <= max(tol, FACTOR * ref), (what, f"quantile {q}", g, "oracle's own", ref)
     fref = float(np.max([np.mean(x > tol) for x in dm]))
     out["frac_over_oracle"] = fref
-    assert out["frac_over"] <= FACTOR * fref + 1e-4, (what, "pixels over", out["frac_over"], "oracle's own", fref)
+    floor = max(1e-4, 4.0 / d.size * 2)   # d holds both field components: four pixels
+    assert out["frac_over"] <= FACTOR * fref + floor, (what, "pixels over", out["frac_over"], "oracle's own", fref)
     return out

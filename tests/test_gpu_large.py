@@ -42,3 +42,53 @@ def test_large_pattern_pair_against_oracle(oracle):
     tie = out["near_tie"].cpu().numpy()[0].astype(bool) | exp["near_tie"]
     assert np.array_equal(out["peak"].cpu().numpy()[0][~tie], exp["peak"][~tie])
     pipe.close()
+
+
+def _oracle_member(args):
+    import oracle
+    import fp32_sensitivity as FS
+    pref, ptest, levels, iters, seed, pre = args
+    return FS.perturbed_register(oracle, pref, ptest, levels, iters, seed=seed, input_ulps=pre)
+
+
+def test_paper_scale_pattern_pair_against_oracle(oracle):
+    """The paper's first test set at its own scale (Section 3.1): 1244 x 1024 patterns (width 1244 does
+    not halve: levels 1244, 622, 311, 155, 77, 38, 19 columns), 7 levels with the stop rule and at most
+    25 iterations per level, 100 ROIs of 256 x 256 on a 10 x 10 grid (the XCF's out-of-shared-memory
+    path).  The oracle replays the library's per-level counts."""
+    import multiprocessing as mp
+    import torch
+    from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
+    import fp32_sensitivity as FS
+    H, W, L = 1024, 1244, 7
+    spec = K.ScanSpec(n_pairs=2, H=H, W=W, n_refs=1, mis_lo_deg=4.0, mis_hi_deg=8.0, strain=1e-4,
+                      strain_mode="norm", counts=500.0, seed=45)
+    refs, tests, ridx, Ft = K.make_scan(spec)
+    roi = K.roi_grid_n(H, W, 256, 10)
+    pipe = Pipeline(PipelineConfig(H, W, roi, 256, L, (25,) * L, stop_tol=1e-4, stop_window=5))
+    out = pipe.run(torch.from_numpy(refs).cuda(), torch.from_numpy(tests).cuda(), torch.from_numpy(ridx).cuda())
+    torch.cuda.synchronize()
+    iters = out["iters"].cpu().numpy()
+    assert iters.shape == (2, L) and iters.min() >= 1
+    for b in range(2):
+        exp = oracle.pipeline(refs[0].astype(np.float64), tests[b].astype(np.float64), roi, 256, spec.geom, L,
+                              [25] * L, 1.0, 1.0, 5, 1e-4, replay=iters[b])
+        pre = max(FS.preprocess_ulps(out["test_pre"].cpu().numpy()[b], exp["ptest"]),
+                  FS.preprocess_ulps(out["ref_pre"].cpu().numpy()[0], exp["pref"]))
+        with mp.get_context("spawn").Pool(4) as pool:
+            members = pool.map(_oracle_member, [(exp["pref"], exp["ptest"], L, iters[b], 900 + m, pre)
+                                                for m in range(4)])
+        field = out["field"].cpu().numpy()[b]
+        # 1e-3 px at 256 px across is ~5e-3 px at 1244
+        fo = FS.assert_field_parity(field, exp["field"], members, tol=1e-3 * W / 256, what=f"1244x1024 pair {b}")
+        Rg = out["R_finite"].cpu().numpy()[b].reshape(3, 3)
+        Fg = out["F"].cpu().numpy()[b].reshape(3, 3)
+        tie = out["near_tie"].cpu().numpy()[b].astype(bool) | exp["near_tie"]
+        peaks_equal = np.array_equal(out["peak"].cpu().numpy()[b][~tie], exp["peak"][~tie])
+        print(f"1244x1024 pair {b}: iters {iters[b].tolist()} rot {rot_err(Rg, exp['R_finite']):.1e} "
+              f"F {np.abs(Fg - exp['F']).max():.1e} peaks equal {peaks_equal} ({int((~tie).sum())} of 100) "
+              f"field {fo}")
+        assert rot_err(Rg, exp["R_finite"]) <= 1e-5
+        assert np.abs(Fg - exp["F"]).max() <= 1e-6
+        assert peaks_equal and (~tie).sum() >= 90
+    pipe.close()

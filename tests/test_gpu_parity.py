@@ -253,13 +253,16 @@ def test_remap_parity(torch, lib, ctx, oracle):
 
 
 # ------------------------------------------------------------------ a7
-@pytest.mark.parametrize("H,S,window", [(128, 32, 1), (256, 64, 1), (64, 16, 0), (256, 128, 1)])
+@pytest.mark.parametrize("H,S,window", [(128, 32, 1), (256, 64, 1), (64, 16, 0), (256, 128, 1), (512, 256, 1),
+                                         (320, 256, 0)])
 def test_xcf_parity(torch, lib, ctx, oracle, H, S, window):
     spec = K.ScanSpec(n_pairs=4, H=H, W=H, n_refs=1, seed=17, mis_lo_deg=0.0, mis_hi_deg=0.6)
     a = np.stack([_pre_pair(oracle, spec, p) for p in range(4)])
     refs, tests = a[:, 0], a[:, 1]
     if S == 128:
         roi = np.array([[128, 128], [100, 140]], np.int32)
+    elif S == 256:   # the out-of-shared-memory path; one ROI per pair reaches outside the image
+        roi = np.array([[H // 2, H // 2], [130, H - 130], [H - 129, 140], [100, H // 2]], np.int32)
     else:
         roi = K.roi_grid(H, H, S, False) if S >= 32 else np.array([[16, 16], [32, 40], [48, 24]], np.int32)
     N = len(roi)
@@ -272,6 +275,10 @@ def test_xcf_parity(torch, lib, ctx, oracle, H, S, window):
                              cuda(torch, roi), N, S, window, q, pk, ph, tie)
     q, pk, ph, tie = q.cpu().numpy(), pk.cpu().numpy(), ph.cpu().numpy(), tie.cpu().numpy().astype(bool)
     excluded = 0
+    inside = np.array([c[0] >= S // 2 and c[1] >= S // 2 and c[0] + S // 2 <= H and c[1] + S // 2 <= H for c in roi])
+    assert np.isnan(q[:, ~inside]).all()
+    roi, q, pk, ph, tie = roi[inside], q[:, inside], pk[:, inside], ph[:, inside], tie[:, inside]
+    N = len(roi)
     for b in range(B):
         eq, epk, eph, etie = oracle.xcf_roi(refs[b], tests[b], roi, S, window=bool(window))
         ok = ~(etie | tie[b])
