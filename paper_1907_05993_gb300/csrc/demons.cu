@@ -36,6 +36,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "internal.cuh"
 #include "tma.cuh"
@@ -96,6 +97,18 @@ __device__ __forceinline__ void warp_cell(int q, float u, int m, int &i, float &
     const float x = (float)q + n;                       // integer-valued, exact
     const float xc = fminf(fmaxf(x, 0.0f), (float)(m - 2));
     f = __saturatef(fr + (x - xc));                     // fr inside, 0 / 1 when clamped
+    i = (int)xc;
+}
+
+// warp_cell with the pixel index q and the largest cell index m - 2 given as
+// floats (integer-valued, exact): the same cell and weight.
+__device__ __forceinline__ void warp_cell_f(float q, float u, float m2, int &i, float &f)
+{
+    const float n = floorf(-u);
+    const float fr = -u - n;
+    const float x = q + n;
+    const float xc = fminf(fmaxf(x, 0.0f), m2);
+    f = __saturatef(fr + (x - xc));
     i = (int)xc;
 }
 

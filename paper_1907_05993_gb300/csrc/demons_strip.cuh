@@ -1,80 +1,114 @@
 // Demons iteration as a vertical sweep over whole pattern rows (included by
-// demons.cu; same arithmetic per pixel as the tile kernels).
+// demons.cu; same arithmetic per pixel as the tile kernels, so the field is
+// bit-identical to theirs).
 //
 // One CTA of NT = w threads owns one active pair of a level w pixels wide and
-// walks down its rows in steps of R = 7 rows; thread t owns column t.  Per step:
-//   x pass of G_f on the step's s rows (runs of 8 outputs from a staged copy
-//     of the rows with replicated edge columns)                    -> RX rows;
+// walks down its rows in steps of R = 7 rows; thread t owns column t and warp
+// v the 32 columns [32 v, 32 v + 32).  Per step:
+//   x pass of G_f on the step's s rows, for the warp's own columns -> RX rows;
 //   per column, in registers: the y pass of G_f over a rolling window of the
-//     last 2r + 1 RX rows gives u (lagging the input by r rows), the warp of
-//     the moving image at x - u and the force of Eq. 1 (test-image rows
-//     staged in shared memory with replicated edges)               -> du rows;
-//   x pass of G_u on the du rows                                   -> DX rows;
-//   per column: the y pass of G_u over a rolling window of DX rows, plus u,
-//     gives s_{k+1} (lagging by 2r rows), stored to HBM.
-// The separable passes thus read each input once per output in the vertical
-// direction (register windows) and have no halo rows at all; only the x passes
-// read a halo of r columns, replicated at the image edges.  Rows outside the
-// image repeat the edge row: the first row pushed into a window fills all of
-// it, and after the last row the last du row is pushed again.  The window
-// length 2r + 1 = 7 equals R, so the register windows rotate back to their
-// starting positions every step.  The next step's s and test-image rows are
-// copied by cp.async while the current step is computed.
+//     last 2r + 1 RX rows gives u (lagging the input by r rows); the bilinear
+//     gathers of the moving image at x - u are issued for all R rows before
+//     any of them is used, then the force of Eq. 1 (test-image rows staged in
+//     shared memory)                                            -> du rows;
+//   one CTA barrier (the du rows' x pass reads r columns of the neighbouring
+//     warps);
+//   x pass of G_u on the du rows, for the warp's own columns     -> DX rows;
+// and, at the start of the next step, per column: the y pass of G_u over a
+// rolling window of DX rows, plus u, gives s_{k+1} (lagging by 2r rows),
+// stored to HBM.  Everything but the du rows stays within a warp, so a step
+// has a single CTA barrier (du rows alternate between two buffers).
+// The separable passes read each input once per output in the vertical
+// direction (register windows) and have no halo rows at all; the x passes
+// read r halo columns on each side, which hold the row's edge values
+// (replicated borders).  Rows outside the image repeat the edge row: the
+// first row pushed into a window fills all of it, and after the last row the
+// last DX row is pushed again.  A window of 2r + 1 = R rows keeps row y in
+// slot y mod R, so its slots are compile-time indices in the unrolled row loop
+// and nothing moves between registers.  The s and test-image rows of step
+// k + 2 are requested by bulk copies (one per row, issued by 16 lanes of one
+// warp, completion on an mbarrier that every thread waits on with a bounded
+// wait) as soon as step k's barrier shows its buffer consumed.
 namespace strip {
 
 constexpr int R = 7;
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int RAD, int NT>
 struct Geo {
     static_assert(2 * RAD + 1 == R, "the register windows rotate with the step only for 2r + 1 = R");
-    static constexpr int SW = NT + 2 * RAD;             // staged s / du row: columns [-r, NT + r)
-    static constexpr int SST = (SW / 2) % 2 ? SW : SW + 2;   // row stride (float2): odd number of 16-byte slots
+    static_assert(RAD == 3, "rows with halo keep their data at a 16-byte boundary 4 elements in");
+    static_assert(NT % 32 == 0 && NT >= 64 && NT / RUN == 4 * (NT / 32), "four x-pass runs per warp and row, two edge warps");
+    static constexpr int HO = 4;                        // halo rows: data column c at index c + HO
+    static constexpr int HST = NT + 10;                 // float2 stride of halo rows (odd 16-byte slots)
+    static constexpr int XST = NT + 2;                  // float2 stride of RX / DX rows (odd 16-byte slots)
     static constexpr int FR_ = R + 2;                   // test-image rows of a step
-    static constexpr int FST = NT + 2 + ((NT + 2) % 4 == 1 ? 0 : 1);  // row stride (float): columns [-1, NT]
-    static constexpr int XST = NT + 2;                  // RX / DX row stride (float2)
-    static constexpr size_t S_OFF = 0;                                    // [2][R][SST] float2
-    static constexpr size_t F_OFF = S_OFF + (size_t)2 * R * SST * 8;      // [2][FR_][FST] float
-    static constexpr size_t X_OFF = F_OFF + (((size_t)2 * FR_ * FST * 4 + 15) / 16) * 16;   // [R][XST] float2
-    static constexpr size_t D_OFF = X_OFF + (size_t)R * XST * 8;         // [R][SST] float2
-    static constexpr size_t BYTES = D_OFF + (size_t)R * SST * 8;
+    static constexpr int FST = NT + 4;                  // float stride of test-image rows (odd 16-byte slots)
+    static_assert((HST / 2) % 2 == 1 && (XST / 2) % 2 == 1 && (FST / 4) % 2 == 1, "odd numbers of 16-byte slots");
+    static constexpr size_t S_OFF = 0;                                   // s rows [2][R][HST] float2
+    static constexpr size_t F_OFF = S_OFF + (size_t)2 * R * HST * 8;     // test rows [2][FR_][FST] float
+    static constexpr size_t D_OFF = F_OFF + (size_t)2 * FR_ * FST * 4;   // du rows [2][R][HST] float2
+    static constexpr size_t X_OFF = D_OFF + (size_t)2 * R * HST * 8;     // RX rows [R][XST] float2
+    static constexpr size_t Y_OFF = X_OFF + (size_t)R * XST * 8;         // DX rows [R][XST] float2
+    static constexpr size_t BYTES = Y_OFF + (size_t)R * XST * 8;
+    static constexpr uint32_t S_BYTES = (uint32_t)R * NT * 8;            // bytes of a step's s rows
+    static constexpr uint32_t F_BYTES = (uint32_t)FR_ * NT * 4;          // ... and test-image rows
+    static_assert(S_OFF % 16 == 0 && F_OFF % 16 == 0 && X_OFF % 16 == 0 && D_OFF % 16 == 0 && Y_OFF % 16 == 0,
+                  "16-byte aligned regions");
 };
 
-// The cp.async copies of step k of a pair: s rows clamp(7k + i) (i < R) with columns [-r, NT + r)
-// clamped, and test-image rows clamp(7k - r - 1 + i) (i < R + 2) with columns [-1, NT] clamped.
+// The bulk copies of step k of a pair into one buffer: s rows clamp(R k + i) (i < R) and test-image
+// rows clamp(R k - r - 1 + i) (i < R + 2), whole rows.  Called by every lane of one warp: lane 0
+// announces the bytes, then lanes 0 .. R - 1 copy the s rows and lanes R .. 2R + 1 the test rows.
 template <int RAD, int NT, bool IN_S>
-__device__ __forceinline__ void stage_copies(const IterArgs &a, int pair, int k, float2 *sS, float *sF)
+__device__ __forceinline__ void issue_step(const IterArgs &a, int pair, int k, float2 *sS, float *sF, uint64_t *bar,
+                                           int lane)
 {
     using G = Geo<RAD, NT>;
     const int h = a.h;
     const size_t plane = (size_t)h * NT;
-    if (IN_S) {
-        const float2 *src = a.in + (size_t)pair * plane;
-        for (int idx = threadIdx.x; idx < R * G::SW; idx += NT) {
-            const int i = idx / G::SW, c = idx - i * G::SW;
-            const int gy = min(7 * k + i, h - 1), gx = min(max(c - RAD, 0), NT - 1);
-            cp_async8(sS + i * G::SST + c, src + (size_t)gy * NT + gx);
+    if (lane == 0) hr_tma::mbar_arrive_expect_tx(bar, (IN_S ? G::S_BYTES : 0u) + G::F_BYTES);
+    __syncwarp();
+    if (lane < R) {
+        if (IN_S) {
+            hr_tma::fence_proxy_async();   // the buffer's previous contents were read by the generic proxy
+            hr_tma::load_bulk(sS + lane * G::HST + G::HO, a.in + (size_t)pair * plane + (size_t)min(R * k + lane, h - 1) * NT,
+                              NT * 8, bar);
         }
+    } else if (lane < R + G::FR_) {
+        const int i = lane - R;
+        hr_tma::fence_proxy_async();
+        hr_tma::load_bulk(sF + i * G::FST,
+                          a.Ftest + (size_t)pair * plane + (size_t)min(max(R * k - RAD - 1 + i, 0), h - 1) * NT,
+                          NT * 4, bar);
     }
-    const float *fsrc = a.Ftest + (size_t)pair * plane;
-    for (int idx = threadIdx.x; idx < G::FR_ * (NT + 2); idx += NT) {
-        const int i = idx / (NT + 2), c = idx - i * (NT + 2);
-        const int gy = min(max(7 * k - RAD - 1 + i, 0), h - 1), gx = min(max(c - 1, 0), NT - 1);
-        cp_async4(sF + i * G::FST + c, fsrc + (size_t)gy * NT + gx);
+}
+
+// x pass of the run of RUN outputs starting at column c0 of a row with halo (data column c at
+// index c + HO = c + r + 1): an aligned window of RUN + 2r + 2 elements from column c0 - r - 1,
+// used from its second element.  Same sums as run_x.
+template <int RAD>
+__device__ __forceinline__ void run_x_halo(const float2 *row, int c0, float2 *out, const float2 (&t)[2 * RAD + 1])
+{
+    constexpr int NW = RUN + 2 * RAD + 2;   // 16 elements: columns c0 - 4 .. c0 + 11
+    float2 win[NW];
+    const float4 *in4 = reinterpret_cast<const float4 *>(row + c0);   // index c0 = column c0 - 4
+#pragma unroll
+    for (int j = 0; j < NW / 2; ++j) {
+        const float4 v = in4[j];
+        win[2 * j] = make_float2(v.x, v.y);
+        win[2 * j + 1] = make_float2(v.z, v.w);
     }
-    cp_async_commit();
+    float2 acc[RUN];
+#pragma unroll
+    for (int o = 0; o < RUN; ++o) acc[o] = __fmul2_rn(t[0], win[o + 1]);
+#pragma unroll
+    for (int k = 1; k <= 2 * RAD; ++k)
+#pragma unroll
+        for (int o = 0; o < RUN; ++o) acc[o] = ffma2(t[k], win[o + 1 + k], acc[o]);
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+#pragma unroll
+    for (int o = 0; o < RUN; o += 2) out4[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
 }
 
 template <int RAD, int NT, bool IN_S>
@@ -84,145 +118,219 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sS0 = reinterpret_cast<float2 *>(smraw + G::S_OFF);
     float *sF0 = reinterpret_cast<float *>(smraw + G::F_OFF);
-    float2 *sX = reinterpret_cast<float2 *>(smraw + G::X_OFF);
-    float2 *sD = reinterpret_cast<float2 *>(smraw + G::D_OFF);
+    float2 *sD0 = reinterpret_cast<float2 *>(smraw + G::D_OFF);
+    float2 *sRX = reinterpret_cast<float2 *>(smraw + G::X_OFF);
+    float2 *sDX = reinterpret_cast<float2 *>(smraw + G::Y_OFF);
     __shared__ float red[NT / 32];
+    __shared__ __align__(8) uint64_t bar[2];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NWARP = NT / 32;
+    // the Gaussian taps are symmetric (t[j] = t[2r - j]): half of them in registers
+    float2 tfh[RAD + 1], tuh[RAD + 1];
+#pragma unroll
+    for (int k = 0; k <= RAD; ++k) {
+        tfh[k] = make_float2(a.taps.f[k], a.taps.f[k]);
+        tuh[k] = make_float2(a.taps.up[k], a.taps.up[k]);
+    }
     float2 tf[2 * RAD + 1], tu[2 * RAD + 1];
 #pragma unroll
     for (int k = 0; k <= 2 * RAD; ++k) {
-        tf[k] = make_float2(a.taps.f[k], a.taps.f[k]);
-        tu[k] = make_float2(a.taps.up[k], a.taps.up[k]);
+        tf[k] = tfh[k <= RAD ? k : 2 * RAD - k];
+        tu[k] = tuh[k <= RAD ? k : 2 * RAD - k];
     }
     const int n_active = *a.n_active;
     if (blockIdx.x == 0 && t == 0) {
         *a.n_next_reset = 0;
         if (a.px_count) atomicAdd(a.px_count, (unsigned long long)n_active * a.h * a.w);
     }
+    if (t == 0) {
+        hr_tma::mbar_init(&bar[0], 1);
+        hr_tma::mbar_init(&bar[1], 1);
+        hr_tma::fence_mbar_init();
+    }
+    __syncthreads();
     const int h = a.h;
     const size_t plane = (size_t)h * NT;
-    const int nsteps = (h + 2 * RAD + R - 1) / R;
-    // one-sided difference (scale 1) in the first and last column
+    const int nsteps = (h + 2 * RAD + R - 1) / R;   // >= 2 for h >= 8
+    // a step whose u / du rows R k - r .. R k + r all lie in 1 .. h - 2 and whose s rows start below
+    // row 0: no window fill, no edge row, no row outside the image (and likewise for its outputs)
+    auto interior_step = [&](int k) { return k >= 1 && R * k + RAD <= h - 2; };
+    // one-sided difference (scale 1) in the first and last column; clamped neighbour columns
     const float sx = (t == 0 || t == NT - 1) ? 1.0f : 0.5f;
+    const int tl = max(t - 1, 0), tr = min(t + 1, NT - 1);
+    const float tf_ = (float)t, mx2 = (float)(NT - 2), my2 = (float)(h - 2);
     const float al2 = a.alpha2;
+    // this lane's x-pass run: row xi, columns [xc0, xc0 + RUN) of the warp's 4 runs (lanes >= 4 R idle)
+    const bool xlane = lane < 4 * R;
+    const int xi = lane % R, xc0 = (4 * warp + lane / R) * RUN;
+    // the r halo columns on each side of R halo rows take the row's edge value (lanes 0 .. R - 1 of
+    // the first and the last warp, one row each), visible to the warp after the __syncwarp
+    auto fill_halo = [&](float2 *rows) {
+        if ((warp == 0 || warp == NWARP - 1) && lane < R) {
+            float2 *row = rows + lane * G::HST;
+            const int c = warp == 0 ? 0 : NT - 1, o = warp == 0 ? -RAD : 1;
+            const float2 v = row[G::HO + c];
+#pragma unroll
+            for (int j = 0; j < RAD; ++j) row[G::HO + c + o + j] = v;
+        }
+        __syncwarp();
+    };
 
-    for (int item = blockIdx.x; item < n_active; item += gridDim.x) {
+    int item = blockIdx.x;
+    uint32_t g = 0;   // steps of this CTA so far: step g uses buffer g & 1, phase parity (g >> 1) & 1
+    if (warp == 0 && item < n_active) {
+        const int p0 = a.active[item];
+        issue_step<RAD, NT, IN_S>(a, p0, 0, sS0, sF0, &bar[0], lane);
+        issue_step<RAD, NT, IN_S>(a, p0, 1, sS0 + R * G::HST, sF0 + G::FR_ * G::FST, &bar[1], lane);
+    }
+    for (; item < n_active; item += gridDim.x) {
         const int pair = a.active[item];
+        const int next_pair = item + (int)gridDim.x < n_active ? a.active[item + gridDim.x] : -1;
         const float *M = a.Mref + (size_t)__ldg(a.ref_idx + pair) * plane;
         const float2 *u0 = a.in + (size_t)pair * plane;   // the level's initial field when !IN_S
         float2 *dst = a.out + (size_t)pair * plane;
-        float2 rxw[R], dxw[R], ucur[R], uprev[R], last_dx = make_float2(0.0f, 0.0f);
+        float2 rxw[R], dxw[R], ucur[R], uprev[RAD], last_dx = make_float2(0.0f, 0.0f);
         float ssd = 0.0f;
-        stage_copies<RAD, NT, IN_S>(a, pair, 0, sS0, sF0);
-        for (int k = 0; k < nsteps; ++k) {
-            float2 *sS = sS0 + (k & 1) * R * G::SST;
-            float *sF = sF0 + (k & 1) * G::FR_ * G::FST;
-            cp_async_wait_all();
-            __syncthreads();   // step k's rows staged; the previous step's DX rows consumed
-            if (k + 1 < nsteps)
-                stage_copies<RAD, NT, IN_S>(a, pair, k + 1, sS0 + ((k + 1) & 1) * R * G::SST,
-                                            sF0 + ((k + 1) & 1) * G::FR_ * G::FST);
-            // ---- x pass of G_f on the step's s rows: RX [R][NT]
+        for (int k = 0; k <= nsteps; ++k) {
+            // ---- outputs of step k - 1: y pass of G_u over the DX window, s = u + G_u * du
+            // (DX rows of the warp's own columns, written by this warp before its __syncwarp).
+            // Interior steps (every row inside, none at an edge) run without the edge handling.
+            if (k > 0) {
+                const int kp = k - 1;
+                auto outputs = [&](auto interior) {
+                    constexpr bool IN = decltype(interior)::value;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const int yu = R * kp + i - RAD, yo = yu - RAD;   // du row entering, output row
+                        if (IN || yu >= 0) {
+                            const float2 v = (IN || yu < h) ? sDX[i * G::XST + t] : last_dx;
+                            if (!IN && yu < h) last_dx = v;
+                            dxw[(i + R - RAD) % R] = v;   // row yu in slot yu mod R
+                            if (!IN && yu == 0) {
+#pragma unroll
+                                for (int j = 0; j < R; ++j) dxw[j] = v;
+                            }
+                        }
+                        if (IN || (yo >= 0 && yo < h)) {
+                            // rows yo - r + j = yu - 2r + j sit in slots (i - 3r + j) mod R
+                            float2 acc = __fmul2_rn(tu[0], dxw[(i + 2 * R - 3 * RAD) % R]);
+#pragma unroll
+                            for (int j = 1; j < R; ++j) acc = ffma2(tu[j], dxw[(i + 2 * R - 3 * RAD + j) % R], acc);
+                            const float2 uo = i >= RAD ? ucur[i - RAD] : uprev[i];
+                            dst[(size_t)yo * NT + t] = __fadd2_rn(uo, acc);
+                        }
+                    }
+                };
+                if (interior_step(kp)) outputs(std::true_type());
+                else outputs(std::false_type());
+#pragma unroll
+                for (int i = 0; i < RAD; ++i) uprev[i] = ucur[R - RAD + i];
+            }
+            if (k == nsteps) break;
+            const int b = g & 1;
+            float2 *sS = sS0 + b * R * G::HST;
+            float *sF = sF0 + b * G::FR_ * G::FST;
+            float2 *sD = sD0 + b * R * G::HST;
+            // step k's rows: every thread waits for the bulk copies (bounded; a wait that gives up
+            // is reported at the barrier below, which every thread reaches)
+            bool ok = hr_tma::mbar_wait(&bar[b], (g >> 1) & 1u);
+            // ---- x pass of G_f on the s rows -> RX (the warp's own columns; the edge warps first
+            // fill the halo columns of the rows with the edge values)
             if (IN_S) {
-                constexpr int NSEG = NT / RUN;
-                for (int it = t; it < R * NSEG; it += NT) {
-                    const int i = it % R, seg = it / R;
-                    run_x<RAD>(sS + i * G::SST + seg * RUN, sX + i * G::XST + seg * RUN, tf);
-                }
-                __syncthreads();
+                fill_halo(sS);
+                if (xlane) run_x_halo<RAD>(sS + xi * G::HST, xc0, sRX + xi * G::XST + xc0, tf);
+                __syncwarp();
             }
-            // ---- per column: y pass of G_f, warp, force, du rows
+            // ---- y pass of G_f: u for rows yu = R k + i - r; the moving image at x - u (every row's
+            // four gathers first); the force of Eq. 1
+            const float yk = (float)(R * k - RAD);
+            auto force_rows = [&](auto interior) {
+                constexpr bool IN = decltype(interior)::value;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int y = R * k + i, yu = y - RAD;   // input row, u row
-                float2 u;
-                if (IN_S) {
-                    const float2 v = sX[i * G::XST + t];
-                    if (y == 0) {
+                for (int i = 0; i < R; ++i) {
+                    const int y = R * k + i, yu = y - RAD;
+                    float2 u;
+                    if (IN_S) {
+                        const float2 v = sRX[i * G::XST + t];
+                        rxw[i] = v;   // row y in slot y mod R = i
+                        if (!IN && y == 0) {
 #pragma unroll
-                        for (int j = 0; j < R; ++j) rxw[j] = v;
+                            for (int j = 0; j < R; ++j) rxw[j] = v;
+                        }
+                        // rows y - 2r + j sit in slots (i - 2r + j) mod R
+                        u = __fmul2_rn(tf[0], rxw[(i + R - 2 * RAD) % R]);
+#pragma unroll
+                        for (int j = 1; j < R; ++j) u = ffma2(tf[j], rxw[(i + R - 2 * RAD + j) % R], u);
                     } else {
-#pragma unroll
-                        for (int j = 0; j < R - 1; ++j) rxw[j] = rxw[j + 1];
-                        rxw[R - 1] = v;
+                        u = (IN || (yu >= 0 && yu < h)) ? u0[(size_t)yu * NT + t] : make_float2(0.0f, 0.0f);
                     }
-                    u = __fmul2_rn(tf[0], rxw[0]);
-#pragma unroll
-                    for (int j = 1; j < R; ++j) u = ffma2(tf[j], rxw[j], u);
-                } else {
-                    u = yu >= 0 && yu < h ? u0[(size_t)yu * NT + t] : make_float2(0.0f, 0.0f);
+                    ucur[i] = u;
                 }
-                ucur[i] = u;
-                if (yu >= 0 && yu < h) {
-                    // test image rows yu - 1 .. yu + 1 are staged rows i .. i + 2
-                    const float *fr_ = sF + i * G::FST + t + 1;
-                    const float fc = fr_[G::FST], fup = fr_[0], fdn = fr_[2 * G::FST];
-                    const float fl = fr_[G::FST - 1], frt = fr_[G::FST + 1];
-                    const float sy = (yu == 0 || yu == h - 1) ? 1.0f : 0.5f;
+                float mA[R], mB[R], mC[R], mD[R], fxv[R], fyv[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int yu = R * k + i - RAD;
+                    // row coordinate as a float (exact integers); rows outside: any valid cell
+                    const float yc = IN ? yk + (float)i : (float)min(max(yu, 0), h - 1);
                     int x0, y0;
-                    float fx, fy;
-                    warp_cell(t, u.x, NT, x0, fx);
-                    warp_cell(yu, u.y, h, y0, fy);
+                    warp_cell_f(tf_, ucur[i].x, mx2, x0, fxv[i]);
+                    warp_cell_f(yc, ucur[i].y, my2, y0, fyv[i]);
                     const float *p = M + y0 * NT + x0;
-                    const float A = __ldg(p), Bv = __ldg(p + 1), C = __ldg(p + NT), D = __ldg(p + NT + 1);
-                    const float omx = fmaf(fx, -1.0f, 1.0f), omy = fmaf(fy, -1.0f, 1.0f);
-                    const float top = fmaf(fx, Bv, omx * A), bot = fmaf(fx, D, omx * C);
-                    const float mw = fmaf(fy, bot, omy * top);
-                    const float gx = sx * fmaf(fl, -1.0f, frt), gy = sy * fmaf(fup, -1.0f, fdn);
-                    const float d = fmaf(fc, -1.0f, mw);
-                    const float den = fmaf(gx, gx, fmaf(gy, gy, (al2 * d) * d));
-                    const float tt = den > 1e-9f ? __fdividef(d, den) : 0.0f;
-                    const float2 du = make_float2(tt * gx, tt * gy);
-                    float2 *drow = sD + i * G::SST;
-                    drow[RAD + t] = du;
-                    if (t == 0) {
-#pragma unroll
-                        for (int j = 0; j < RAD; ++j) drow[j] = du;
-                    }
-                    if (t == NT - 1) {
-#pragma unroll
-                        for (int j = 0; j < RAD; ++j) drow[RAD + NT + j] = du;
-                    }
-                    ssd = fmaf(d, d, ssd);
+                    mA[i] = __ldg(p);
+                    mB[i] = __ldg(p + 1);
+                    mC[i] = __ldg(p + NT);
+                    mD[i] = __ldg(p + NT + 1);
                 }
-            }
-            __syncthreads();   // du rows complete
-            // ---- x pass of G_u on the du rows that exist: DX [R][NT]
-            {
-                constexpr int NSEG = NT / RUN;
-                for (int it = t; it < R * NSEG; it += NT) {
-                    const int i = it % R, seg = it / R, yu = R * k + i - RAD;
-                    if (yu >= 0 && yu < h) run_x<RAD>(sD + i * G::SST + seg * RUN, sX + i * G::XST + seg * RUN, tu);
-                }
-            }
-            __syncthreads();   // DX rows complete
-            // ---- per column: y pass of G_u, s_{k+1} = u + G_u * du, stored
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int y = R * k + i, yu = y - RAD, yo = yu - RAD;   // input, u/du, output rows
-                if (yu >= 0) {
-                    const float2 v = yu < h ? sX[i * G::XST + t] : last_dx;
-                    if (yu < h) last_dx = v;
-                    if (yu == 0) {
-#pragma unroll
-                        for (int j = 0; j < R; ++j) dxw[j] = v;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < R - 1; ++j) dxw[j] = dxw[j + 1];
-                        dxw[R - 1] = v;
+                for (int i = 0; i < R; ++i) {
+                    const int yu = R * k + i - RAD;
+                    if (IN || (yu >= 0 && yu < h)) {
+                        // test image rows yu - 1 .. yu + 1 are staged rows i .. i + 2
+                        const float *fr_ = sF + i * G::FST;
+                        const float fc = fr_[G::FST + t], fup = fr_[t], fdn = fr_[2 * G::FST + t];
+                        const float fl = fr_[G::FST + tl], frt = fr_[G::FST + tr];
+                        const float sy = (!IN && (yu == 0 || yu == h - 1)) ? 1.0f : 0.5f;
+                        const float fx = fxv[i], fy = fyv[i];
+                        const float omx = fmaf(fx, -1.0f, 1.0f), omy = fmaf(fy, -1.0f, 1.0f);
+                        const float top = fmaf(fx, mB[i], omx * mA[i]), bot = fmaf(fx, mD[i], omx * mC[i]);
+                        const float mw = fmaf(fy, bot, omy * top);
+                        const float gx = sx * fmaf(fl, -1.0f, frt), gy = sy * fmaf(fup, -1.0f, fdn);
+                        const float d = fmaf(fc, -1.0f, mw);
+                        const float den = fmaf(gx, gx, fmaf(gy, gy, (al2 * d) * d));
+                        const float tt = den > 1e-9f ? __fdividef(d, den) : 0.0f;
+                        const float2 du = make_float2(tt * gx, tt * gy);
+                        sD[i * G::HST + G::HO + t] = du;
+                        ssd = fmaf(d, d, ssd);
                     }
                 }
-                if (yo >= 0 && yo < h) {
-                    float2 acc = __fmul2_rn(tu[0], dxw[0]);
-#pragma unroll
-                    for (int j = 1; j < R; ++j) acc = ffma2(tu[j], dxw[j], acc);
-                    const float2 uo = i >= RAD ? ucur[i - RAD] : uprev[i - RAD + R];
-                    dst[(size_t)yo * NT + t] = __fadd2_rn(uo, acc);
+            };
+            if (interior_step(k)) force_rows(std::true_type());
+            else force_rows(std::false_type());
+            // du rows complete; step k's s and test rows consumed by every warp
+            if (!__syncthreads_and(ok)) {   // a copy did not arrive: report, let this CTA's copies land, stop
+                if (t == 0) {
+                    atomicExch(a.err, 1);
+                    hr_tma::mbar_wait(&bar[b], (g >> 1) & 1u);
+                    if (k + 1 < nsteps || next_pair >= 0) hr_tma::mbar_wait(&bar[b ^ 1], ((g + 1) >> 1) & 1u);
                 }
+                return;
             }
-#pragma unroll
-            for (int i = 0; i < R; ++i) uprev[i] = ucur[i];
+            if (warp == 0) {   // step k + 2 into the buffer just consumed
+                if (k + 2 < nsteps)
+                    issue_step<RAD, NT, IN_S>(a, pair, k + 2, sS, sF, &bar[b], lane);
+                else if (next_pair >= 0)
+                    issue_step<RAD, NT, IN_S>(a, next_pair, k + 2 - nsteps, sS, sF, &bar[b], lane);
+            }
+            // ---- x pass of G_u on the du rows that exist -> DX (the warp's own columns; the edge
+            // warps first fill the halo columns with the edge values)
+            fill_halo(sD);
+            if (xlane) {
+                const int yu = R * k + xi - RAD;
+                if (yu >= 0 && yu < h) run_x_halo<RAD>(sD + xi * G::HST, xc0, sDX + xi * G::XST + xc0, tu);
+            }
+            __syncwarp();
+            ++g;
         }
         // SSD of the pair (one partial: the level runs with tiles = 1)
         for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
@@ -230,7 +338,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
         __syncthreads();
         if (t == 0) {
             float s = 0.0f;
-            for (int j = 0; j < NT / 32; ++j) s += red[j];
+            for (int j = 0; j < NWARP; ++j) s += red[j];
             a.part[(size_t)pair * a.tiles] = s;
         }
     }
