@@ -41,10 +41,11 @@ struct Geo {
     static_assert(NT % 32 == 0 && NT >= 64 && NT / RUN == 4 * (NT / 32), "four x-pass runs per warp and row, two edge warps");
     static constexpr int HO = 4;                        // halo rows: data column c at index c + HO
     static constexpr int HST = NT + 10;                 // float2 stride of halo rows (odd 16-byte slots)
-    static constexpr int XST = NT + 2;                  // float2 stride of RX / DX rows (odd 16-byte slots)
+    static constexpr int XST = NT + 10;                 // float2 stride of RX / DX rows (the same)
     static constexpr int FR_ = R + 2;                   // test-image rows of a step
     static constexpr int FST = NT + 4;                  // float stride of test-image rows (odd 16-byte slots)
     static_assert((HST / 2) % 2 == 1 && (XST / 2) % 2 == 1 && (FST / 4) % 2 == 1, "odd numbers of 16-byte slots");
+    static_assert((HST / 2) % 8 == 5 && (XST / 2) % 8 == 5, "the x-pass lane map below is conflict-free for 5 mod 8");
     static constexpr size_t S_OFF = 0;                                   // s rows [2][R][HST] float2
     static constexpr size_t F_OFF = S_OFF + (size_t)2 * R * HST * 8;     // test rows [2][FR_][FST] float
     static constexpr size_t D_OFF = F_OFF + (size_t)2 * FR_ * FST * 4;   // du rows [2][R][HST] float2
@@ -161,9 +162,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
     const int tl = max(t - 1, 0), tr = min(t + 1, NT - 1);
     const float tf_ = (float)t, mx2 = (float)(NT - 2), my2 = (float)(h - 2);
     const float al2 = a.alpha2;
-    // this lane's x-pass run: row xi, columns [xc0, xc0 + RUN) of the warp's 4 runs (lanes >= 4 R idle)
-    const bool xlane = lane < 4 * R;
-    const int xi = lane % R, xc0 = (4 * warp + lane / R) * RUN;
+    // this lane's x-pass run: row xi, run xs of the warp's 4 (columns [xc0, xc0 + RUN)).  The 28 runs
+    // of R rows x 4 fill lanes 0..6 of each group of 8 (lane 7 idle), chosen so that the 16-byte
+    // slots (5 xi + 4 xs + j) mod 8 that the 8 lanes of a shared-memory phase touch are distinct
+    // (row strides of 5 mod 8 slots): rows 0-2 x runs {0,1} and {2,3} with row 3 run 0 / 1 in the
+    // first two groups, row 3 run 2 / 3 with rows 4-6 x runs {0,1} and {2,3} in the last two.
+    const int xp = lane >> 3, xq = lane & 7;
+    const bool xlane = xq != 7;
+    const int xi = xp < 2 ? (xq < 6 ? xq >> 1 : 3) : (xq == 0 ? 3 : 4 + ((xq - 1) >> 1));
+    const int xs = xp < 2 ? (xq < 6 ? (xq & 1) + 2 * xp : xp) : (xq == 0 ? xp : ((xq - 1) & 1) + 2 * (xp - 2));
+    const int xc0 = (4 * warp + xs) * RUN;
     // the r halo columns on each side of R halo rows take the row's edge value (lanes 0 .. R - 1 of
     // the first and the last warp, one row each), visible to the warp after the __syncwarp
     auto fill_halo = [&](float2 *rows) {
@@ -198,6 +206,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
             // Interior steps (every row inside, none at an edge) run without the edge handling.
             if (k > 0) {
                 const int kp = k - 1;
+                float2 *dk = dst + (ptrdiff_t)(R * kp - 2 * RAD) * NT + t;   // row yo for i = 0
                 auto outputs = [&](auto interior) {
                     constexpr bool IN = decltype(interior)::value;
 #pragma unroll
@@ -218,7 +227,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
 #pragma unroll
                             for (int j = 1; j < R; ++j) acc = ffma2(tu[j], dxw[(i + 2 * R - 3 * RAD + j) % R], acc);
                             const float2 uo = i >= RAD ? ucur[i - RAD] : uprev[i];
-                            dst[(size_t)yo * NT + t] = __fadd2_rn(uo, acc);
+                            dk[i * NT] = __fadd2_rn(uo, acc);   // row yo
                         }
                     }
                 };
@@ -282,26 +291,60 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
                     mC[i] = __ldg(p + NT);
                     mD[i] = __ldg(p + NT + 1);
                 }
+                // the force of one row (scalar) ...
+                auto force1 = [&](int i, int yu) {
+                    // test image rows yu - 1 .. yu + 1 are staged rows i .. i + 2
+                    const float *fr_ = sF + i * G::FST;
+                    const float fc = fr_[G::FST + t], fup = fr_[t], fdn = fr_[2 * G::FST + t];
+                    const float fl = fr_[G::FST + tl], frt = fr_[G::FST + tr];
+                    const float sy = (!IN && (yu == 0 || yu == h - 1)) ? 1.0f : 0.5f;
+                    const float fx = fxv[i], fy = fyv[i];
+                    const float omx = fmaf(fx, -1.0f, 1.0f), omy = fmaf(fy, -1.0f, 1.0f);
+                    const float top = fmaf(fx, mB[i], omx * mA[i]), bot = fmaf(fx, mD[i], omx * mC[i]);
+                    const float mw = fmaf(fy, bot, omy * top);
+                    const float gx = sx * fmaf(fl, -1.0f, frt), gy = sy * fmaf(fup, -1.0f, fdn);
+                    const float d = fmaf(fc, -1.0f, mw);
+                    const float den = fmaf(gx, gx, fmaf(gy, gy, (al2 * d) * d));
+                    const float tt = den > 1e-9f ? __fdividef(d, den) : 0.0f;
+                    sD[i * G::HST + G::HO + t] = make_float2(tt * gx, tt * gy);
+                    ssd = fmaf(d, d, ssd);
+                };
+                // ... and of rows i, i + 1 of an interior step in packed FP32x2 arithmetic (every
+                // rounding step that of force1: a - b as fma(b, -1, a), products and fmas in order)
+                auto force2 = [&](int i) {
+                    const float *fr_ = sF + i * G::FST;
+                    const float f0 = fr_[t], f1 = fr_[G::FST + t], f2 = fr_[2 * G::FST + t], f3 = fr_[3 * G::FST + t];
+                    const float2 fl = make_float2(fr_[G::FST + tl], fr_[2 * G::FST + tl]);
+                    const float2 frt = make_float2(fr_[G::FST + tr], fr_[2 * G::FST + tr]);
+                    const float2 n1 = make_float2(-1.0f, -1.0f), one = make_float2(1.0f, 1.0f);
+                    const float2 fx = make_float2(fxv[i], fxv[i + 1]), fy = make_float2(fyv[i], fyv[i + 1]);
+                    const float2 omx = __ffma2_rn(fx, n1, one), omy = __ffma2_rn(fy, n1, one);
+                    const float2 top = __ffma2_rn(fx, make_float2(mB[i], mB[i + 1]),
+                                                  __fmul2_rn(omx, make_float2(mA[i], mA[i + 1])));
+                    const float2 bot = __ffma2_rn(fx, make_float2(mD[i], mD[i + 1]),
+                                                  __fmul2_rn(omx, make_float2(mC[i], mC[i + 1])));
+                    const float2 mw = __ffma2_rn(fy, bot, __fmul2_rn(omy, top));
+                    const float2 gx = __fmul2_rn(make_float2(sx, sx), __ffma2_rn(fl, n1, frt));
+                    const float2 gy = __fmul2_rn(make_float2(0.5f, 0.5f), __ffma2_rn(make_float2(f0, f1), n1, make_float2(f2, f3)));
+                    const float2 d = __ffma2_rn(make_float2(f1, f2), n1, mw);
+                    const float2 a2 = make_float2(al2, al2);
+                    const float2 den = __ffma2_rn(gx, gx, __ffma2_rn(gy, gy, __fmul2_rn(__fmul2_rn(a2, d), d)));
+                    const float t0 = den.x > 1e-9f ? __fdividef(d.x, den.x) : 0.0f;
+                    const float t1 = den.y > 1e-9f ? __fdividef(d.y, den.y) : 0.0f;
+                    sD[i * G::HST + G::HO + t] = make_float2(t0 * gx.x, t0 * gy.x);
+                    sD[(i + 1) * G::HST + G::HO + t] = make_float2(t1 * gx.y, t1 * gy.y);
+                    ssd = fmaf(d.x, d.x, ssd);
+                    ssd = fmaf(d.y, d.y, ssd);
+                };
+                if (IN) {
 #pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const int yu = R * k + i - RAD;
-                    if (IN || (yu >= 0 && yu < h)) {
-                        // test image rows yu - 1 .. yu + 1 are staged rows i .. i + 2
-                        const float *fr_ = sF + i * G::FST;
-                        const float fc = fr_[G::FST + t], fup = fr_[t], fdn = fr_[2 * G::FST + t];
-                        const float fl = fr_[G::FST + tl], frt = fr_[G::FST + tr];
-                        const float sy = (!IN && (yu == 0 || yu == h - 1)) ? 1.0f : 0.5f;
-                        const float fx = fxv[i], fy = fyv[i];
-                        const float omx = fmaf(fx, -1.0f, 1.0f), omy = fmaf(fy, -1.0f, 1.0f);
-                        const float top = fmaf(fx, mB[i], omx * mA[i]), bot = fmaf(fx, mD[i], omx * mC[i]);
-                        const float mw = fmaf(fy, bot, omy * top);
-                        const float gx = sx * fmaf(fl, -1.0f, frt), gy = sy * fmaf(fup, -1.0f, fdn);
-                        const float d = fmaf(fc, -1.0f, mw);
-                        const float den = fmaf(gx, gx, fmaf(gy, gy, (al2 * d) * d));
-                        const float tt = den > 1e-9f ? __fdividef(d, den) : 0.0f;
-                        const float2 du = make_float2(tt * gx, tt * gy);
-                        sD[i * G::HST + G::HO + t] = du;
-                        ssd = fmaf(d, d, ssd);
+                    for (int i = 0; i + 1 < R; i += 2) force2(i);
+                    force1(R - 1, R * k - RAD + R - 1);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const int yu = R * k + i - RAD;
+                        if (yu >= 0 && yu < h) force1(i, yu);
                     }
                 }
             };
