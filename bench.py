@@ -172,16 +172,22 @@ def xcf_roofline(ms, B, wl, fp32_peak_tflops, hbm_peak):
             "algorithmic": f"{flops / B / 1e6:.2f} MFLOP and {nbytes / B / 1e3:.0f} KB per pair"}
 
 
-def code_digest(path):
-    """SHA-256 of a C/CUDA source with its // comments, trailing blanks and empty lines removed: a
-    change of the code (not of its comments) changes it.  The demons sources hold no '//' inside
-    string literals."""
+def code_digest(*paths):
+    """SHA-256 of C/CUDA sources (in the order given) with their // comments, trailing blanks and empty
+    lines removed: a change of the code (not of its comments) changes it.  The demons sources hold no
+    '//' inside string literals."""
     lines = []
-    for line in open(path, encoding="utf-8").read().splitlines():
-        code = line.split("//", 1)[0].rstrip()
-        if code:
-            lines.append(code)
+    for path in paths:
+        for line in open(path, encoding="utf-8").read().splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                lines.append(code)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
+def demons_sources():
+    csrc = os.path.join(ROOT, "paper_1907_05993_gb300", "csrc")
+    return os.path.join(csrc, "demons.cu"), os.path.join(csrc, "demons_strip.cuh")
 
 
 def traffic_per_launch(px_per_launch):
@@ -190,8 +196,7 @@ def traffic_per_launch(px_per_launch):
     path = os.path.join(ROOT, "profiles", "demons_iter_traffic.json")
     try:
         d = json.load(open(path))
-        src = os.path.join(ROOT, "paper_1907_05993_gb300", "csrc", "demons.cu")
-        if d.get("demons_cu_code_sha256") != code_digest(src):
+        if d.get("demons_code_sha256") != code_digest(*demons_sources()):
             return None
         return d["dram_bytes_per_pixel_iter"] * px_per_launch
     except Exception:
@@ -401,7 +406,8 @@ def run_ours(args, rank, world, local_rank):
                     "path": f"Pipeline.run_host: pinned host inputs, {E2E_CHUNKS} slices growing 1:2:4:8, copy of "
                             f"slice k+1 overlapping slice k, F/R/status back to pinned host"},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": "demons_iter_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "demons iteration (every launch of every level; shapes in "
+                                                   "demons_tile_shape_per_level)", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s",
