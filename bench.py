@@ -325,6 +325,8 @@ def run_ours(args, rank, world, local_rank):
     def shape_name(v):
         if v == 5:
             return "row sweep/w threads"
+        if v == 6:
+            return "row sweep, one launch per level/w threads"
         return "x".join(map(str, P.TILE_SHAPES[v])) + f"/{P.TILE_THREADS[v]}t"
     tile_choice = [
         {"level": l, "shape": shape_name(P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l)),

@@ -237,16 +237,22 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
  * 5 = the row sweep: one CTA of w threads per pair walks down whole rows of
  * the level with the separable y passes in per-column register windows (no
  * halo rows; levels 64, 128 or 256 pixels wide; other levels fall back to
- * shape 4).  Shapes 1-5 exist for the Gaussian radius 3 (sigma = 1); other
- * radii always use shape 0.  Every shape computes each output pixel with the
- * same operations in the same order, so the field is the same; only the
- * grouping of the per-tile SSD partials changes. */
-#define HREBSD_TILE_VARIANTS 6
+ * shape 4); 6 = the row sweep with every iteration after the first of a
+ * level in one launch, each pair iterating in its CTA until the stop rule
+ * (applied in the CTA, the same rule on the same history) ends it, so a level
+ * costs 4 launches instead of two per iteration (levels with a cap of one
+ * iteration run as shape 5).  Shapes 1-6 exist for the Gaussian radius 3
+ * (sigma = 1); other radii always use shape 0.  Every shape computes each
+ * output pixel with the same operations in the same order, so the field is
+ * the same; only the grouping of the per-tile SSD partials changes (shapes 5
+ * and 6 share theirs: same counts, same field). */
+#define HREBSD_TILE_VARIANTS 7
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small
  * rotation field (min(B, 2048) pairs; 2 warm-up iterations, then the best of
- * 3 timed batches of 4, CUDA events on `stream`) and keep, for later
+ * 3 timed batches of 4, CUDA events on `stream`; shape 6: one warm-up launch,
+ * then the best of 3 launches of 7 iterations) and keep, for later
  * registrations of that level size in this context, the shape with the least
  * time x (1 + 0.01 log2(4096 / tile area)): smaller tiles carry a 1 % handicap
  * per halving of the area, because the synthetic timing showed a tie where

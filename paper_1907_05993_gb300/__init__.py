@@ -297,10 +297,11 @@ def elastic_params(g, R, tilt_rad, stiffness=None, ref_idx=None):
                           _p(ref_idx, t.int32), int(R))
 
 
-TILE_VARIANTS = 6
-TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64), ("w", "rows"))   # 5: the row sweep
-TILE_THREADS = (256, 256, 256, 512, 768, "w")
-TILE_AREAS = (2048, 1024, 1024, 2048, 4096, 65536)   # outputs per work item (the row sweep: a 256 x 256 level)
+TILE_VARIANTS = 7
+# 5: the row sweep; 6: the row sweep with a level's iterations after the first in one launch
+TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64), ("w", "rows"), ("w", "rows"))
+TILE_THREADS = (256, 256, 256, 512, 768, "w", "w")
+TILE_AREAS = (2048, 1024, 1024, 2048, 4096, 65536, 65536)   # outputs per work item (row sweep: a 256 x 256 level)
 
 
 def hrebsd_autotune(ctx, B, H, W, params, stream=None):

@@ -1022,10 +1022,11 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float2 *u0, con
 // (and hence the last bits of the level SSD) are grouped differently.  The
 // extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
 // use shape 0.
-constexpr int kTileVariants = 6;
+constexpr int kTileVariants = 7;
 constexpr int kStripVariant = 5;   // the row sweep (demons_strip.cuh): one CTA per pair, whole rows
-constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 256};
-constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 256};
+constexpr int kLoopVariant = 6;    // the row sweep with every iteration k >= 1 of a level in one launch
+constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 256, 256};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 256, 256};
 constexpr int kMinTX = 32, kMinTY = 16;   // smallest tile extents (size the per-tile SSD partials)
 bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }
 constexpr bool min_extents_ok()
@@ -1041,13 +1042,13 @@ static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
 // windows are 2r + 1 = 7 rows, the rows of one step).
 bool strip_ok(int rad, int w) { return rad == 3 && (w == 64 || w == 128 || w == 256); }
 
-template <int NT, bool IN_S>
-int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream_t st)
+template <int NT, bool IN_S, bool LOOP>
+int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c, int max_items, cudaStream_t st)
 {
     using G = strip::Geo<3, NT>;
     static int configured_dev = -1;
     static int occ = 0;
-    auto k = strip::demons_strip_kernel<3, NT, IN_S>;
+    auto k = strip::demons_strip_kernel<3, NT, IN_S, LOOP>;
     if (configured_dev != ctx->device) {
         HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES));
         HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, G::BYTES));
@@ -1058,19 +1059,34 @@ int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, int max_items, cudaStream
     if (grid > max_items) grid = max_items;
     if (grid < 1) grid = 1;
     hr_prof_begin(ctx, st);
-    k<<<grid, NT, G::BYTES, st>>>(a);
+    k<<<grid, NT, G::BYTES, st>>>(a, c);
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
 }
 
-// a.tiles must be 1 (one SSD partial per pair); a.in is s_k, or u_0 when !in_s.
+// One iteration over the active pairs.  a.tiles must be 1 (one SSD partial per pair); a.in is s_k,
+// or u_0 when !in_s.
 int launch_strip(hrebsd_ctx *ctx, bool in_s, const IterArgs &a, int max_items, cudaStream_t st)
 {
+    const strip::LoopArgs c{};
     switch (a.w) {
-    case 64: return in_s ? launch_strip_t<64, true>(ctx, a, max_items, st) : launch_strip_t<64, false>(ctx, a, max_items, st);
-    case 128: return in_s ? launch_strip_t<128, true>(ctx, a, max_items, st) : launch_strip_t<128, false>(ctx, a, max_items, st);
-    case 256: return in_s ? launch_strip_t<256, true>(ctx, a, max_items, st) : launch_strip_t<256, false>(ctx, a, max_items, st);
+    case 64: return in_s ? launch_strip_t<64, true, false>(ctx, a, c, max_items, st) : launch_strip_t<64, false, false>(ctx, a, c, max_items, st);
+    case 128: return in_s ? launch_strip_t<128, true, false>(ctx, a, c, max_items, st) : launch_strip_t<128, false, false>(ctx, a, c, max_items, st);
+    case 256: return in_s ? launch_strip_t<256, true, false>(ctx, a, c, max_items, st) : launch_strip_t<256, false, false>(ctx, a, c, max_items, st);
+    default: return HREBSD_EINVAL;
+    }
+}
+
+// Iterations 1 .. cap - 1 of a level in one launch for the pairs of a.active (the survivors of
+// iteration 0), each ended by the stop rule in its CTA; a.in / a.out unused (s_k alternates between
+// c.s0 and c.s1 as in the per-iteration launches).
+int launch_strip_loop(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c, int max_items, cudaStream_t st)
+{
+    switch (a.w) {
+    case 64: return launch_strip_t<64, true, true>(ctx, a, c, max_items, st);
+    case 128: return launch_strip_t<128, true, true>(ctx, a, c, max_items, st);
+    case 256: return launch_strip_t<256, true, true>(ctx, a, c, max_items, st);
     default: return HREBSD_EINVAL;
     }
 }
@@ -1346,21 +1362,25 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         const int h = H >> l, w = W >> l;
         const int cap = p->max_iters[l];
         int var = hr_tuned_variant(ctx, rad, h, w);
-        const bool use_strip = var == kStripVariant && strip_ok(rad, w) && !ctx->no_tma;
-        if (var == kStripVariant && !use_strip) var = 4;   // the row sweep does not cover this level: 64x64 tiles
+        const bool sweep_v = var == kStripVariant || var == kLoopVariant;
+        const bool use_strip = sweep_v && strip_ok(rad, w) && !ctx->no_tma;
+        if (sweep_v && !use_strip) var = 4;   // the row sweep does not cover this level: 64x64 tiles
+        // the whole level after iteration 0 in one launch (needs the stop rule's history: cap > 1)
+        const bool use_loop = use_strip && var == kLoopVariant && cap > 1;
         CUtensorMap tmS[3], tmF;
         const bool use_tma = !use_strip && rad > 0 && !ctx->no_tma && cap > 1 &&
                              encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, (const float2 *)u0, tl[l],
                                          B, h, w, tmS, &tmF);
-        // The launches of one level: list reset, cap x (iteration, control),
-        // finalize, prolongation.  Replayed from a cached CUDA graph when possible.
+        // The launches of one level: list reset, cap x (iteration, control) -- or, in the loop
+        // form, iteration 0 and its control, then one launch for the rest --, finalize,
+        // prolongation.  Replayed from a cached CUDA graph when possible.
         auto emit = [&](cudaStream_t st) -> int {
             int e2;
             hr_prof_begin(ctx, st);
             iota_kernel<<<(B + 255) / 256, 256, 0, st>>>(list0, B, cnt);
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
             HR_LAUNCHED(ctx);
-            for (int k = 0; k < cap; ++k) {
+            for (int k = 0; k < (use_loop ? 1 : cap); ++k) {
                 const bool tma_k = !use_strip && use_tma && (k > 0 || rad == 3);
                 const int tx = tma_k ? kVarTX[var] : TX, ty = tma_k ? kVarTY[var] : TY;
                 const int tiles_x = use_strip ? 1 : (w + tx - 1) / tx;
@@ -1413,6 +1433,40 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 hr_prof_end(ctx, PROF_CTRL, st);
                 HR_LAUNCHED(ctx);
             }
+            if (use_loop) {   // iterations 1 .. cap - 1 of the survivors of iteration 0 (list1)
+                IterArgs a;
+                a.Ftest = tl[l];
+                a.Mref = rl[l];
+                a.ref_idx = ref_idx;
+                a.in = nullptr;
+                a.out = nullptr;
+                a.part = (float *)part;
+                a.active = list1;
+                a.n_active = cnt + 1;
+                a.n_next_reset = nullptr;
+                a.h = h;
+                a.w = w;
+                a.tiles_x = 1;
+                a.tiles = 1;
+                a.in_is_s = 1;
+                a.alpha2 = p->alpha * p->alpha;
+                a.taps = taps;
+                a.px_count = hr_prof_pixiters(ctx);
+                a.err = ctx->d_err;
+                strip::LoopArgs c;
+                c.s0 = (float2 *)s0;
+                c.s1 = (float2 *)s1;
+                c.hist = (double *)hist;
+                c.iters = iters;
+                c.status = status;
+                c.hist_stride = cap_max + 1;
+                c.cap = cap;
+                c.window = p->stop_window;
+                c.level = l;
+                c.levels = L;
+                c.tol = p->stop_tol;
+                if ((e2 = launch_strip_loop(ctx, a, c, B, st))) return e2;
+            }
             const int tiles_x = (w + TX - 1) / TX, tiles = tiles_x * ((h + TY - 1) / TY);
             float *dst = l == 0 ? field : (float *)uout;
             if ((e2 = dispatch_finalize(ctx, rad, l == 0, (const float2 *)u0, (const float2 *)s0, (const float2 *)s1,
@@ -1440,7 +1494,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                             ctx->d_err};
         static_assert(sizeof(kp) / sizeof(kp[0]) <= sizeof(key.p) / sizeof(key.p[0]), "graph key");
         for (size_t i = 0; i < sizeof(kp) / sizeof(kp[0]); ++i) key.p[i] = kp[i];
-        const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window, (int)use_strip};
+        const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window, (int)use_strip,
+                          (int)use_loop};
         for (size_t i = 0; i < sizeof(ki) / sizeof(ki[0]); ++i) key.i[i] = ki[i];
         key.f[0] = p->alpha;
         key.f[1] = p->stop_tol;
@@ -1498,6 +1553,7 @@ __global__ void tune_fill_kernel(float *img, int n_img, float2 *s0, float2 *s1, 
 }
 
 enum { WS_TUNE_IMG = 9, WS_TUNE_S0, WS_TUNE_S1, WS_TUNE_PART, WS_TUNE_IDX };
+constexpr int WS_TUNE_LOOP = 21;   // the loop form's history, counts and status
 
 }  // namespace
 
@@ -1547,6 +1603,11 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
     if ((e = hr_ws(ctx, WS_TUNE_S1, Bt * px0 * 8, &s1))) return e;
     if ((e = hr_ws(ctx, WS_TUNE_PART, (size_t)Bt * tiles0 * 4, &part))) return e;
     if ((e = hr_ws(ctx, WS_TUNE_IDX, ((size_t)2 * Bt + 4) * 4, &idx))) return e;
+    constexpr int kLoopCap = 8;   // the loop form runs iterations 1 .. kLoopCap - 1 per timed launch
+    void *lws;
+    if ((e = hr_ws(ctx, WS_TUNE_LOOP, (size_t)Bt * (kLoopCap + 1) * 8 + (size_t)Bt * 8, &lws))) return e;
+    double *lhist = (double *)lws;
+    int32_t *liters = (int32_t *)(lhist + (size_t)Bt * (kLoopCap + 1)), *lstatus = liters + Bt;
     int32_t *ridx = (int32_t *)idx, *list = ridx + Bt, *cnt = list + Bt;
     cudaStream_t st = hr_stream(stream);
     const int prof = ctx->prof_on;
@@ -1570,7 +1631,8 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
             int best_v = 0;
             for (int v = 0; v < kTileVariants; ++v) {
                 if (!variant_ok(rad, v) || ctx->no_tma) continue;
-                const bool sv = v == kStripVariant;
+                const bool lv = v == kLoopVariant;
+                const bool sv = v == kStripVariant || lv;
                 if (sv && !strip_ok(rad, w)) continue;
                 CUtensorMap tmS[3], tmF;
                 if (!sv && !encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
@@ -1594,18 +1656,45 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 a.in_is_s = 1;
                 a.alpha2 = p->alpha * p->alpha;
                 a.taps = taps;
-                // 2 warm-up iterations, then the best of 3 timed batches of 4
+                // 2 warm-up iterations, then the best of 3 timed batches of 4 (the loop form: one
+                // warm-up launch, then the best of 3 launches of kLoopCap - 1 iterations each)
                 constexpr int kWarm = 2, kBatch = 4, kRounds = 3;
                 float ms = 0.0f;
                 int k = 0;
-                for (; k < kWarm; ++k) {
+                if (lv) {
+                    strip::LoopArgs c;
+                    c.s0 = (float2 *)s0;
+                    c.s1 = (float2 *)s1;
+                    c.hist = lhist;
+                    c.iters = liters;
+                    c.status = lstatus;
+                    c.hist_stride = kLoopCap + 1;
+                    c.cap = kLoopCap;
+                    c.window = 0;   // no stop rule: every pair runs all iterations
+                    c.level = 0;
+                    c.levels = 1;
+                    c.tol = 0.0f;
+                    HR_CHECK(cudaMemsetAsync(lstatus, 0, (size_t)Bt * 4, st));
+                    for (int rep = 0; rep <= kRounds; ++rep) {
+                        HR_CHECK(cudaEventRecord(ev[0], st));
+                        int e2 = launch_strip_loop(ctx, a, c, Bt, st);
+                        if (e2) return e2;
+                        HR_CHECK(cudaEventRecord(ev[1], st));
+                        HR_CHECK(cudaEventSynchronize(ev[1]));
+                        float t = 0.0f;
+                        HR_CHECK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+                        t /= (float)(kLoopCap - 1);
+                        if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+                    }
+                }
+                for (; !lv && k < kWarm; ++k) {
                     a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                     a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
                     int e2 = sv ? launch_strip(ctx, true, a, Bt, st)
                                 : dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                     if (e2) return e2;
                 }
-                for (int rep = 0; rep < kRounds; ++rep) {
+                for (int rep = 0; !lv && rep < kRounds; ++rep) {
                     HR_CHECK(cudaEventRecord(ev[0], st));
                     for (int j = 0; j < kBatch; ++j, ++k) {
                         a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;

@@ -58,32 +58,41 @@ struct Geo {
                   "16-byte aligned regions");
 };
 
-// The bulk copies of step k of a pair into one buffer: s rows clamp(R k + i) (i < R) and test-image
-// rows clamp(R k - r - 1 + i) (i < R + 2), whole rows.  Called by every lane of one warp: lane 0
-// announces the bytes, then lanes 0 .. R - 1 copy the s rows and lanes R .. 2R + 1 the test rows.
-template <int RAD, int NT, bool IN_S>
-__device__ __forceinline__ void issue_step(const IterArgs &a, int pair, int k, float2 *sS, float *sF, uint64_t *bar,
-                                           int lane)
+// The bulk copies of step k of a pair into one buffer: s rows clamp(R k + i) (i < R) of the pair's
+// plane sp (when copy_s) and test-image rows clamp(R k - r - 1 + i) (i < R + 2) of its plane fp, whole
+// rows.  Called by every lane of one warp: lane 0 announces the bytes, then lanes 0 .. R - 1 copy the
+// s rows and lanes R .. 2R + 1 the test rows.
+template <int RAD, int NT>
+__device__ __forceinline__ void issue_step(bool copy_s, const float2 *sp, const float *fp, int h, int k, float2 *sS,
+                                           float *sF, uint64_t *bar, int lane)
 {
     using G = Geo<RAD, NT>;
-    const int h = a.h;
-    const size_t plane = (size_t)h * NT;
-    if (lane == 0) hr_tma::mbar_arrive_expect_tx(bar, (IN_S ? G::S_BYTES : 0u) + G::F_BYTES);
+    if (lane == 0) hr_tma::mbar_arrive_expect_tx(bar, (copy_s ? G::S_BYTES : 0u) + G::F_BYTES);
     __syncwarp();
     if (lane < R) {
-        if (IN_S) {
+        if (copy_s) {
             hr_tma::fence_proxy_async();   // the buffer's previous contents were read by the generic proxy
-            hr_tma::load_bulk(sS + lane * G::HST + G::HO, a.in + (size_t)pair * plane + (size_t)min(R * k + lane, h - 1) * NT,
-                              NT * 8, bar);
+            hr_tma::load_bulk(sS + lane * G::HST + G::HO, sp + (size_t)min(R * k + lane, h - 1) * NT, NT * 8, bar);
         }
     } else if (lane < R + G::FR_) {
         const int i = lane - R;
         hr_tma::fence_proxy_async();
-        hr_tma::load_bulk(sF + i * G::FST,
-                          a.Ftest + (size_t)pair * plane + (size_t)min(max(R * k - RAD - 1 + i, 0), h - 1) * NT,
-                          NT * 4, bar);
+        hr_tma::load_bulk(sF + i * G::FST, fp + (size_t)min(max(R * k - RAD - 1 + i, 0), h - 1) * NT, NT * 4, bar);
     }
 }
+
+// The whole level in one launch (the row sweep's LOOP form): every active pair iterates in its CTA
+// until the stop rule of the control kernel (same rule, same FP64 history, one SSD partial per pair)
+// ends it, so the level needs no launch per iteration.  Iterations k >= 1; iteration 0 (which reads
+// u_0) runs as a plain launch first.
+struct LoopArgs {
+    float2 *s0, *s1;        // s_k for even / odd k
+    double *hist;           // [B][hist_stride]
+    int32_t *iters;         // [B][levels]
+    int32_t *status;        // [B]
+    int hist_stride, cap, window, level, levels;
+    float tol;
+};
 
 // x pass of the run of RUN outputs starting at column c0 of a row with halo (data column c at
 // index c + HO = c + r + 1): an aligned window of RUN + 2r + 2 elements from column c0 - r - 1,
@@ -112,9 +121,10 @@ __device__ __forceinline__ void run_x_halo(const float2 *row, int c0, float2 *ou
     for (int o = 0; o < RUN; o += 2) out4[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
 }
 
-template <int RAD, int NT, bool IN_S>
-__global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
+template <int RAD, int NT, bool IN_S, bool LOOP>
+__global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, LoopArgs c)
 {
+    static_assert(!LOOP || IN_S, "the loop form runs the iterations k >= 1, which read s_k");
     using G = Geo<RAD, NT>;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *sS0 = reinterpret_cast<float2 *>(smraw + G::S_OFF);
@@ -124,6 +134,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
     float2 *sDX = reinterpret_cast<float2 *>(smraw + G::Y_OFF);
     __shared__ float red[NT / 32];
     __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_next;   // LOOP: the pair's next iteration, or -1 once the stop rule ended it
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NWARP = NT / 32;
@@ -141,7 +152,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
         tu[k] = tuh[k <= RAD ? k : 2 * RAD - k];
     }
     const int n_active = *a.n_active;
-    if (blockIdx.x == 0 && t == 0) {
+    if (!LOOP && blockIdx.x == 0 && t == 0) {
         *a.n_next_reset = 0;
         if (a.px_count) atomicAdd(a.px_count, (unsigned long long)n_active * a.h * a.w);
     }
@@ -185,19 +196,33 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
         __syncwarp();
     };
 
+    // the planes that iteration kk of a pair reads (s_kk, or u_0 when !IN_S) and writes (s_kk+1)
+    auto src_of = [&](int pair, int kk) -> const float2 * {
+        return (LOOP ? ((kk & 1) ? c.s1 : c.s0) : a.in) + (size_t)pair * plane;
+    };
+    auto dst_of = [&](int pair, int kk) -> float2 * {
+        return (LOOP ? (((kk + 1) & 1) ? c.s1 : c.s0) : a.out) + (size_t)pair * plane;
+    };
+    auto fsrc_of = [&](int pair) { return a.Ftest + (size_t)pair * plane; };
+    constexpr int K_FIRST = LOOP ? 1 : 0;   // the iteration of an item's first sweep (LOOP: after k = 0)
+
     int item = blockIdx.x;
     uint32_t g = 0;   // steps of this CTA so far: step g uses buffer g & 1, phase parity (g >> 1) & 1
     if (warp == 0 && item < n_active) {
         const int p0 = a.active[item];
-        issue_step<RAD, NT, IN_S>(a, p0, 0, sS0, sF0, &bar[0], lane);
-        issue_step<RAD, NT, IN_S>(a, p0, 1, sS0 + R * G::HST, sF0 + G::FR_ * G::FST, &bar[1], lane);
+        issue_step<RAD, NT>(IN_S, src_of(p0, K_FIRST), fsrc_of(p0), h, 0, sS0, sF0, &bar[0], lane);
+        issue_step<RAD, NT>(IN_S, src_of(p0, K_FIRST), fsrc_of(p0), h, 1, sS0 + R * G::HST, sF0 + G::FR_ * G::FST,
+                            &bar[1], lane);
     }
     for (; item < n_active; item += gridDim.x) {
         const int pair = a.active[item];
         const int next_pair = item + (int)gridDim.x < n_active ? a.active[item + gridDim.x] : -1;
         const float *M = a.Mref + (size_t)__ldg(a.ref_idx + pair) * plane;
         const float2 *u0 = a.in + (size_t)pair * plane;   // the level's initial field when !IN_S
-        float2 *dst = a.out + (size_t)pair * plane;
+        const float *fp = fsrc_of(pair);
+      for (int kit = K_FIRST;; ++kit) {   // LOOP: the pair's iterations; otherwise the one sweep
+        const float2 *sp = src_of(pair, kit);
+        float2 *dst = dst_of(pair, kit);
         float2 rxw[R], dxw[R], ucur[R], uprev[RAD], last_dx = make_float2(0.0f, 0.0f);
         float ssd = 0.0f;
         for (int k = 0; k <= nsteps; ++k) {
@@ -236,7 +261,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
 #pragma unroll
                 for (int i = 0; i < RAD; ++i) uprev[i] = ucur[R - RAD + i];
             }
-            if (k == nsteps) break;
+            if (k == nsteps) {
+                // LOOP: the next iteration's bulk copies read these rows of s_{k+1} (async proxy)
+                if (LOOP) asm volatile("fence.proxy.async.global;" ::: "memory");
+                break;
+            }
             const int b = g & 1;
             float2 *sS = sS0 + b * R * G::HST;
             float *sF = sF0 + b * G::FR_ * G::FST;
@@ -355,15 +384,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
                 if (t == 0) {
                     atomicExch(a.err, 1);
                     hr_tma::mbar_wait(&bar[b], (g >> 1) & 1u);
-                    if (k + 1 < nsteps || next_pair >= 0) hr_tma::mbar_wait(&bar[b ^ 1], ((g + 1) >> 1) & 1u);
+                    if (k + 1 < nsteps || (!LOOP && next_pair >= 0))
+                        hr_tma::mbar_wait(&bar[b ^ 1], ((g + 1) >> 1) & 1u);
                 }
                 return;
             }
             if (warp == 0) {   // step k + 2 into the buffer just consumed
                 if (k + 2 < nsteps)
-                    issue_step<RAD, NT, IN_S>(a, pair, k + 2, sS, sF, &bar[b], lane);
-                else if (next_pair >= 0)
-                    issue_step<RAD, NT, IN_S>(a, next_pair, k + 2 - nsteps, sS, sF, &bar[b], lane);
+                    issue_step<RAD, NT>(IN_S, sp, fp, h, k + 2, sS, sF, &bar[b], lane);
+                else if (!LOOP && next_pair >= 0)
+                    issue_step<RAD, NT>(IN_S, src_of(next_pair, K_FIRST), fsrc_of(next_pair), h, k + 2 - nsteps, sS,
+                                        sF, &bar[b], lane);
             }
             // ---- x pass of G_u on the du rows that exist -> DX (the warp's own columns; the edge
             // warps first fill the halo columns with the edge values)
@@ -379,11 +410,55 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a)
         for (int o = 16; o > 0; o >>= 1) ssd += __shfl_xor_sync(0xffffffffu, ssd, o);
         if (lane == 0) red[warp] = ssd;
         __syncthreads();
-        if (t == 0) {
+        if (!LOOP) {
+            if (t == 0) {
+                float s = 0.0f;
+                for (int j = 0; j < NWARP; ++j) s += red[j];
+                a.part[(size_t)pair * a.tiles] = s;
+            }
+            break;
+        }
+        if (t == 0) {   // the control kernel's stop rule after iteration kit, on the same FP64 history
             float s = 0.0f;
             for (int j = 0; j < NWARP; ++j) s += red[j];
-            a.part[(size_t)pair * a.tiles] = s;
+            const double E = 0.0 + (double)s;
+            double *hh = c.hist + (size_t)pair * c.hist_stride;
+            hh[kit] = E;
+            int32_t *itp = c.iters + (size_t)pair * c.levels + c.level;
+            int nk = -1;
+            if (!isfinite(E)) {
+                *itp = kit;
+                c.status[pair] |= HREBSD_PAIR_NONFINITE;
+            } else if (c.window > 0 && kit >= c.window && (hh[kit - c.window] - E) < (double)c.tol * hh[kit - c.window]) {
+                *itp = kit;
+            } else if (kit + 1 >= c.cap) {
+                *itp = c.cap;
+                c.status[pair] |= HREBSD_PAIR_CAPPED;
+            } else {
+                nk = kit + 1;
+            }
+            if (a.px_count) atomicAdd(a.px_count, (unsigned long long)h * NT);
+            s_next = nk;
         }
+        __syncthreads();
+        const int nk = s_next;
+        if (nk < 0) {   // the pair is done: the next pair's first two steps
+            if (warp == 0 && next_pair >= 0) {
+                issue_step<RAD, NT>(true, src_of(next_pair, K_FIRST), fsrc_of(next_pair), h, 0, sS0 + (g & 1) * R * G::HST,
+                                    sF0 + (g & 1) * G::FR_ * G::FST, &bar[g & 1], lane);
+                issue_step<RAD, NT>(true, src_of(next_pair, K_FIRST), fsrc_of(next_pair), h, 1,
+                                    sS0 + ((g + 1) & 1) * R * G::HST, sF0 + ((g + 1) & 1) * G::FR_ * G::FST,
+                                    &bar[(g + 1) & 1], lane);
+            }
+            break;
+        }
+        if (warp == 0) {   // the pair's next iteration: its first two steps
+            issue_step<RAD, NT>(true, src_of(pair, nk), fp, h, 0, sS0 + (g & 1) * R * G::HST,
+                                sF0 + (g & 1) * G::FR_ * G::FST, &bar[g & 1], lane);
+            issue_step<RAD, NT>(true, src_of(pair, nk), fp, h, 1, sS0 + ((g + 1) & 1) * R * G::HST,
+                                sF0 + ((g + 1) & 1) * G::FR_ * G::FST, &bar[(g + 1) & 1], lane);
+        }
+      }
     }
 }
 

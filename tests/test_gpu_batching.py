@@ -89,9 +89,9 @@ def test_autotune_records_the_fastest_shape(torch, lib):
     params = lib.demons_params(4, [100] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
     ms = lib.hrebsd_autotune(ctx, 64, 256, 256, params)
     assert ms.shape == (4, lib.TILE_VARIANTS)
-    # the row sweep (shape 5) covers levels 64, 128 and 256 pixels wide, not 32
+    # the row sweep (shapes 5 and 6) covers levels 64, 128 and 256 pixels wide, not 32
     assert np.isfinite(ms[:, :5]).all() and (ms[:, :5] > 0).all(), ms
-    assert np.isfinite(ms[:3, 5]).all() and np.isnan(ms[3, 5]), ms
+    assert np.isfinite(ms[:3, 5:]).all() and np.isnan(ms[3, 5:]).all(), ms
     area = np.array(lib.TILE_AREAS, dtype=np.float64)
     score = ms * (1.0 + 0.01 * np.maximum(0.0, np.log2(4096.0 / area)))   # the documented handicap of small tiles
     for l in range(4):
@@ -102,6 +102,25 @@ def test_autotune_records_the_fastest_shape(torch, lib):
     with pytest.raises(lib.HrebsdError):
         lib.hrebsd_autotune(ctx, 8, 60, 64, lib.demons_params(4, [5] * 4))   # coarsest level 7 x 8
     lib.hrebsd_destroy(ctx)
+
+
+def test_level_in_one_launch_matches_row_sweep_with_stop_rule(torch, lib, pairs):
+    """Shape 6 runs a level's iterations after the first in one launch and applies the stop rule in
+    each pair's CTA; with the same SSD partials as shape 5 (one per pair) it must stop every pair at
+    the same iteration and give the same field, bit for bit, also with a cap that ends some pairs."""
+    for caps in ([100] * 4, [9, 30, 100, 100]):
+        params = lib.demons_params(4, caps, 1.0, 1.0, 1.0, 1e-4, 5)
+        out = []
+        for v in (5, 6):
+            ctx = lib.hrebsd_create(0)
+            for l in range(4):
+                lib.hrebsd_set_tile_variant(ctx, 256 >> l, 256 >> l, v)
+            out.append(_register(torch, lib, ctx, pairs, params))
+            lib.hrebsd_destroy(ctx)
+        (f5, it5, st5), (f6, it6, st6) = out
+        assert np.array_equal(it5, it6) and np.array_equal(st5, st6), (it5, it6, st5, st6)
+        assert np.array_equal(f5, f6)
+        assert it5.max() > 1
 
 
 def test_graph_replay_matches_direct_launches(torch, lib, pairs):
