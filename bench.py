@@ -327,6 +327,8 @@ def run_ours(args, rank, world, local_rank):
             return "row sweep/w threads"
         if v == 6:
             return "row sweep, one launch per level/w threads"
+        if v == 7:
+            return "level in shared memory/512t"
         return "x".join(map(str, P.TILE_SHAPES[v])) + f"/{P.TILE_THREADS[v]}t"
     tile_choice = [
         {"level": l, "shape": shape_name(P.hrebsd_get_tile_variant(pipe.ctx, wl["H"] >> l, wl["W"] >> l)),
@@ -389,6 +391,13 @@ def run_ours(args, rank, world, local_rank):
     if pool is not None:
         pool.close()
         pool.join()
+    # latency of one pair through the whole chain (the single-pair workload), rank 0 of a 1-GPU run
+    single = None
+    if world == 1 and not args.no_single:
+        sp = single_pair_latency(local_rank)
+        single = {"workload": "1 pair 128x128, 2 deg, 3 levels x 50 iterations, 21 ROIs 32x32",
+                  "ms_per_pair_graphs": sp[1][0], "ms_per_pair_direct": sp[0][0],
+                  "kernel_launches_per_pair": sp[1][1]}
 
     if rank == 0:
         it = prof["demons_iter"]
@@ -428,6 +437,8 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if single is not None:
+            line["single_pair_latency"] = single
         if lvp is not None:
             line["learned_vs_plain"] = lvp
         print(json.dumps(line), flush=True)
@@ -674,10 +685,9 @@ def run_compare(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ single pair (latency)
-def run_single(args, rank, world, local_rank):
-    """The single-pair workload (128x128, 3 levels x 50 iterations, 21 ROIs 32x32): latency of one
-    pair through the whole chain, with the per-level CUDA graphs and with direct launches."""
-    import numpy as np
+def single_pair_latency(local_rank, warmup=3, reps=20):
+    """Latency of one pair through the whole chain (128x128, 3 levels x 50 iterations, 21 ROIs 32x32),
+    with the per-level CUDA graphs and with direct launches: {graphs: (ms, launches per pair)}."""
     import torch
     import paper_1907_05993_gb300 as P
     from paper_1907_05993_gb300.pipeline import Pipeline, PipelineConfig
@@ -692,10 +702,9 @@ def run_single(args, rank, world, local_rank):
         pipe = Pipeline(PipelineConfig(128, 128, roi, 32, 3, (50, 50, 50)))
         P.hrebsd_set_option(pipe.ctx, P.OPT_GRAPHS, graphs)
         out = {}
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(3, warmup)):
             pipe.run(refs, tests, ridx, out=out)
         torch.cuda.synchronize()
-        reps = max(20, args.steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = P.hrebsd_launch_count(pipe.ctx)
         e0.record()
@@ -705,8 +714,16 @@ def run_single(args, rank, world, local_rank):
         torch.cuda.synchronize()
         res[graphs] = (e0.elapsed_time(e1) / reps, (P.hrebsd_launch_count(pipe.ctx) - l0) / reps)
         pipe.close()
+    return res
+
+
+def run_single(args, rank, world, local_rank):
+    """The single-pair workload (128x128, 3 levels x 50 iterations, 21 ROIs 32x32): latency of one
+    pair through the whole chain, with the per-level CUDA graphs and with direct launches."""
+    reps = max(20, args.steps)
+    res = single_pair_latency(local_rank, args.warmup, reps)
     line = {"metric": "single-pair latency (demons+XCF)", "workload": "single", "value": res[1][0], "unit": "ms/pair",
-            "higher_is_better": False, "n_gpus": 1, "steps": max(20, args.steps), "warmup": max(3, args.warmup),
+            "higher_is_better": False, "n_gpus": 1, "steps": reps, "warmup": max(3, args.warmup),
             "data": "synthetic (seeded kinematic Kikuchi generator)", "dtype": "f32",
             "config": {"workload": "1 pair 128x128, 2 deg, 3 levels x 50 iterations, 21 ROIs 32x32"},
             "ms_per_pair_graphs": res[1][0], "ms_per_pair_direct": res[0][0], "kernel_launches_per_pair": res[1][1]}
@@ -825,6 +842,7 @@ def main():
     ap.add_argument("--learned-start", type=int, default=64, choices=(64, 128))
     ap.add_argument("--oracle-pairs", type=int, default=500)
     ap.add_argument("--no-learned", action="store_true", help="default run: skip the learned-vs-plain comparison")
+    ap.add_argument("--no-single", action="store_true", help="default run: skip the single-pair latency")
     ap.add_argument("--lvp-train-pairs", type=int, default=20_000)
     ap.add_argument("--lvp-epochs", type=int, default=20)
     ap.add_argument("--learned-caps", type=int, nargs=4, default=(25, 25, 10, 0))

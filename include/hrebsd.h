@@ -240,19 +240,29 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
  * shape 4); 6 = the row sweep with every iteration after the first of a
  * level in one launch, each pair iterating in its CTA until the stop rule
  * (applied in the CTA, the same rule on the same history) ends it, so a level
- * costs 4 launches instead of two per iteration (levels with a cap of one
- * iteration run as shape 5).  Shapes 1-6 exist for the Gaussian radius 3
+ * costs 5 launches instead of two per iteration (levels with a cap of one
+ * iteration run as shape 5); shape 5 itself takes this form when the batch has
+ * no more pairs than the level has resident CTAs (one pair per CTA: nobody
+ * waits), and per-iteration launches otherwise (they re-balance the uneven
+ * iteration counts of the pairs after every iteration).  A level without a
+ * set or tuned shape runs shape 5 where it applies and shape 0 elsewhere.
+ * 7 = the whole level in shared memory (levels of at most 64 x 64 pixels):
+ * one CTA of 512 threads per pair holds the field, iterates, applies the stop
+ * rule and writes the level's final field, one launch per level (other
+ * levels run shape 5).  Shapes 1-6 exist for the Gaussian radius 3
  * (sigma = 1); other radii always use shape 0.  Every shape computes each
  * output pixel with the same operations in the same order, so the field is
  * the same; only the grouping of the per-tile SSD partials changes (shapes 5
  * and 6 share theirs: same counts, same field). */
-#define HREBSD_TILE_VARIANTS 7
+#define HREBSD_TILE_VARIANTS 8
 
 /* Autotuner: for each pyramid level of an H x W registration with `params`,
  * time every tile shape on synthetic striped patterns displaced by a small
  * rotation field (min(B, 2048) pairs; 2 warm-up iterations, then the best of
- * 3 timed batches of 4, CUDA events on `stream`; shape 6: one warm-up launch,
- * then the best of 3 launches of 7 iterations) and keep, for later
+ * 3 timed batches of 4, CUDA events on `stream`; shapes 6 and 7: one warm-up
+ * launch, then the best of 3 launches of 7 (shape 6) or 8 (shape 7)
+ * iterations; shape 6 is reported but never chosen,
+ * since the synthetic pairs all run the same number of iterations) and keep, for later
  * registrations of that level size in this context, the shape with the least
  * time x (1 + 0.01 log2(4096 / tile area)): smaller tiles carry a 1 % handicap
  * per halving of the area, because the synthetic timing showed a tie where
@@ -263,7 +273,8 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
 int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebsd_demons_params *params, float *ms_out,
                     void *stream);
 /* Set (variant 0..HREBSD_TILE_VARIANTS-1) or clear (-1) the tile shape used
- * for levels of size h x w; get returns the current choice (0 if none). */
+ * for levels of size h x w; get returns the current choice (0 if none was set
+ * or tuned: the level then runs the default above). */
 int hrebsd_set_tile_variant(hrebsd_ctx *ctx, int h, int w, int variant);
 int hrebsd_get_tile_variant(const hrebsd_ctx *ctx, int h, int w);
 

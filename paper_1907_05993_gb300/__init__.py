@@ -297,11 +297,12 @@ def elastic_params(g, R, tilt_rad, stiffness=None, ref_idx=None):
                           _p(ref_idx, t.int32), int(R))
 
 
-TILE_VARIANTS = 7
-# 5: the row sweep; 6: the row sweep with a level's iterations after the first in one launch
-TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64), ("w", "rows"), ("w", "rows"))
-TILE_THREADS = (256, 256, 256, 512, 768, "w", "w")
-TILE_AREAS = (2048, 1024, 1024, 2048, 4096, 65536, 65536)   # outputs per work item (row sweep: a 256 x 256 level)
+TILE_VARIANTS = 8
+# 5: the row sweep; 6: the row sweep with a level's iterations after the first in one launch;
+# 7: the whole level (at most 64 x 64) in shared memory, one launch
+TILE_SHAPES = ((64, 32), (32, 32), (64, 16), (64, 32), (64, 64), ("w", "rows"), ("w", "rows"), ("h", "w"))
+TILE_THREADS = (256, 256, 256, 512, 768, "w", "w", 512)
+TILE_AREAS = (2048, 1024, 1024, 2048, 4096, 65536, 65536, 4096)   # outputs per work item (at most)
 
 
 def hrebsd_autotune(ctx, B, H, W, params, stream=None):

@@ -812,6 +812,7 @@ __global__ void __launch_bounds__(NT_, MINB) demons_iter_tma_kernel(const __grid
 }
 
 #include "demons_strip.cuh"
+#include "demons_level.cuh"
 
 struct CtrlArgs {
     const float *part;       // [B][tiles]
@@ -1022,11 +1023,12 @@ bool encode_level_maps(const float2 *s0, const float2 *s1, const float2 *u0, con
 // (and hence the last bits of the level SSD) are grouped differently.  The
 // extra shapes are compiled for the radius of sigma = 1 (r = 3); other radii
 // use shape 0.
-constexpr int kTileVariants = 7;
+constexpr int kTileVariants = 8;
 constexpr int kStripVariant = 5;   // the row sweep (demons_strip.cuh): one CTA per pair, whole rows
 constexpr int kLoopVariant = 6;    // the row sweep with every iteration k >= 1 of a level in one launch
-constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 256, 256};
-constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 256, 256};
+constexpr int kLevelVariant = 7;   // the whole level in shared memory (demons_level.cuh), <= 64 x 64
+constexpr int kVarTX[kTileVariants] = {64, 32, 64, 64, 64, 256, 256, 64};
+constexpr int kVarTY[kTileVariants] = {32, 32, 16, 32, 64, 256, 256, 64};
 constexpr int kMinTX = 32, kMinTY = 16;   // smallest tile extents (size the per-tile SSD partials)
 bool variant_ok(int rad, int v) { return v == 0 || (rad == 3 && v > 0 && v < kTileVariants); }
 constexpr bool min_extents_ok()
@@ -1091,11 +1093,60 @@ int launch_strip_loop(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs 
     }
 }
 
+// The tile shape of a level: the tuned or pinned one, else the row sweep where it applies (the fastest
+// shape measured at 64, 128 and 256 pixels wide), else shape 0.
 int hr_tuned_variant(const hrebsd_ctx *ctx, int rad, int h, int w)
 {
     for (const auto &t : ctx->tune)
         if (t.h == h && t.w == w) return variant_ok(rad, t.var) ? t.var : 0;
-    return 0;
+    return strip_ok(rad, w) ? kStripVariant : 0;
+}
+
+// The whole level in shared memory covers levels of at most 64 x 64 pixels at the Gaussian radius 3.
+bool level_ok(int rad, int h, int w) { return rad == 3 && h <= lvl::MAXD && w <= lvl::MAXD; }
+
+// One launch for a whole level of B pairs (pairs from the counter a.work, zeroed here).
+int launch_level(hrebsd_ctx *ctx, const lvl::LevelArgs &a, cudaStream_t st)
+{
+    static int configured_dev = -1;
+    static int occ = 0;
+    auto k = lvl::demons_level_kernel<3>;
+    if (configured_dev != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lvl::BYTES));
+        HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, lvl::NT, lvl::BYTES));
+        if (occ < 1) occ = 1;
+        configured_dev = ctx->device;
+    }
+    int grid = ctx->num_sms * occ;
+    if (grid > a.B) grid = a.B;
+    if (grid < 1) grid = 1;
+    HR_CHECK(cudaMemsetAsync(a.work, 0, sizeof(int), st));
+    hr_prof_begin(ctx, st);
+    k<<<grid, lvl::NT, lvl::BYTES, st>>>(a);
+    hr_prof_end(ctx, PROF_ITER, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
+// Pairs the loop form keeps resident at once (one CTA each) at a level w pixels wide.
+template <int NT>
+int strip_capacity_t(hrebsd_ctx *ctx)
+{
+    using G = strip::Geo<3, NT>;
+    static int configured_dev = -1;
+    static int occ = 0;
+    if (configured_dev != ctx->device) {
+        auto k = strip::demons_strip_kernel<3, NT, true, true>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, G::BYTES) != cudaSuccess)
+            occ = 0;
+        configured_dev = ctx->device;
+    }
+    return ctx->num_sms * occ;
+}
+int strip_capacity(hrebsd_ctx *ctx, int w)
+{
+    return w == 64 ? strip_capacity_t<64>(ctx) : w == 128 ? strip_capacity_t<128>(ctx) : w == 256 ? strip_capacity_t<256>(ctx) : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1362,13 +1413,19 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         const int h = H >> l, w = W >> l;
         const int cap = p->max_iters[l];
         int var = hr_tuned_variant(ctx, rad, h, w);
+        // the whole level in shared memory, one launch (needs at least one iteration)
+        const bool use_level = var == kLevelVariant && level_ok(rad, h, w) && cap >= 1;
+        if (var == kLevelVariant && !use_level) var = kStripVariant;
         const bool sweep_v = var == kStripVariant || var == kLoopVariant;
         const bool use_strip = sweep_v && strip_ok(rad, w) && !ctx->no_tma;
         if (sweep_v && !use_strip) var = 4;   // the row sweep does not cover this level: 64x64 tiles
-        // the whole level after iteration 0 in one launch (needs the stop rule's history: cap > 1)
-        const bool use_loop = use_strip && var == kLoopVariant && cap > 1;
+        // the whole level after iteration 0 in one launch (needs the stop rule's history: cap > 1):
+        // shape 6, or shape 5 when every pair has a CTA of its own, so that no pair waits for another
+        // (more pairs than CTAs: per-iteration launches re-balance the uneven counts every iteration)
+        const bool use_loop = use_strip && cap > 1 &&
+                              (var == kLoopVariant || (var == kStripVariant && B <= strip_capacity(ctx, w)));
         CUtensorMap tmS[3], tmF;
-        const bool use_tma = !use_strip && rad > 0 && !ctx->no_tma && cap > 1 &&
+        const bool use_tma = !use_level && !use_strip && rad > 0 && !ctx->no_tma && cap > 1 &&
                              encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, (const float2 *)u0, tl[l],
                                          B, h, w, tmS, &tmF);
         // The launches of one level: list reset, cap x (iteration, control) -- or, in the loop
@@ -1376,6 +1433,43 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         // prolongation.  Replayed from a cached CUDA graph when possible.
         auto emit = [&](cudaStream_t st) -> int {
             int e2;
+            if (use_level) {   // the whole level, final field included, in one launch
+                lvl::LevelArgs a;
+                a.Ftest = tl[l];
+                a.Mref = rl[l];
+                a.ref_idx = ref_idx;
+                a.u0 = (const float2 *)u0;
+                a.uout = l == 0 ? field : (float *)uout;
+                a.hist = (double *)hist;
+                a.iters = iters;
+                a.status = status;
+                a.work = cnt;
+                a.px_count = hr_prof_pixiters(ctx);
+                a.B = B;
+                a.h = h;
+                a.w = w;
+                a.hist_stride = cap_max + 1;
+                a.cap = cap;
+                a.window = p->stop_window;
+                a.level = l;
+                a.levels = L;
+                a.planar = l == 0;
+                a.tol = p->stop_tol;
+                a.alpha2 = p->alpha * p->alpha;
+                a.taps = taps;
+                if ((e2 = launch_level(ctx, a, st))) return e2;
+                if (l > 0) {
+                    const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
+                    if ((long long)B * Hf > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
+                    const unsigned rows = (unsigned)B * (unsigned)Hf;
+                    const int threads = Wf >= 256 ? 256 : (Wf + 31) / 32 * 32;
+                    hr_prof_begin(ctx, st);
+                    prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
+                    hr_prof_end(ctx, PROF_DEMONS_AUX, st);
+                    HR_LAUNCHED(ctx);
+                }
+                return HREBSD_OK;
+            }
             hr_prof_begin(ctx, st);
             iota_kernel<<<(B + 255) / 256, 256, 0, st>>>(list0, B, cnt);
             hr_prof_end(ctx, PROF_DEMONS_AUX, st);
@@ -1465,6 +1559,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 c.level = l;
                 c.levels = L;
                 c.tol = p->stop_tol;
+                c.work = cnt;   // list0's count, free after iteration 0: the loop's item counter
+                HR_CHECK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
                 if ((e2 = launch_strip_loop(ctx, a, c, B, st))) return e2;
             }
             const int tiles_x = (w + TX - 1) / TX, tiles = tiles_x * ((h + TY - 1) / TY);
@@ -1495,7 +1591,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         static_assert(sizeof(kp) / sizeof(kp[0]) <= sizeof(key.p) / sizeof(key.p[0]), "graph key");
         for (size_t i = 0; i < sizeof(kp) / sizeof(kp[0]); ++i) key.p[i] = kp[i];
         const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window, (int)use_strip,
-                          (int)use_loop};
+                          (int)use_loop, (int)use_level};
         for (size_t i = 0; i < sizeof(ki) / sizeof(ki[0]); ++i) key.i[i] = ki[i];
         key.f[0] = p->alpha;
         key.f[1] = p->stop_tol;
@@ -1633,9 +1729,11 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 if (!variant_ok(rad, v) || ctx->no_tma) continue;
                 const bool lv = v == kLoopVariant;
                 const bool sv = v == kStripVariant || lv;
+                const bool vv = v == kLevelVariant;
                 if (sv && !strip_ok(rad, w)) continue;
+                if (vv && !level_ok(rad, h, w)) continue;
                 CUtensorMap tmS[3], tmF;
-                if (!sv && !encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
+                if (!sv && !vv && !encode_maps(rad, v, (const float2 *)s0, (const float2 *)s1, nullptr, test, Bt, h, w, tmS, &tmF))
                     continue;
                 const int tiles_x = sv ? 1 : (w + kVarTX[v] - 1) / kVarTX[v];
                 const int tiles = sv ? 1 : tiles_x * ((h + kVarTY[v] - 1) / kVarTY[v]);
@@ -1661,6 +1759,43 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 constexpr int kWarm = 2, kBatch = 4, kRounds = 3;
                 float ms = 0.0f;
                 int k = 0;
+                if (vv) {   // whole levels of kLoopCap iterations: one warm-up launch, then the best of 3
+                    lvl::LevelArgs la;
+                    la.Ftest = test;
+                    la.Mref = ref;
+                    la.ref_idx = ridx;
+                    la.u0 = (const float2 *)s0;
+                    la.uout = (float *)s1;
+                    la.hist = lhist;
+                    la.iters = liters;
+                    la.status = lstatus;
+                    la.work = cnt + 2;
+                    la.px_count = nullptr;
+                    la.B = Bt;
+                    la.h = h;
+                    la.w = w;
+                    la.hist_stride = kLoopCap + 1;
+                    la.cap = kLoopCap;
+                    la.window = 0;
+                    la.level = 0;
+                    la.levels = 1;
+                    la.planar = 0;
+                    la.tol = 0.0f;
+                    la.alpha2 = p->alpha * p->alpha;
+                    la.taps = taps;
+                    HR_CHECK(cudaMemsetAsync(lstatus, 0, (size_t)Bt * 4, st));
+                    for (int rep = 0; rep <= kRounds; ++rep) {
+                        HR_CHECK(cudaEventRecord(ev[0], st));
+                        int e2 = launch_level(ctx, la, st);
+                        if (e2) return e2;
+                        HR_CHECK(cudaEventRecord(ev[1], st));
+                        HR_CHECK(cudaEventSynchronize(ev[1]));
+                        float t = 0.0f;
+                        HR_CHECK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+                        t /= (float)kLoopCap;
+                        if (rep == 1 || (rep > 1 && t < ms)) ms = t;
+                    }
+                }
                 if (lv) {
                     strip::LoopArgs c;
                     c.s0 = (float2 *)s0;
@@ -1674,8 +1809,10 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                     c.level = 0;
                     c.levels = 1;
                     c.tol = 0.0f;
+                    c.work = cnt + 2;
                     HR_CHECK(cudaMemsetAsync(lstatus, 0, (size_t)Bt * 4, st));
                     for (int rep = 0; rep <= kRounds; ++rep) {
+                        HR_CHECK(cudaMemsetAsync(c.work, 0, sizeof(int), st));
                         HR_CHECK(cudaEventRecord(ev[0], st));
                         int e2 = launch_strip_loop(ctx, a, c, Bt, st);
                         if (e2) return e2;
@@ -1687,14 +1824,14 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                         if (rep == 1 || (rep > 1 && t < ms)) ms = t;
                     }
                 }
-                for (; !lv && k < kWarm; ++k) {
+                for (; !lv && !vv && k < kWarm; ++k) {
                     a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
                     a.out = (k & 1) ? (float2 *)s0 : (float2 *)s1;
                     int e2 = sv ? launch_strip(ctx, true, a, Bt, st)
                                 : dispatch_iter_tma(ctx, rad, v, true, tmS[k & 1], tmF, a, Bt * tiles, st);
                     if (e2) return e2;
                 }
-                for (int rep = 0; !lv && rep < kRounds; ++rep) {
+                for (int rep = 0; !lv && !vv && rep < kRounds; ++rep) {
                     HR_CHECK(cudaEventRecord(ev[0], st));
                     for (int j = 0; j < kBatch; ++j, ++k) {
                         a.in = (k & 1) ? (const float2 *)s1 : (const float2 *)s0;
@@ -1711,6 +1848,10 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                     if (rep == 0 || t < ms) ms = t;
                 }
                 if (ms_out) ms_out[l * kTileVariants + v] = ms;
+                // shape 6 is timed but not chosen: its synthetic pairs all run the same number of
+                // iterations, while on scan data a pair with many iterations holds its CTA alone
+                // (shape 5 switches to the loop form by itself when every pair has a CTA)
+                if (lv) continue;
                 // Score = time x (1 + 1 % per halving of the tile area below 64 x 64): the
                 // synthetic patterns (small, smooth displacements; every pair active) timed the
                 // 64x32 and 64x64 shapes as a tie at 256x256 where the 64x64 one was 4 % faster

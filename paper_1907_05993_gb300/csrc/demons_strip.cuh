@@ -84,12 +84,14 @@ __device__ __forceinline__ void issue_step(bool copy_s, const float2 *sp, const 
 // The whole level in one launch (the row sweep's LOOP form): every active pair iterates in its CTA
 // until the stop rule of the control kernel (same rule, same FP64 history, one SSD partial per pair)
 // ends it, so the level needs no launch per iteration.  Iterations k >= 1; iteration 0 (which reads
-// u_0) runs as a plain launch first.
+// u_0) runs as a plain launch first.  A CTA whose pair stops takes the next item of the active list
+// from an atomic counter, so pairs with many iterations do not hold up a fixed share of the list.
 struct LoopArgs {
     float2 *s0, *s1;        // s_k for even / odd k
     double *hist;           // [B][hist_stride]
     int32_t *iters;         // [B][levels]
     int32_t *status;        // [B]
+    int *work;              // the next item of the active list to take (zero at launch)
     int hist_stride, cap, window, level, levels;
     float tol;
 };
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
     __shared__ float red[NT / 32];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_next;   // LOOP: the pair's next iteration, or -1 once the stop rule ended it
+    __shared__ int s_item;   // LOOP: the item taken from the counter
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int NWARP = NT / 32;
@@ -207,6 +210,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
     constexpr int K_FIRST = LOOP ? 1 : 0;   // the iteration of an item's first sweep (LOOP: after k = 0)
 
     int item = blockIdx.x;
+    if (LOOP) {
+        if (t == 0) s_item = atomicAdd(c.work, 1);
+        __syncthreads();
+        item = s_item;
+    }
     uint32_t g = 0;   // steps of this CTA so far: step g uses buffer g & 1, phase parity (g >> 1) & 1
     if (warp == 0 && item < n_active) {
         const int p0 = a.active[item];
@@ -214,9 +222,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
         issue_step<RAD, NT>(IN_S, src_of(p0, K_FIRST), fsrc_of(p0), h, 1, sS0 + R * G::HST, sF0 + G::FR_ * G::FST,
                             &bar[1], lane);
     }
-    for (; item < n_active; item += gridDim.x) {
+    while (item < n_active) {
         const int pair = a.active[item];
-        const int next_pair = item + (int)gridDim.x < n_active ? a.active[item + gridDim.x] : -1;
+        const int next_pair = !LOOP && item + (int)gridDim.x < n_active ? a.active[item + gridDim.x] : -1;
+        int next_item = item + (int)gridDim.x;
         const float *M = a.Mref + (size_t)__ldg(a.ref_idx + pair) * plane;
         const float2 *u0 = a.in + (size_t)pair * plane;   // the level's initial field when !IN_S
         const float *fp = fsrc_of(pair);
@@ -438,17 +447,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
                 nk = kit + 1;
             }
             if (a.px_count) atomicAdd(a.px_count, (unsigned long long)h * NT);
+            if (nk < 0) s_item = atomicAdd(c.work, 1);
             s_next = nk;
         }
         __syncthreads();
         const int nk = s_next;
-        if (nk < 0) {   // the pair is done: the next pair's first two steps
-            if (warp == 0 && next_pair >= 0) {
-                issue_step<RAD, NT>(true, src_of(next_pair, K_FIRST), fsrc_of(next_pair), h, 0, sS0 + (g & 1) * R * G::HST,
+        if (nk < 0) {   // the pair is done: the next item's first two steps
+            next_item = s_item;
+            if (warp == 0 && next_item < n_active) {
+                const int np = a.active[next_item];
+                issue_step<RAD, NT>(true, src_of(np, K_FIRST), fsrc_of(np), h, 0, sS0 + (g & 1) * R * G::HST,
                                     sF0 + (g & 1) * G::FR_ * G::FST, &bar[g & 1], lane);
-                issue_step<RAD, NT>(true, src_of(next_pair, K_FIRST), fsrc_of(next_pair), h, 1,
-                                    sS0 + ((g + 1) & 1) * R * G::HST, sF0 + ((g + 1) & 1) * G::FR_ * G::FST,
-                                    &bar[(g + 1) & 1], lane);
+                issue_step<RAD, NT>(true, src_of(np, K_FIRST), fsrc_of(np), h, 1, sS0 + ((g + 1) & 1) * R * G::HST,
+                                    sF0 + ((g + 1) & 1) * G::FR_ * G::FST, &bar[(g + 1) & 1], lane);
             }
             break;
         }
@@ -459,6 +470,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
                                 sF0 + ((g + 1) & 1) * G::FR_ * G::FST, &bar[(g + 1) & 1], lane);
         }
       }
+        item = next_item;
     }
 }
 

@@ -89,11 +89,14 @@ def test_autotune_records_the_fastest_shape(torch, lib):
     params = lib.demons_params(4, [100] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
     ms = lib.hrebsd_autotune(ctx, 64, 256, 256, params)
     assert ms.shape == (4, lib.TILE_VARIANTS)
-    # the row sweep (shapes 5 and 6) covers levels 64, 128 and 256 pixels wide, not 32
+    # the row sweep (shapes 5 and 6) covers levels 64, 128 and 256 pixels wide, not 32; the level in
+    # shared memory (7) levels of at most 64 x 64
     assert np.isfinite(ms[:, :5]).all() and (ms[:, :5] > 0).all(), ms
-    assert np.isfinite(ms[:3, 5:]).all() and np.isnan(ms[3, 5:]).all(), ms
+    assert np.isfinite(ms[:3, 5:7]).all() and np.isnan(ms[3, 5:7]).all(), ms
+    assert np.isnan(ms[:2, 7]).all() and np.isfinite(ms[2:, 7]).all(), ms
     area = np.array(lib.TILE_AREAS, dtype=np.float64)
     score = ms * (1.0 + 0.01 * np.maximum(0.0, np.log2(4096.0 / area)))   # the documented handicap of small tiles
+    score[:, 6] = np.nan   # shape 6 is timed but never chosen
     for l in range(4):
         assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == int(np.nanargmin(score[l]))
     # radius 0 (no smoothing): nothing to tune
@@ -107,7 +110,11 @@ def test_autotune_records_the_fastest_shape(torch, lib):
 def test_level_in_one_launch_matches_row_sweep_with_stop_rule(torch, lib, pairs):
     """Shape 6 runs a level's iterations after the first in one launch and applies the stop rule in
     each pair's CTA; with the same SSD partials as shape 5 (one per pair) it must stop every pair at
-    the same iteration and give the same field, bit for bit, also with a cap that ends some pairs."""
+    the same iteration and give the same field, bit for bit, also with a cap that ends some pairs.
+    The four pairs are repeated to 1,600, more than the resident CTAs of any level, so that shape 5
+    runs one launch per iteration (with fewer pairs it takes the one-launch form itself)."""
+    refs, tests, ridx = pairs
+    big = (refs, np.tile(tests, (400, 1, 1)), np.tile(ridx, 400))
     for caps in ([100] * 4, [9, 30, 100, 100]):
         params = lib.demons_params(4, caps, 1.0, 1.0, 1.0, 1e-4, 5)
         out = []
@@ -115,12 +122,13 @@ def test_level_in_one_launch_matches_row_sweep_with_stop_rule(torch, lib, pairs)
             ctx = lib.hrebsd_create(0)
             for l in range(4):
                 lib.hrebsd_set_tile_variant(ctx, 256 >> l, 256 >> l, v)
-            out.append(_register(torch, lib, ctx, pairs, params))
+            out.append(_register(torch, lib, ctx, big, params))
             lib.hrebsd_destroy(ctx)
         (f5, it5, st5), (f6, it6, st6) = out
         assert np.array_equal(it5, it6) and np.array_equal(st5, st6), (it5, it6, st5, st6)
         assert np.array_equal(f5, f6)
         assert it5.max() > 1
+        assert np.array_equal(f5[:4], f5[4:8]) and np.array_equal(it5[:4], it5[-4:])
 
 
 def test_graph_replay_matches_direct_launches(torch, lib, pairs):

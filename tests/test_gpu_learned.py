@@ -131,11 +131,12 @@ def _field_stats(args):
                 "frac": float(np.mean(d > FS.FIELD_TOL)), "mfrac": [float(np.mean(x > FS.FIELD_TOL)) for x in dm],
                 "size": d.size}
     members = FS.perturbed_fields(oracle, pr, pt, 3, it, members=8, seed0=77 + p, input_ulps=pre)
-    st = stats(members)
+    st = first8 = stats(members)
     if (any(st["g"][q] > max(FS.FIELD_TOL, FS.FACTOR * max(st["m"][q])) for q in FS.QUANTILES)
             or st["frac"] > FS.FACTOR * max(st["mfrac"]) + _pixel_floor(st["size"])):
         members += FS.perturbed_fields(oracle, pr, pt, 3, it, members=24, seed0=77 + p + 8, input_ulps=pre)
         st = stats(members)
+    st["first8"] = first8   # the population test uses the first eight whatever the outcome
     return st
 
 
@@ -143,15 +144,17 @@ def test_training_targets_spot_checked_against_oracle(oracle):
     """Training targets (the final field of the full registration, box-averaged to 64x64 in 64x64-pixel
     units) from the library path on a seeded 1 % sample of the 200,000 training pairs, against the
     oracle's registration of the same numpy-rendered pairs replaying the library's per-level iteration
-    counts.  A target within 5e-4 everywhere passes.  The others' 128x128 fields are compared with the
-    oracle's own FP32 executions of the same pair (tests/fp32_sensitivity.py), as a population: if the
-    library's field is no further from the FP64 oracle than an FP32 execution is, then at each quantile
-    it exceeds all n executions of a pair with probability 1 / (n + 1), so the number of pairs where it
-    does must stay within the binomial expectation plus three standard deviations (and one); every pair
-    is held to 10x its executions' largest value and to the fraction-of-pixels rule of the field bar.
-    The executions' deviations are heavy-tailed (one pair: the 99.9 % quantile ranged from 6e-6 to
-    3.6e-3 px over 24 executions), which is why a fixed factor over a few executions, pair by pair,
-    fails by chance when dozens of pairs are checked."""
+    counts.  A target within 5e-4 everywhere passes; every other pair's 128x128 field is held to 10x
+    the largest deviation among the oracle's own FP32 executions of that pair (tests/fp32_sensitivity.py;
+    8, or 32 beyond the per-pair field bar) at each quantile and in the fraction of pixels above 1e-3 px.
+    The distribution is tested as a population on a seeded subset of 250 pairs drawn without regard to
+    their outcome (selecting pairs by the library's own deviation would bias the test): if the library's
+    field is no further from the FP64 oracle than an FP32 execution is, at each statistic it exceeds all
+    n executions of a pair with probability 1 / (n + 1), so the number of pairs where it does must stay
+    within the binomial expectation plus three standard deviations (and one).  The executions'
+    deviations are heavy-tailed (one pair: the 99.9 % quantile ranged from 6e-6 to 3.6e-3 px over 24
+    executions), which is why a fixed factor over a few executions, pair by pair, fails by chance when
+    hundreds of pairs are checked."""
     import multiprocessing as mp
     import torch
     import paper_1907_05993_gb300 as P
@@ -180,15 +183,21 @@ def test_training_targets_spot_checked_against_oracle(oracle):
             tg = target.cpu().numpy().astype(np.float64)
             dev = pool.map(_target_check, [(p, it[i], tg[i]) for i, p in enumerate(pairs)], chunksize=8)
             loose = [i for i, d in enumerate(dev) if d > TARGET_TOL]
-            stats = pool.map(_field_stats, [(pairs[i], it[i], field[i].cpu().numpy().astype(np.float64),
-                                             refs[i].cpu().numpy(), tests[i].cpu().numpy()) for i in loose],
-                             chunksize=1)
+            subset = sorted(np.random.default_rng(4041).choice(n, 250, replace=False).tolist())
+            checked = sorted(set(loose) | set(subset))
+            got = pool.map(_field_stats, [(pairs[i], it[i], field[i].cpu().numpy().astype(np.float64),
+                                           refs[i].cpu().numpy(), tests[i].cpu().numpy()) for i in checked],
+                           chunksize=1)
+            by_index = dict(zip(checked, got))
         finally:
             P.hrebsd_destroy(ctx)
+    loose_stats = [by_index[i] for i in loose]
+    stats = [by_index[i]["first8"] for i in subset]
     K = len(stats)
-    lines = [f"training targets: {n - K}/{n} within {TARGET_TOL} everywhere (worst {max(dev):.2e}); {K} compared "
-             f"with the oracle's FP32 executions ({sum(1 for st in stats if st['n'] > 8)} of them with 32)"]
-    for st in stats:   # per pair: hard caps on every quantile and on the fraction of pixels above 1e-3 px
+    lines = [f"training targets: {n - len(loose)}/{n} within {TARGET_TOL} everywhere (worst {max(dev):.2e}); "
+             f"{len(loose)} held to 10x the oracle's FP32 executions "
+             f"({sum(1 for st in loose_stats if st['n'] > 8)} of them with 32); population test on {K} pairs"]
+    for st in loose_stats:   # per pair: hard caps on every quantile and on the fraction of pixels above 1e-3 px
         for q in FS.QUANTILES:
             assert st["g"][q] <= max(FS.FIELD_TOL, HARD_FACTOR * max(st["m"][q])), (st["p"], q, st["g"][q], max(st["m"][q]))
         assert st["frac"] <= HARD_FACTOR * max(st["mfrac"]) + _pixel_floor(st["size"]), \
