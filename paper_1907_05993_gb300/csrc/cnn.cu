@@ -294,8 +294,12 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, size_t
 // padded to 16; the padded entries see zero inputs, so their gradients are zero
 // and they stay at zero).  -> BF16 copy of the same layout, and the BF16
 // input-gradient layout [ci][tap'][co] with tap' = 8 - tap (the flipped
-// kernel with input and output channels exchanged).
-__global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp, bf16 *wf, bf16 *wd, bf16 *wt, int bn)
+// kernel with input and output channels exchanged); the tensor-memory tile
+// layouts of the forward kernel (wt) and of the input-gradient kernel (wtd:
+// output channel c, input channel o, tap 8 - tap; null where ci is not a
+// multiple of its channel block).
+__global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp, bf16 *wf, bf16 *wd, bf16 *wt, int bn,
+                                       bf16 *wtd)
 {
     const int total = co * 9 * cinp;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -306,6 +310,9 @@ __global__ void weights_to_bf16_kernel(const float *w, int ci, int co, int cinp,
         // tensor-memory path: [co / bn][cinp / 16][c % 16 / 8][tap][o % bn][c % 8]
         if (wt)
             wt[(((((size_t)(o / bn) * (cinp / 16) + c / 16) * 2 + (c % 16) / 8) * 9 + tap) * bn + o % bn) * 8 + c % 8] =
+                __float2bfloat16_rn(v);
+        if (wtd && c < ci)   // co is a multiple of 16
+            wtd[(((((size_t)(c / bn) * (co / 16) + o / 16) * 2 + (o % 16) / 8) * 9 + (8 - tap)) * bn + c % bn) * 8 + o % 8] =
                 __float2bfloat16_rn(v);
     }
 }
@@ -331,7 +338,7 @@ struct hr_cnn_net {
     size_t n_params = 0;
     size_t w_off[NCONV + 1], b_off[NCONV + 1];   // index NCONV = head
     float *W = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
-    bf16 *wf[NCONV + 1] = {}, *wd[NCONV] = {}, *wt[NCONV] = {};
+    bf16 *wf[NCONV + 1] = {}, *wd[NCONV] = {}, *wt[NCONV] = {}, *wtd[NCONV] = {};
     int step = 0;
     // activations for a batch capacity
     int cap = 0;
@@ -345,6 +352,7 @@ struct hr_cnn_net {
     float *g_cat = nullptr;                                 // FP32 gradient of a concat input
     bf16 *dpre = nullptr;
     std::vector<void *> allocs;
+    size_t param_allocs = 0;   // allocations of the parameter block (kept when activations are regrown)
 };
 
 namespace {
@@ -362,8 +370,8 @@ int net_alloc(std::vector<void *> &allocs, size_t bytes, void **p)
 
 void net_free_acts(hr_cnn_net *n)
 {
-    // activations are the allocations after the parameter block (index >= 4 + 15 + 14 + 14)
-    const size_t keep = 4 + (NCONV + 1) + 2 * NCONV;
+    // activations are the allocations after the parameter block (its count recorded when it was made)
+    const size_t keep = n->param_allocs;
     for (size_t i = keep; i < n->allocs.size(); ++i) cudaFree(n->allocs[i]);
     if (n->allocs.size() > keep) n->allocs.resize(keep);
     n->cap = 0;
@@ -407,6 +415,15 @@ int ensure_net(hrebsd_ctx *ctx)
         }
         n->wt[l] = (bf16 *)p;
     }
+    for (int l = 1; l < NCONV; ++l) {   // the input gradients on tensor memory where the channel block divides ci
+        if (kLayers[l].cin % tma_bn(kLayers[l].res)) continue;
+        if ((e = net_alloc(n->allocs, (size_t)kLayers[l].cin * 9 * kLayers[l].cout * sizeof(bf16), &p))) {
+            delete n;
+            return e;
+        }
+        n->wtd[l] = (bf16 *)p;
+    }
+    n->param_allocs = n->allocs.size();
     ctx->cnn = n;
     return HREBSD_OK;
 }
@@ -459,7 +476,7 @@ int refresh_bf16(hrebsd_ctx *ctx, cudaStream_t st)
     for (int l = 0; l < NCONV; ++l) {
         const int ci = kLayers[l].cin, co = kLayers[l].cout;
         weights_to_bf16_kernel<<<grid_for(ctx, (size_t)co * 9 * pad16(ci)), 256, 0, st>>>(
-            n->W + n->w_off[l], ci, co, pad16(ci), n->wf[l], n->wd[l], n->wt[l], tma_bn(kLayers[l].res));
+            n->W + n->w_off[l], ci, co, pad16(ci), n->wf[l], n->wd[l], n->wt[l], tma_bn(kLayers[l].res), n->wtd[l]);
         HR_LAUNCHED(ctx);
     }
     cast_bf16_kernel<<<1, 64, 0, st>>>(n->W + n->w_off[NCONV], HEAD_COUT * HEAD_CIN, n->wf[NCONV]);
@@ -504,7 +521,8 @@ int launch_tma_t(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_
     TmaConvArgs t;
     t.wt = wt;
     t.bias = a.bias;
-    t.y = reinterpret_cast<bf16 *>(a.y);
+    t.y = a.y_fp32 ? nullptr : reinterpret_cast<bf16 *>(a.y);
+    t.yf = a.y_fp32 ? reinterpret_cast<float *>(a.y) : nullptr;
     t.ys = a.ys;
     t.yo = a.yo;
     t.relu = a.relu;
@@ -562,7 +580,7 @@ int launch_tma_t(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_
 
 int launch_tma_conv(hrebsd_ctx *ctx, const ConvArgs &a, const bf16 *wt, cudaStream_t st)
 {
-    if (!wt || !ctx->cnn_tc || a.y_fp32 || a.H != a.W || a.N < 1 || a.cin % 16) return 1;
+    if (!wt || !ctx->cnn_tc || a.H != a.W || a.N < 1 || a.cin % 16) return 1;
     if (a.xs % 8 || a.xo % 8 || a.ys % 8 || a.yo % 8) return 1;
     switch (a.H) {
     case 64: return launch_tma_t<64>(ctx, a, wt, st);
@@ -761,7 +779,8 @@ int conv_bwd(hrebsd_ctx *ctx, int l, const float *dpost, int ds, int dof, float 
     bias_grad_kernel<<<grid_for(ctx, P), 256, 0, st>>>(n->dpre, L.cout, P, n->G + n->b_off[l]);
     HR_LAUNCHED(ctx);
     if (dx)
-        return conv(ctx, n->dpre, L.cout, 0, L.cout, n->wd[l], nullptr, L.cin, dx, L.cin, 0, 1, 0, B, L.res, st);
+        return conv(ctx, n->dpre, L.cout, 0, L.cout, n->wd[l], nullptr, L.cin, dx, L.cin, 0, 1, 0, B, L.res, st,
+                    n->wtd[l]);
     return HREBSD_OK;
 }
 

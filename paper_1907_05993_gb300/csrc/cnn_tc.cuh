@@ -55,7 +55,8 @@ struct TmaGeom {
 struct TmaConvArgs {
     const bf16 *wt;      // [cout / BN][cin / 16][2][9][BN][8]
     const float *bias;   // [cout] or null
-    bf16 *y;             // output (NHWC, channel stride ys, offset yo)
+    bf16 *y;             // output (NHWC, channel stride ys, offset yo), or null when yf is set
+    float *yf;           // FP32 output in the same layout (the input gradients), or null
     int ys, yo, relu;
     int cin, cout, N;
     int cw;              // channels per box (16, 32 or 64)
@@ -223,7 +224,21 @@ __global__ void __launch_bounds__(kTmaConvThreads, 1)
 #pragma unroll
                 for (int c0 = 0; c0 < BN; c0 += 16) hr_tc::ld16_async(d + (uint32_t)(m * BN + c0), &v[c0]);
                 hr_tc::wait_ld();
-                if (prel[j] >= 0 && T.n0 + pnl[j] < a.N) {
+                if (prel[j] >= 0 && T.n0 + pnl[j] < a.N && a.yf) {   // FP32 output
+                    float4 *dst = reinterpret_cast<float4 *>(a.yf + (pbase + prel[j]) * a.ys + a.yo + o0);
+#pragma unroll
+                    for (int c0 = 0; c0 < BN; c0 += 4) {
+                        float4 o4 = make_float4(v[c0] + bias_s[o0 + c0], v[c0 + 1] + bias_s[o0 + c0 + 1],
+                                                v[c0 + 2] + bias_s[o0 + c0 + 2], v[c0 + 3] + bias_s[o0 + c0 + 3]);
+                        if (a.relu) {
+                            o4.x = fmaxf(o4.x, 0.0f);
+                            o4.y = fmaxf(o4.y, 0.0f);
+                            o4.z = fmaxf(o4.z, 0.0f);
+                            o4.w = fmaxf(o4.w, 0.0f);
+                        }
+                        dst[c0 / 4] = o4;
+                    }
+                } else if (prel[j] >= 0 && T.n0 + pnl[j] < a.N) {
                     uint4 *dst = reinterpret_cast<uint4 *>(a.y + (pbase + prel[j]) * a.ys + a.yo + o0);
 #pragma unroll
                     for (int c0 = 0; c0 < BN; c0 += 8) {
