@@ -10,10 +10,12 @@
 #include <string.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "cnn_kernels.cuh"
 #include "cnn_tc.cuh"
+
 #include "internal.cuh"
 
 using namespace hr_cnn;
@@ -351,6 +353,7 @@ struct hr_cnn_net {
     float *g_a = nullptr, *g_b = nullptr, *g_c = nullptr;   // FP32 gradient scratch (largest activation)
     float *g_cat = nullptr;                                 // FP32 gradient of a concat input
     bf16 *dpre = nullptr;
+    bf16 *xT = nullptr, *dyS[3] = {};   // planar copies for the tcgen05 weight gradients
     std::vector<void *> allocs;
     size_t param_allocs = 0;   // allocations of the parameter block (kept when activations are regrown)
 };
@@ -465,6 +468,14 @@ int ensure_acts(hrebsd_ctx *ctx, int B)
     NA(n->g_c, gmax * sizeof(float));
     NA(n->g_cat, gmax * sizeof(float));
     NA(n->dpre, gmax * sizeof(bf16));
+    size_t xmax = 0, dmax = 0;   // the largest conv input (padded channels) and output, in elements
+    for (int l = 0; l < NCONV; ++l) {
+        const size_t px = (size_t)B * kLayers[l].res * kLayers[l].res;
+        xmax = std::max(xmax, px * pad16(kLayers[l].cin));
+        dmax = std::max(dmax, px * kLayers[l].cout);
+    }
+    NA(n->xT, xmax * sizeof(bf16));
+    for (int k = 0; k < 3; ++k) NA(n->dyS[k], dmax * sizeof(bf16));
 #undef NA
     n->cap = B;
     return HREBSD_OK;
@@ -662,27 +673,88 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
     return HREBSD_OK;
 }
 
+// Weight gradients on tcgen05 (planar copies, then the TMA-fed GEMM per tap); 1 = not applicable.
+template <int NB>
+int wgrad_tc_t(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs, int xo, int cin, float *dw, int N,
+               int res, cudaStream_t st)
+{
+    hr_cnn_net *n = ctx->cnn;
+    const int P = N * res * res;
+    planar_shift_kernel<<<dim3((unsigned)((P + 63) / 64), (unsigned)((cin + 31) / 32)), 256, 0, st>>>(
+        x, xs, xo, cin, P, res, nullptr, n->xT, nullptr);
+    HR_LAUNCHED(ctx);
+    planar_shift_kernel<<<dim3((unsigned)((P + 63) / 64), (unsigned)((cout + 31) / 32)), 256, 0, st>>>(
+        dy, cout, 0, cout, P, res, n->dyS[0], n->dyS[1], n->dyS[2]);
+    HR_LAUNCHED(ctx);
+    // planar [channel][image][pixel] as 4-D maps {pixels of an image, images, channels, 1}, 64-pixel boxes
+    const uint64_t ip = (uint64_t)res * res * 2;
+    const uint64_t dX[4] = {(uint64_t)res * res, (uint64_t)N, (uint64_t)cin, 1};
+    const uint64_t sX[3] = {ip, (uint64_t)P * 2, (uint64_t)cin * P * 2};
+    const uint32_t bX[4] = {64, 1, 128, 1};
+    const uint64_t dD[4] = {(uint64_t)res * res, (uint64_t)N, (uint64_t)cout, 1};
+    const uint64_t sD[3] = {ip, (uint64_t)P * 2, (uint64_t)cout * P * 2};
+    const uint32_t bD[4] = {64, 1, (uint32_t)NB, 1};
+    CUtensorMap tx, td[3];
+    if (hr_encode_tmap_bf16_4d(&tx, n->xT, dX, sX, bX, 128)) return 1;
+    for (int k = 0; k < 3; ++k)
+        if (hr_encode_tmap_bf16_4d(&td[k], n->dyS[k], dD, sD, bD, 128)) return 1;
+    WgradTcArgs a;
+    a.dw = dw;
+    a.cin = cin;
+    a.cout = cout;
+    a.res = res;
+    a.ncb = (cin + 127) / 128;
+    a.nob = cout / NB;
+    a.ktiles = P / 64;
+    const int items = a.ncb * a.nob;
+    a.splits = ctx->num_sms / items;
+    if (a.splits < 1) a.splits = 1;
+    if (a.splits > a.ktiles) a.splits = a.ktiles;
+    constexpr int STAGE = 128 * 128 + 9 * NB * 128;
+    a.nst = (200 * 1024) / STAGE;
+    if (a.nst > 8) a.nst = 8;
+    const size_t smem = (size_t)a.nst * STAGE + 1024;   // + slack for 1024-byte alignment
+    static int configured = -1;
+    if (configured != ctx->device) {
+        HR_CHECK(cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      210 * 1024));
+        configured = ctx->device;
+    }
+    conv3x3_wgrad_tc_kernel<NB><<<(unsigned)(items * a.splits), kWgradThreads, smem, st>>>(tx, td[0], td[1], td[2], a,
+                                                                                          ctx->d_err);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
+}
+
 int wgrad(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs, int xo, int cin, float *dw, int N, int res,
           cudaStream_t st)
 {
-    WgradArgs a;
-    a.dy = dy;
-    a.cout = cout;
-    a.x = x;
-    a.xs = xs;
-    a.xo = xo;
-    a.cin = cin;
-    a.dw = dw;
-    a.N = N;
-    a.H = res;
-    a.W = res;
-    const int P = N * res * res;
-    a.chunk = 2048;
-    dim3 grid((P + a.chunk - 1) / a.chunk, 9 * ((cin + 63) / 64), (cout + 63) / 64);
     hr_prof_begin(ctx, st);
-    conv3x3_wgrad_kernel<<<grid, 128, 0, st>>>(a);
+    int e = 1;
+    if (ctx->cnn_tc && ctx->cnn->xT && cout % 16 == 0 && (res == 8 || res == 16 || res == 32 || res == 64))
+        e = cout % 32 == 0 ? wgrad_tc_t<32>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, st)
+                           : wgrad_tc_t<16>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, st);
+    if (e == 1) {   // mma.sync over pixel chunks
+        WgradArgs a;
+        a.dy = dy;
+        a.cout = cout;
+        a.x = x;
+        a.xs = xs;
+        a.xo = xo;
+        a.cin = cin;
+        a.dw = dw;
+        a.N = N;
+        a.H = res;
+        a.W = res;
+        const int P = N * res * res;
+        a.chunk = 2048;
+        dim3 grid((P + a.chunk - 1) / a.chunk, 9 * ((cin + 63) / 64), (cout + 63) / 64);
+        conv3x3_wgrad_kernel<<<grid, 128, 0, st>>>(a);
+        HR_LAUNCHED(ctx);
+    } else if (e) {
+        return e;
+    }
     hr_prof_end(ctx, PROF_CNN, st);
-    HR_LAUNCHED(ctx);
     return HREBSD_OK;
 }
 

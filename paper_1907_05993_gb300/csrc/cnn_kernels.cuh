@@ -367,4 +367,39 @@ __global__ void __launch_bounds__(128) conv3x3_wgrad_kernel(WgradArgs a)
     }
 }
 
+// Planar BF16 copies of an NHWC tensor (channel stride ss, offset so, C channels, P pixels of images
+// res x res): dk[c][q] = src[q + s_k][c] with s_0 = +1, s_1 = 0, s_2 = -1, zero where x + s_k leaves
+// the row [0, res); null outputs are skipped.  A block moves 64 pixels x 32 channels through a shared
+// tile with one halo pixel on each side: 16-byte loads along channels (ss, so and C multiples of 8),
+// 16-byte stores of 8 pixels along each output row (P a multiple of 64).
+__global__ void __launch_bounds__(256) planar_shift_kernel(const bf16 *src, int ss, int so, int C, int P, int res,
+                                                         bf16 *d0, bf16 *d1, bf16 *d2)
+{
+    __shared__ unsigned short tile[66][34];   // [pixel][channel]; row stride of 17 words
+    const int q0 = blockIdx.x * 64, c0 = blockIdx.y * 32;
+    for (int i = threadIdx.x; i < 66 * 4; i += 256) {   // 66 pixels x 4 groups of 8 channels
+        const int r = i >> 2, g = i & 3, q = q0 - 1 + r, c = c0 + g * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (q >= 0 && q < P && c < C) v = *reinterpret_cast<const uint4 *>(src + (size_t)q * ss + so + c);
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tile[r][g * 8 + j] = h[j];
+    }
+    __syncthreads();
+    unsigned short *out[3] = {reinterpret_cast<unsigned short *>(d0), reinterpret_cast<unsigned short *>(d1),
+                              reinterpret_cast<unsigned short *>(d2)};
+    for (int i = threadIdx.x; i < 3 * 32 * 8; i += 256) {   // (copy, channel, 8-pixel group)
+        const int k = i / 256, c = (i >> 3) & 31, g = i & 7;
+        if (!out[k] || c0 + c >= C) continue;
+        const int sft = 1 - k;
+        __align__(16) unsigned short h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int jj = g * 8 + j, x = (q0 + jj) % res;
+            h[j] = (x + sft >= 0 && x + sft < res) ? tile[jj + 1 + sft][c] : (unsigned short)0;
+        }
+        *reinterpret_cast<uint4 *>(out[k] + (size_t)(c0 + c) * P + q0 + g * 8) = *reinterpret_cast<const uint4 *>(h);
+    }
+}
+
 }  // namespace hr_cnn

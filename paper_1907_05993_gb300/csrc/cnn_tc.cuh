@@ -277,3 +277,154 @@ __global__ void __launch_bounds__(kTmaConvThreads, 1)
 }
 
 }  // namespace hr_cnn
+
+namespace hr_cnn {
+
+// Weight gradients of a 3x3 convolution on tcgen05:
+//   dw[o][tap][c] = sum_p dy[p][o] x[p + off(tap)][c] = sum_q dy[q - off(tap)][o] x[q][c],
+// a GEMM per tap over the pixels q (K).  With K-major operands (the library's tested descriptor
+// form) the pixels must be contiguous: the inputs come transposed to planar [channel][image][pixel]
+// BF16 (xT, and dy in three copies shifted by +1, 0, -1 pixels along x with zeros past the row ends);
+// the shift along y is the TMA coordinate (whole rows, 16-byte aligned; rows outside read zero).
+// D[c][tap * NB + o] = A (128 input channels x 64 pixels) B_tap^T (NB output channels x 64 pixels),
+// accumulated over the CTA's range of 64-pixel K tiles; the epilogue adds D into dw with atomics.
+// Warp 0: TMA producer; warp 1: MMA issuer; warps 2-5: epilogue (TMEM lanes = input channels).
+struct WgradTcArgs {
+    float *dw;        // [cout][9][cin], accumulated
+    int cin, cout, res;
+    int ncb, nob;     // 128-channel input blocks, NB-channel output blocks
+    int splits;       // K ranges per (input block, output block)
+    int ktiles;       // 64-pixel K tiles in all images
+    int nst;          // pipeline stages
+};
+
+constexpr int kWgradThreads = 192;
+
+template <int NB>
+__global__ void __launch_bounds__(kWgradThreads, 1)
+    conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmD0,
+                            const __grid_constant__ CUtensorMap tmD1, const __grid_constant__ CUtensorMap tmD2,
+                            WgradTcArgs a, int *err)
+{
+    static_assert(NB % 16 == 0 && 9 * NB <= 512, "one output block of every tap in TMEM");
+    constexpr int MAXST = 8;
+    constexpr uint32_t A_BYTES = 128 * 128;      // 128 channels x 64 pixels BF16
+    constexpr uint32_t B_BYTES = NB * 128;       // NB channels x 64 pixels BF16
+    constexpr uint32_t STAGE = A_BYTES + 9 * B_BYTES;
+    static_assert(STAGE % 1024 == 0, "1024-byte aligned stages (128-byte swizzle)");
+    constexpr uint32_t TMEM_COLS = 9 * NB <= 256 ? 256 : 512;
+    extern __shared__ __align__(1024) unsigned char wg_smem_raw[];
+    __shared__ __align__(8) uint64_t full[MAXST], empty[MAXST], accf, drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_s;
+    unsigned char *smem = wg_smem_raw + ((1024u - (hr_tma::smem_u32(wg_smem_raw) & 1023u)) & 1023u);
+    volatile int *abort = &abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nst = a.nst;
+    // this CTA's item: input block, output block, K range
+    const int cb = blockIdx.x % a.ncb, rest = blockIdx.x / a.ncb, ob = rest % a.nob, sp = rest / a.nob;
+    const int k0 = (int)((long long)sp * a.ktiles / a.splits), k1 = (int)((long long)(sp + 1) * a.ktiles / a.splits);
+    const int tiles_per_img = a.res * a.res / 64;
+    if (tid == 0) {
+        for (int i = 0; i < nst; ++i) {
+            hr_tma::mbar_init(&full[i], 1);
+            hr_tma::mbar_init(&empty[i], 1);
+        }
+        hr_tma::mbar_init(&accf, 1);
+        hr_tma::mbar_init(&drain, 1);
+        abort_s = 0;
+        hr_tma::fence_mbar_init();
+    }
+    if (warp == 1) hr_tc::tmem_alloc(&tmem_base, TMEM_COLS);
+    hr_tc::fence_before_sync();
+    __syncthreads();
+    hr_tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    if (k1 > k0) {
+        if (warp == 0) {
+            if (lane == 0) {   // producer: per K tile the x tile and the 9 shifted dy tiles
+                int it = 0;
+                for (int kt = k0; kt < k1 && !*abort; ++kt, ++it) {
+                    const int s = it % nst, k = it / nst;
+                    if (k >= 1 && !tmaconv::wait(&empty[s], (k - 1) & 1, abort)) break;
+                    unsigned char *base = smem + s * STAGE;
+                    const int n = kt / tiles_per_img, p0 = (kt - n * tiles_per_img) * 64;
+                    hr_tma::mbar_arrive_expect_tx(&full[s], STAGE);
+                    hr_tma::load_4d(base, &tmX, &full[s], p0, n, cb * 128, 0);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ty = tap / 3 - 1, tx = tap % 3 - 1;   // off(tap) = (ty, tx)
+                        const CUtensorMap *tm = tx < 0 ? &tmD0 : (tx == 0 ? &tmD1 : &tmD2);
+                        hr_tma::load_4d(base + A_BYTES + tap * B_BYTES, tm, &full[s], p0 - ty * a.res, n, ob * NB, 0);
+                    }
+                }
+                if (*abort) {   // copies still in flight land before the CTA leaves (bounded)
+                    for (int j = it - nst < 0 ? 0 : it - nst; j < it; ++j)
+                        (void)hr_tma::mbar_wait(&full[j % nst], (j / nst) & 1);
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {   // MMA issuer: D[:, tap * NB ..] += A B_tap^T, 4 K steps of 16 pixels
+                constexpr uint32_t idesc = hr_tc::idesc_bf16(128, NB);
+                int it = 0;
+                bool ok = true;
+                for (int kt = k0; kt < k1 && !*abort; ++kt, ++it) {
+                    const int s = it % nst, k = it / nst;
+                    if (!tmaconv::wait(&full[s], k & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    hr_tc::fence_after_sync();
+                    const uint32_t sa = hr_tma::smem_u32(smem + s * STAGE);
+                    const uint64_t ad = hr_tc::smem_desc_swz(sa, 128);
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const uint64_t bd = hr_tc::smem_desc_swz(sa + A_BYTES + tap * B_BYTES, 128);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            hr_tc::mma_bf16(tb + (uint32_t)(tap * NB), ad + 2u * kk, bd + 2u * kk, idesc,
+                                            (kt > k0 || kk > 0) ? 1u : 0u);
+                    }
+                    hr_tc::commit(&empty[s]);
+                }
+                if (ok) hr_tc::commit(&accf);
+            }
+        } else {   // epilogue: warps 2-5, TMEM lane quadrant warp % 4 = 32 input channels
+            const int quad = warp & 3;
+            const bool got = tmaconv::wait(&accf, 0, abort);
+            if (__all_sync(0xffffffffu, got)) {
+                hr_tc::fence_after_sync();
+                const int c = cb * 128 + quad * 32 + lane;
+                for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+                    for (int j0 = 0; j0 < NB; j0 += 16) {
+                        float v[16];
+                        hr_tc::ld16(tb + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tap * NB + j0), v);
+                        if (c < a.cin) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const int o = ob * NB + j0 + j;
+                                if (o < a.cout) atomicAdd(a.dw + ((size_t)o * 9 + tap) * a.cin + c, v[j]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // an MMA thread that gave up may leave MMAs in flight: let them finish before TMEM is freed
+    hr_tc::fence_before_sync();
+    __syncthreads();
+    if (*abort) {
+        if (tid == 32) {
+            hr_tc::commit(&drain);   // arrives once every MMA issued so far has completed
+            (void)hr_tma::mbar_wait(&drain, 0);
+        }
+        if (tid == 0) atomicExch(err, 1);
+        __syncthreads();
+    }
+    hr_tc::fence_after_sync();
+    if (warp == 1) hr_tc::tmem_dealloc(tb, TMEM_COLS);
+}
+
+}  // namespace hr_cnn
