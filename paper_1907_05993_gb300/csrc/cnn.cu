@@ -189,6 +189,75 @@ __global__ void relu_bwd_kernel(const float *dpost, int ds, int dof, const bf16 
     }
 }
 
+// The ReLU backward, the bias gradient and the planar copies of the tcgen05 weight gradients in one
+// pass: dpre[p][c] = BF16(dpost[p][c] if out[p][c] > 0 else 0) (dense [P][C]); db[c] += sum_p dpre[p][c];
+// dk[c][q] = dpre[q + s_k][c] (s_k = +1, 0, -1; zero past the row ends).  A block walks tiles of 64
+// pixels x 32 channels (with the two halo pixels; C, ds, dof, os and oo multiples of 8; P a multiple
+// of 64), keeps its bias sums in registers and adds them to db once (few atomics per address).
+__global__ void __launch_bounds__(256) relu_bwd_planar_kernel(const float *dpost, int ds, int dof, const bf16 *out,
+                                                              int os, int oo, int C, int P, int res, bf16 *dpre,
+                                                              bf16 *d0, bf16 *d1, bf16 *d2, float *db)
+{
+    __shared__ unsigned short tile[66][34];
+    __shared__ float bsum[64][33];
+    const int c0 = blockIdx.y * 32, t = threadIdx.x;
+    float part[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // channels c0 + (t & 3) * 8 + j of this thread's centre pixels
+    unsigned short *dk[3] = {reinterpret_cast<unsigned short *>(d0), reinterpret_cast<unsigned short *>(d1),
+                             reinterpret_cast<unsigned short *>(d2)};
+    for (int tq = blockIdx.x; tq < P / 64; tq += gridDim.x) {
+        const int q0 = tq * 64;
+        for (int i = t; i < 66 * 4; i += 256) {   // 66 pixels x 4 groups of 8 channels
+            const int r = i >> 2, g = i & 3, q = q0 - 1 + r, c = c0 + g * 8;
+            __align__(16) unsigned short h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (q >= 0 && q < P && c < C) {
+                const uint4 ov = *reinterpret_cast<const uint4 *>(out + (size_t)q * os + oo + c);
+                const float4 g0 = *reinterpret_cast<const float4 *>(dpost + (size_t)q * ds + dof + c);
+                const float4 g1 = *reinterpret_cast<const float4 *>(dpost + (size_t)q * ds + dof + c + 4);
+                const bf16 *ob = reinterpret_cast<const bf16 *>(&ov);
+                const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bf16 bv = __float2bfloat16_rn(__bfloat162float(ob[j]) > 0.0f ? gv[j] : 0.0f);
+                    h[j] = *reinterpret_cast<const unsigned short *>(&bv);
+                }
+                if (r >= 1 && r <= 64) {   // a centre pixel: dpre and the bias sums
+                    *reinterpret_cast<uint4 *>(dpre + (size_t)q * C + c) = *reinterpret_cast<const uint4 *>(h);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const unsigned short u = h[j];
+                        part[j] += __bfloat162float(*reinterpret_cast<const bf16 *>(&u));
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) tile[r][g * 8 + j] = h[j];
+        }
+        __syncthreads();
+        for (int i = t; i < 3 * 32 * 8; i += 256) {   // (copy, channel, 8-pixel group)
+            const int k = i / 256, c = (i >> 3) & 31, g = i & 7;
+            if (c0 + c >= C) continue;
+            const int sft = 1 - k;
+            __align__(16) unsigned short h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int jj = g * 8 + j, x = (q0 + jj) % res;
+                h[j] = (x + sft >= 0 && x + sft < res) ? tile[jj + 1 + sft][c] : (unsigned short)0;
+            }
+            *reinterpret_cast<uint4 *>(dk[k] + (size_t)(c0 + c) * P + q0 + g * 8) = *reinterpret_cast<const uint4 *>(h);
+        }
+        __syncthreads();   // the tile is read before the next one is written
+    }
+    // a thread's centre pixels all lie in its channel group t & 3: reduce over the 64 threads of each group
+#pragma unroll
+    for (int j = 0; j < 8; ++j) bsum[t >> 2][(t & 3) * 8 + j] = part[j];
+    __syncthreads();
+    if (t < 32 && c0 + t < C) {
+        float s = 0.0f;
+        for (int k = 0; k < 64; ++k) s += bsum[k][t];
+        atomicAdd(db + c0 + t, s);
+    }
+}
+
 // db[o] += sum_p dpre[p][o]
 __global__ void bias_grad_kernel(const bf16 *dpre, int C, size_t P, float *db)
 {
@@ -674,18 +743,21 @@ int conv(hrebsd_ctx *ctx, const bf16 *x, int xs, int xo, int cin, const bf16 *w,
 }
 
 // Weight gradients on tcgen05 (planar copies, then the TMA-fed GEMM per tap); 1 = not applicable.
+// dy_planar: n->dyS already holds dy's three shifted planar copies.
 template <int NB>
 int wgrad_tc_t(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs, int xo, int cin, float *dw, int N,
-               int res, cudaStream_t st)
+               int res, bool dy_planar, cudaStream_t st)
 {
     hr_cnn_net *n = ctx->cnn;
     const int P = N * res * res;
     planar_shift_kernel<<<dim3((unsigned)((P + 63) / 64), (unsigned)((cin + 31) / 32)), 256, 0, st>>>(
         x, xs, xo, cin, P, res, nullptr, n->xT, nullptr);
     HR_LAUNCHED(ctx);
-    planar_shift_kernel<<<dim3((unsigned)((P + 63) / 64), (unsigned)((cout + 31) / 32)), 256, 0, st>>>(
-        dy, cout, 0, cout, P, res, n->dyS[0], n->dyS[1], n->dyS[2]);
-    HR_LAUNCHED(ctx);
+    if (!dy_planar) {
+        planar_shift_kernel<<<dim3((unsigned)((P + 63) / 64), (unsigned)((cout + 31) / 32)), 256, 0, st>>>(
+            dy, cout, 0, cout, P, res, n->dyS[0], n->dyS[1], n->dyS[2]);
+        HR_LAUNCHED(ctx);
+    }
     // planar [channel][image][pixel] as 4-D maps {pixels of an image, images, channels, 1}, 64-pixel boxes
     const uint64_t ip = (uint64_t)res * res * 2;
     const uint64_t dX[4] = {(uint64_t)res * res, (uint64_t)N, (uint64_t)cin, 1};
@@ -726,14 +798,19 @@ int wgrad_tc_t(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs,
     return HREBSD_OK;
 }
 
+bool wgrad_tc_ok(hrebsd_ctx *ctx, int cout, int res)
+{
+    return ctx->cnn_tc && ctx->cnn->xT && cout % 16 == 0 && (res == 8 || res == 16 || res == 32 || res == 64);
+}
+
 int wgrad(hrebsd_ctx *ctx, const bf16 *dy, int cout, const bf16 *x, int xs, int xo, int cin, float *dw, int N, int res,
-          cudaStream_t st)
+          cudaStream_t st, bool dy_planar = false)
 {
     hr_prof_begin(ctx, st);
     int e = 1;
-    if (ctx->cnn_tc && ctx->cnn->xT && cout % 16 == 0 && (res == 8 || res == 16 || res == 32 || res == 64))
-        e = cout % 32 == 0 ? wgrad_tc_t<32>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, st)
-                           : wgrad_tc_t<16>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, st);
+    if (wgrad_tc_ok(ctx, cout, res))
+        e = cout % 32 == 0 ? wgrad_tc_t<32>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, dy_planar, st)
+                           : wgrad_tc_t<16>(ctx, dy, cout, x, xs, xo, cin, dw, N, res, dy_planar, st);
     if (e == 1) {   // mma.sync over pixel chunks
         WgradArgs a;
         a.dy = dy;
@@ -842,14 +919,27 @@ int conv_bwd(hrebsd_ctx *ctx, int l, const float *dpost, int ds, int dof, float 
     layer_views(n, in, out);
     const LayerDef &L = kLayers[l];
     const size_t P = (size_t)B * L.res * L.res;
-    relu_bwd_kernel<<<grid_for(ctx, P * L.cout), 256, 0, st>>>(dpost, ds, dof, out[l].p, out[l].s, out[l].o, L.cout, P,
-                                                              n->dpre);
-    HR_LAUNCHED(ctx);
     int e;
-    if ((e = wgrad(ctx, n->dpre, L.cout, in[l].p, in[l].s, in[l].o, pad16(L.cin), n->G + n->w_off[l], B, L.res, st)))
-        return e;
-    bias_grad_kernel<<<grid_for(ctx, P), 256, 0, st>>>(n->dpre, L.cout, P, n->G + n->b_off[l]);
-    HR_LAUNCHED(ctx);
+    if (wgrad_tc_ok(ctx, L.cout, L.res)) {   // ReLU backward, bias gradient and dy's planar copies in one pass
+        const size_t tiles = P / 64, cap = (size_t)ctx->num_sms * 4;
+        relu_bwd_planar_kernel<<<dim3((unsigned)(tiles < cap ? tiles : cap), (unsigned)((L.cout + 31) / 32)), 256, 0,
+                                 st>>>(
+            dpost, ds, dof, out[l].p, out[l].s, out[l].o, L.cout, (int)P, L.res, n->dpre, n->dyS[0], n->dyS[1],
+            n->dyS[2], n->G + n->b_off[l]);
+        HR_LAUNCHED(ctx);
+        if ((e = wgrad(ctx, n->dpre, L.cout, in[l].p, in[l].s, in[l].o, pad16(L.cin), n->G + n->w_off[l], B, L.res,
+                       st, true)))
+            return e;
+    } else {
+        relu_bwd_kernel<<<grid_for(ctx, P * L.cout), 256, 0, st>>>(dpost, ds, dof, out[l].p, out[l].s, out[l].o,
+                                                                  L.cout, P, n->dpre);
+        HR_LAUNCHED(ctx);
+        if ((e = wgrad(ctx, n->dpre, L.cout, in[l].p, in[l].s, in[l].o, pad16(L.cin), n->G + n->w_off[l], B, L.res,
+                       st)))
+            return e;
+        bias_grad_kernel<<<grid_for(ctx, P), 256, 0, st>>>(n->dpre, L.cout, P, n->G + n->b_off[l]);
+        HR_LAUNCHED(ctx);
+    }
     if (dx)
         return conv(ctx, n->dpre, L.cout, 0, L.cout, n->wd[l], nullptr, L.cin, dx, L.cin, 0, 1, 0, B, L.res, st,
                     n->wtd[l]);
