@@ -792,8 +792,8 @@ def run_cnn(args, rank, world, local_rank):
                          "tflops": flop * B / (res[0][0] / 1e3) / 1e12},
             "train_step": {"batch": 256, "ms_tcgen05": res[("train", 1)], "ms_mma_sync": res[("train", 0)],
                            "pairs_per_s": 256 / (res[("train", 1)] / 1e3),
-                           "note": "forward, loss, backward (weight gradients on mma.sync; input gradients of "
-                                   "11 of 13 layers on tcgen05 in the first column), Adam"}}
+                           "note": "forward, loss, backward, Adam; first column: forward, weight-gradient and (11 of 13 "
+                                   "layers) input-gradient convolutions on tcgen05"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -364,8 +364,13 @@ __global__ void __launch_bounds__(kWgradThreads, 1)
                 }
             }
         } else if (warp == 1) {
-            if (lane == 0) {   // MMA issuer: D[:, tap * NB ..] += A B_tap^T, 4 K steps of 16 pixels
-                constexpr uint32_t idesc = hr_tc::idesc_bf16(128, NB);
+            if (lane == 0) {   // MMA issuer: D += A B^T, 4 K steps of 16 pixels
+                // the nine B tiles are consecutive rows of one K-major matrix (tap, output channel): one
+                // MMA covers taps [0, T0) and, where 9 NB > 256, a second one taps [T0, 9)
+                constexpr int T0 = 9 * NB <= 256 ? 9 : 256 / NB;
+                constexpr uint32_t idesc0 = hr_tc::idesc_bf16(128, T0 * NB);
+                constexpr uint32_t idesc1 = hr_tc::idesc_bf16(128, T0 < 9 ? (9 - T0) * NB : 16);
+                static_assert((T0 * NB) % 16 == 0 && ((9 - T0) * NB) % 16 == 0, "MMA widths of 16-column steps");
                 int it = 0;
                 bool ok = true;
                 for (int kt = k0; kt < k1 && !*abort; ++kt, ++it) {
@@ -377,13 +382,13 @@ __global__ void __launch_bounds__(kWgradThreads, 1)
                     hr_tc::fence_after_sync();
                     const uint32_t sa = hr_tma::smem_u32(smem + s * STAGE);
                     const uint64_t ad = hr_tc::smem_desc_swz(sa, 128);
+                    const uint64_t bd0 = hr_tc::smem_desc_swz(sa + A_BYTES, 128);
+                    const uint64_t bd1 = hr_tc::smem_desc_swz(sa + A_BYTES + T0 * B_BYTES, 128);
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const uint64_t bd = hr_tc::smem_desc_swz(sa + A_BYTES + tap * B_BYTES, 128);
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            hr_tc::mma_bf16(tb + (uint32_t)(tap * NB), ad + 2u * kk, bd + 2u * kk, idesc,
-                                            (kt > k0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t acc = (kt > k0 || kk > 0) ? 1u : 0u;
+                        hr_tc::mma_bf16(tb, ad + 2u * kk, bd0 + 2u * kk, idesc0, acc);
+                        if (T0 < 9) hr_tc::mma_bf16(tb + (uint32_t)(T0 * NB), ad + 2u * kk, bd1 + 2u * kk, idesc1, acc);
                     }
                     hr_tc::commit(&empty[s]);
                 }
