@@ -2,9 +2,11 @@
 //
 // Section 2 normalises every pattern to zero mean before correlation and
 // Section 3.3 corrects the background before registration.  One CTA owns one
-// pattern and streams it four times (moments, mean, variance, output); the
-// pattern (at most a few hundred KB) stays in L2 between the passes, so HBM
-// sees one read and one write per pixel.
+// pattern: it reads it for the background moments, divides it by the fitted
+// quadric once (float-float) writing the quotient less a constant to the
+// output, then reads that back for the variance and the normalised output;
+// the pattern (at most a few hundred KB) stays in L2 between the passes, so
+// HBM sees about one read and one write per pixel.
 #include <math.h>
 
 #include "internal.cuh"
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
     __shared__ double coef[6];
     __shared__ float2 rowA[kMaxDim], rowB[kMaxDim];   // per row: c0 + c2 y + c5 y^2 and c1 + c4 y (hi, lo)
     __shared__ float2 colX[kMaxDim];                  // per column: x (hi, lo)
-    __shared__ int ok_flag;
+    __shared__ float rowY[kMaxDim];                   // per row: y (the correctly rounded FP32 coordinate)
     const size_t base = (size_t)blockIdx.x * H * W;
     const float *img = in + base;
     const int n = H * W;
@@ -117,7 +119,17 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
     // FP64: the quadric's coefficients come out of a poorly conditioned 6 x 6 system, and plain FP32
     // sums of ~128 terms would move the output by ~1e-4.
     constexpr int kChunk = 8;
-    // pass 1: quadric moments b_k = sum phi_k I (basis at the correctly rounded pixel coordinates)
+    if (flat) {   // the pixel coordinates, once per row and column
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            const ff x = pixel_coord(j, W);
+            colX[j] = make_float2(x.hi, x.lo);
+        }
+        for (int i = threadIdx.x; i < H; i += blockDim.x) rowY[i] = pixel_coord(i, H).hi;
+        __syncthreads();
+    }
+    // pass 1: quadric moments b_k = sum phi_k I (basis at the correctly rounded pixel coordinates);
+    // b_0 is the pattern's sum
+    double total = 0.0;
     if (flat) {
         double d[6] = {0, 0, 0, 0, 0, 0};
         for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
                 if (p < n) {
                     const int i = p / W, j = p - i * W;
                     float phi[6];
-                    basis6(__fdiv_rn((float)(2 * j + 1 - W), (float)W), __fdiv_rn((float)(2 * i + 1 - H), (float)H), phi);
+                    basis6(colX[j].x, rowY[i], phi);
                     const float v = img[p];
 #pragma unroll
                     for (int k = 0; k < 6; ++k) acc[k] = fmaf(phi[k], v, acc[k]);
@@ -138,13 +150,13 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
             for (int k = 0; k < 6; ++k) d[k] += (double)acc[k];
         }
         block_sum<6>(d, red);
+        total = d[0];
         if (threadIdx.x == 0) {
             for (int r = 0; r < 6; ++r) {
                 double c = 0.0;
                 for (int k = 0; k < 6; ++k) c += qi.ginv[r * 6 + k] * d[k];
                 coef[r] = c;
             }
-            ok_flag = 1;
         }
         __syncthreads();
         // per-row parts of the quadric in FP64, kept as hi + lo
@@ -154,10 +166,6 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
             const ff Bc = ff_from_double(coef[1] + y * coef[4]);
             rowA[i] = make_float2(A.hi, A.lo);
             rowB[i] = make_float2(Bc.hi, Bc.lo);
-        }
-        for (int j = threadIdx.x; j < W; j += blockDim.x) {
-            const ff x = pixel_coord(j, W);
-            colX[j] = make_float2(x.hi, x.lo);
         }
         __syncthreads();
     }
@@ -170,49 +178,72 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
         const ff A = {rowA[i].x, rowA[i].y}, Bc = {rowB[i].x, rowB[i].y};
         return ff_add(A, ff_mul(x, ff_add(Bc, ff_mul(x, C))));
     };
+    // the division is skipped when the fitted surface is not positive at every pixel (checked on the
+    // FP32 value of the quadric, whose sign differs from the hi + lo one only within rounding of zero)
+    bool use_fit = flat;
     if (flat) {
-        // the division is skipped when the fitted surface is not positive everywhere
-        int bad = 0;
-        for (int p = threadIdx.x; p < n; p += blockDim.x) bad |= !(fit_at(p).hi > 0.0f);
-        if (__syncthreads_or(bad) && threadIdx.x == 0) ok_flag = 0;
-        __syncthreads();
+        bool bad = false;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int i = p / W, j = p - i * W;
+            const float x = colX[j].x;
+            bad |= !(fmaf(x, fmaf(x, C.hi, rowB[i].x), rowA[i].x) > 0.0f);
+        }
+        use_fit = !__syncthreads_or(bad);
     }
-    const bool use_fit = flat && ok_flag;
 
-    // the pattern divided by the quadric, as hi + lo
+    // the pattern divided by the quadric, as hi + lo: q ~ v / f (within 2 units of the last place,
+    // from the correctly rounded reciprocal), the remainder v - q f.hi exact by fma, then the
+    // correction (remainder - q f.lo) / f; with the division by f.hi a product with the same
+    // reciprocal (its error lands ~2^-24 below the correction, itself ~2^-24 below q)
     auto value = [&](int p) -> ff {
         const float v = img[p];
         if (!use_fit) return {v, 0.0f};
         const ff f = fit_at(p);
-        const float q = __fdiv_rn(v, f.hi);
-        float r = __fmaf_rn(-q, f.hi, v);   // exact remainder of the correctly rounded quotient
+        const float rf = __frcp_rn(f.hi);
+        const float q = __fmul_rn(v, rf);
+        float r = __fmaf_rn(-q, f.hi, v);
         r = __fmaf_rn(-q, f.lo, r);
-        return two_sum(q, __fdiv_rn(r, f.hi));
+        return two_sum(q, __fmul_rn(r, rf));
     };
-
-    // pass 2: mean
+    // pass 2: the quotient less K (1 for the background-divided pattern, whose values lie near one;
+    // the mean intensity, rounded, for the raw one), d = (q.hi - K) + q.lo in FP32: the leading part
+    // cancels before rounding, so d keeps the float-float accuracy of q and the mean of d is small; d
+    // is stored in the output (the pattern is read before it is overwritten, by the same thread) and
+    // summed for the mean
+    if (!flat) {   // the raw pattern's sum for K
+        double t[1] = {0.0};
+        for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
+            float sv = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) {
+                const int p = p0 + c * blockDim.x;
+                if (p < n) sv += img[p];
+            }
+            t[0] += (double)sv;
+        }
+        block_sum<1>(t, red);
+        total = t[0];
+    }
+    const float K = use_fit ? 1.0f : (float)(total / n);
+    float *o = out + base;
     double m[1] = {0.0};
     for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
-        float sh = 0.0f, sl = 0.0f;
+        float sd = 0.0f;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             const int p = p0 + c * blockDim.x;
             if (p < n) {
                 const ff q = value(p);
-                sh += q.hi;
-                sl += q.lo;
+                const float d = __fadd_rn(__fsub_rn(q.hi, K), q.lo);
+                o[p] = d;
+                sd += d;
             }
         }
-        m[0] += (double)sh + (double)sl;
+        m[0] += (double)sd;
     }
     block_sum<1>(m, red);
-    const double mean = m[0] / n;
-    const ff mu = ff_from_double(mean);
-    // the quotient minus the mean, in FP32 at the end (both parts subtracted before the sum)
-    auto centred = [&](int p) -> float {
-        const ff q = value(p);
-        return __fadd_rn(__fsub_rn(q.hi, mu.hi), __fsub_rn(q.lo, mu.lo));
-    };
+    const double mean_d = m[0] / n, mean = mean_d + (double)K;
+    const float md = (float)mean_d;
     // pass 3: variance about the mean
     double v2[1] = {0.0};
     for (int p0 = threadIdx.x; p0 < n; p0 += kChunk * blockDim.x) {
@@ -221,18 +252,17 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(const float *__
         for (int c = 0; c < kChunk; ++c) {
             const int p = p0 + c * blockDim.x;
             if (p < n) {
-                const float d = centred(p);
+                const float d = __fsub_rn(o[p], md);
                 ss = fmaf(d, d, ss);
             }
         }
         v2[0] += (double)ss;
     }
     block_sum<1>(v2, red);
-    const double sd = sqrt(v2[0] / n);
-    const float inv = (sd > 0.0 && sd > 1e-6 * fabs(mean)) ? (float)(1.0 / sd) : 0.0f;
-    // pass 4: output (in and out may alias: every pixel is read before it is written by the same thread)
-    float *o = out + base;
-    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = centred(p) * inv;
+    const double sdv = sqrt(v2[0] / n);
+    const float inv = (sdv > 0.0 && sdv > 1e-6 * fabs(mean)) ? (float)(1.0 / sdv) : 0.0f;
+    // pass 4: output
+    for (int p = threadIdx.x; p < n; p += blockDim.x) o[p] = __fsub_rn(o[p], md) * inv;
 }
 
 // One pyramid level down: the 2x2 box mean, floor(H/2) x floor(W/2) (an odd
