@@ -916,18 +916,19 @@ __global__ void __launch_bounds__(256) demons_finalize_kernel(const float2 *u0, 
 // The fine level is H x W, 2h x 2w or one more row/column where the size did not halve (the extra row or
 // column samples past the coarse edge: the clamped edge value).  One CTA per fine row (blockIdx.x =
 // pair x H + row), threads along the row.
+// Grid-stride over the B H W fine pixels (row-major, so consecutive threads write consecutive pixels).
 __global__ void __launch_bounds__(256) prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B,
                                                       int h, int w, int H, int W)
 {
-    const int b = (int)(blockIdx.x / (unsigned)H), i = (int)(blockIdx.x - (unsigned)b * H);
-    if (b >= B) return;
-    const float2 *src = uc + (size_t)b * h * w;
-    float2 *dst = uf + ((size_t)b * H + i) * W;
-    const float y = ((float)i + 0.5f) * 0.5f - 0.5f;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    const size_t total = (size_t)B * H * W;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = idx / (unsigned)W;   // fine row over all pairs
+        const int j = (int)(idx - r * (unsigned)W);
+        const int b = (int)(r / (unsigned)H), i = (int)(r - (size_t)b * H);
+        const float y = ((float)i + 0.5f) * 0.5f - 0.5f;
         const float x = ((float)j + 0.5f) * 0.5f - 0.5f;
-        const float2 v = bilinear2_clamped(src, h, w, x, y);
-        dst[j] = make_float2(2.0f * v.x, 2.0f * v.y);
+        const float2 v = bilinear2_clamped(uc + (size_t)b * h * w, h, w, x, y);
+        uf[idx] = make_float2(2.0f * v.x, 2.0f * v.y);
     }
 }
 
@@ -1460,11 +1461,10 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 if ((e2 = launch_level(ctx, a, st))) return e2;
                 if (l > 0) {
                     const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
-                    if ((long long)B * Hf > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
-                    const unsigned rows = (unsigned)B * (unsigned)Hf;
-                    const int threads = Wf >= 256 ? 256 : (Wf + 31) / 32 * 32;
+                    const size_t px = (size_t)B * Hf * Wf, blocks = (px + 255) / 256, cap = (size_t)ctx->num_sms * 16;
                     hr_prof_begin(ctx, st);
-                    prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
+                    prolong_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(
+                        (const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
                     hr_prof_end(ctx, PROF_DEMONS_AUX, st);
                     HR_LAUNCHED(ctx);
                 }
@@ -1570,11 +1570,10 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 return e2;
             if (l > 0) {
                 const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
-                if ((long long)B * Hf > 0x7fffffffLL) return HREBSD_EINVAL;   // one CTA per fine row
-                const unsigned rows = (unsigned)B * (unsigned)Hf;
-                const int threads = Wf >= 256 ? 256 : (Wf + 31) / 32 * 32;
+                const size_t px = (size_t)B * Hf * Wf, blocks = (px + 255) / 256, cap = (size_t)ctx->num_sms * 16;
                 hr_prof_begin(ctx, st);
-                prolong_kernel<<<rows, threads, 0, st>>>((const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
+                prolong_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>((const float2 *)uout,
+                                                                                       (float2 *)u0, B, h, w, Hf, Wf);
                 hr_prof_end(ctx, PROF_DEMONS_AUX, st);
                 HR_LAUNCHED(ctx);
             }

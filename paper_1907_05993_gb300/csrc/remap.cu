@@ -4,9 +4,10 @@
 // projection of R^T r', r' = (x' - xpc, y' - ypc, Z*): the reference point
 // that Eq. 2 maps onto x' under the pure rotation R.  The value is a Keys
 // (1981) cubic convolution (a = -0.5) over 4x4 reference pixels with
-// replicated borders.  One thread per output pixel, one CTA per output row;
-// the references (a few grains) are gathered through the read-only path and
-// stay in L2, so HBM traffic is the 4 B written per pixel.
+// replicated borders.  One thread per output pixel of a row; a persistent
+// grid walks the rows of all pairs; the references (a few grains) are
+// gathered through the read-only path and stay in L2, so HBM traffic is the
+// 4 B written per pixel.
 #include "internal.cuh"
 
 namespace {
@@ -22,15 +23,15 @@ __device__ __forceinline__ void keys_weights(float t, float *wt)
     wt[3] = ((a * s3 - 5.0f * a) * s3 + 8.0f * a) * s3 - 4.0f * a;
 }
 
-// One CTA per output row (blockIdx.x = pair x H + row, all index arithmetic
-// 32-bit and per CTA), threads along the row; R^T of the pair is read once per
-// CTA and kept in FP32 registers.
+// A CTA walks output rows (row = pair x H + i, all index arithmetic 32-bit
+// and per row), threads along the row; R^T of the pair is read once per row
+// and kept in FP32 registers.
 __global__ void __launch_bounds__(256) remap_kernel(const float *__restrict__ ref, const int32_t *__restrict__ ref_idx,
                                                     const double *__restrict__ Rf, int B, int H, int W, float xpc,
                                                     float ypc, float zs, float *__restrict__ out)
 {
-    const int b = (int)(blockIdx.x / (unsigned)H), i = (int)(blockIdx.x - (unsigned)b * H);
-    if (b >= B) return;
+  for (unsigned row = blockIdx.x; row < (unsigned)B * (unsigned)H; row += gridDim.x) {
+    const int b = (int)(row / (unsigned)H), i = (int)(row - (unsigned)b * H);
     float r[9];
     const double *R = Rf + (size_t)b * 9;
 #pragma unroll
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(256) remap_kernel(const float *__restrict__ re
         }
         orow[j] = acc;
     }
+  }
 }
 
 }  // namespace
@@ -81,8 +83,9 @@ extern "C" int hrebsd_remap(hrebsd_ctx *ctx, const float *ref, const int32_t *re
     const long long rows = (long long)B * H;
     if (rows > 0x7fffffffLL || (long long)H * W > 0x7fffffffLL) return HREBSD_EINVAL;
     const int threads = W >= 256 ? 256 : (W + 31) / 32 * 32;
+    const long long cap = (long long)ctx->num_sms * (2048 / threads);   // resident CTAs
     hr_prof_begin(ctx, hr_stream(stream));
-    remap_kernel<<<(unsigned)rows, threads, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
+    remap_kernel<<<(unsigned)(rows < cap ? rows : cap), threads, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
                                                       (float)(g->ystar * H), (float)(g->zstar * W), remapped);
     hr_prof_end(ctx, PROF_REMAP, hr_stream(stream));
     HR_LAUNCHED(ctx);
