@@ -91,13 +91,25 @@ int hrebsd_device_error(hrebsd_ctx *ctx);
  * point, or when the caller's stream is itself capturing (the launches then go
  * into the caller's graph).  Same results either way. */
 #define HREBSD_OPT_GRAPHS 2
-/* HREBSD_OPT_CNN_TC (value 0/1, default 1): run the forward 3x3 convolutions
- * of the learned initialiser on the fifth-generation tensor cores (input halo
- * tiles by TMA, tcgen05 MMAs into tensor memory); 0 selects the mma.sync
- * kernels.  Gradients always use the mma.sync kernels.  Same operands and
- * FP32 accumulation; the sums are grouped differently, so results agree to
- * FP32 rounding before the BF16 store. */
+/* HREBSD_OPT_CNN_TC (value 0/1, default 1): run the 3x3 convolutions of the
+ * learned initialiser on the fifth-generation tensor cores (input halo tiles
+ * by TMA, tcgen05 MMAs into tensor memory): the forward pass, the weight
+ * gradients, and the input gradients of every layer whose channel counts the
+ * tcgen05 kernel takes (the others run the mma.sync kernel); 0 selects the
+ * mma.sync kernels for all of them.
+ * Same operands and FP32 accumulation; the sums are grouped differently, so
+ * results agree to FP32 rounding before the BF16 store. */
 #define HREBSD_OPT_CNN_TC 3
+/* HREBSD_OPT_TEX_GATHER (value 0/1, default 1): the row-sweep demons
+ * iteration (tile shapes 5 and 6) reads the four moving-image pixels of each
+ * bilinear sample with one texture gather from a copy of the level's
+ * reference images in a CUDA array held by the context (one array per level
+ * width, grown when a call needs more rows; growing it synchronises the device
+ * and drops the cached graphs); 0 selects plain global loads.  The same four
+ * values enter the same arithmetic, so the results are identical.  Levels whose
+ * R x h rows exceed the device's texture-gather height, and the
+ * allocation-free entry point, use the plain loads. */
+#define HREBSD_OPT_TEX_GATHER 4
 int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value);
 
 /* Tracing: per kernel class, CUDA-event time of every launch (events are

@@ -20,7 +20,7 @@ __all__ = [
     "HrebsdError", "load", "hrebsd_geometry", "hrebsd_demons_params", "demons_params", "hrebsd_create",
     "hrebsd_destroy", "hrebsd_status_string", "hrebsd_launch_count", "hrebsd_preprocess_batch",
     "hrebsd_demons_register_batch", "hrebsd_demons_register_batch_noalloc", "hrebsd_fit_rotation", "hrebsd_remap", "hrebsd_xcf_roi_batch",
-    "hrebsd_solve_F", "hrebsd_elastic", "elastic_params", "NORM_DET1", "NORM_TRACTION_FREE", "hrebsd_cnn_save", "hrebsd_cnn_load", "hrebsd_gauss_taps", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "TILE_VARIANTS",
+    "hrebsd_solve_F", "hrebsd_elastic", "elastic_params", "NORM_DET1", "NORM_TRACTION_FREE", "hrebsd_cnn_save", "hrebsd_cnn_load", "hrebsd_gauss_taps", "hrebsd_strain_stress", "hrebsd_profile_enable", "hrebsd_profile_read", "hrebsd_device_error", "hrebsd_set_option", "OPT_NO_TMA", "OPT_GRAPHS", "OPT_CNN_TC", "OPT_TEX_GATHER", "TILE_VARIANTS",
     "hrebsd_autotune", "hrebsd_probe_fp32_fma", "hrebsd_polar_batch", "hrebsd_tc_selftest", "hrebsd_wait_selftest", "hrebsd_cnn_get_state", "hrebsd_cnn_set_state", "hrebsd_fit_quality", "hrebsd_bandpass_batch", "hrebsd_mean_pattern",
     "hrebsd_background_batch", "hrebsd_shift_zoom_batch", "hrebsd_ssim_warped", "hrebsd_set_tile_variant", "hrebsd_get_tile_variant", "hrebsd_field_resample", "PROF_CLASSES", "PAIR_CAPPED", "PAIR_NONFINITE", "PAIR_FIT_FAILED",
 ]
@@ -198,6 +198,7 @@ def hrebsd_launch_count(ctx) -> int:
 OPT_NO_TMA = 1
 OPT_GRAPHS = 2
 OPT_CNN_TC = 3
+OPT_TEX_GATHER = 4
 
 
 def hrebsd_device_error(ctx):

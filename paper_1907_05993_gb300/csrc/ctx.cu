@@ -230,6 +230,10 @@ int hrebsd_destroy(hrebsd_ctx *ctx)
         if (b.ptr) cudaFree(b.ptr);
     hr_cnn_destroy(ctx);
     for (auto &g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+    for (auto &m : ctx->mtex) {
+        cudaDestroyTextureObject(m.tex);
+        cudaFreeArray(m.arr);
+    }
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto &p : ctx->pending) {
         cudaEventDestroy(p.a);
@@ -277,6 +281,7 @@ int hrebsd_set_option(hrebsd_ctx *ctx, int option, int value)
     case HREBSD_OPT_NO_TMA: ctx->no_tma = value ? 1 : 0; return HREBSD_OK;
     case HREBSD_OPT_GRAPHS: ctx->graphs = value ? 1 : 0; return HREBSD_OK;
     case HREBSD_OPT_CNN_TC: ctx->cnn_tc = value ? 1 : 0; return HREBSD_OK;
+    case HREBSD_OPT_TEX_GATHER: ctx->tex_gather = value ? 1 : 0; return HREBSD_OK;
     default: return HREBSD_EINVAL;
     }
 }

@@ -77,6 +77,9 @@ struct IterArgs {
     int in_is_s;
     float alpha2;
     Taps taps;
+    // row sweep: texture over the level's reference images stacked as R x h rows of w (a CUDA array;
+    // reference r's row y is texture row r h + y), 0 = plain loads from Mref
+    unsigned long long mtex = 0;
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
@@ -110,6 +113,17 @@ __device__ __forceinline__ void warp_cell_f(float q, float u, float m2, int &i, 
     const float xc = fminf(fmaxf(x, 0.0f), m2);
     f = __saturatef(fr + (x - xc));
     i = (int)xc;
+}
+
+// warp_cell_f with the cell index returned as a float (integer-valued, exact): the texture
+// coordinate of the cell's four-texel gather.  Same cell and weight.
+__device__ __forceinline__ void warp_cell_ff(float q, float u, float m2, float &xc, float &f)
+{
+    const float n = floorf(-u);
+    const float fr = -u - n;
+    const float x = q + n;
+    xc = fminf(fmaxf(x, 0.0f), m2);
+    f = __saturatef(fr + (x - xc));
 }
 
 // Bilinear sample of M at the point (qx - ux, qy - uy), clamped to the image;
@@ -1045,13 +1059,13 @@ static_assert(HREBSD_TILE_VARIANTS == kTileVariants, "tile variants");
 // windows are 2r + 1 = 7 rows, the rows of one step).
 bool strip_ok(int rad, int w) { return rad == 3 && (w == 64 || w == 128 || w == 256); }
 
-template <int NT, bool IN_S, bool LOOP>
-int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c, int max_items, cudaStream_t st)
+template <int NT, bool IN_S, bool LOOP, bool TEX>
+int launch_strip_tt(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c, int max_items, cudaStream_t st)
 {
     using G = strip::Geo<3, NT>;
     static int configured_dev = -1;
     static int occ = 0;
-    auto k = strip::demons_strip_kernel<3, NT, IN_S, LOOP>;
+    auto k = strip::demons_strip_kernel<3, NT, IN_S, LOOP, TEX>;
     if (configured_dev != ctx->device) {
         HR_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES));
         HR_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, G::BYTES));
@@ -1066,6 +1080,13 @@ int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c,
     hr_prof_end(ctx, PROF_ITER, st);
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
+}
+// The moving image by texture gathers when a.mtex is set, else by plain loads.
+template <int NT, bool IN_S, bool LOOP>
+int launch_strip_t(hrebsd_ctx *ctx, const IterArgs &a, const strip::LoopArgs &c, int max_items, cudaStream_t st)
+{
+    return a.mtex ? launch_strip_tt<NT, IN_S, LOOP, true>(ctx, a, c, max_items, st)
+                  : launch_strip_tt<NT, IN_S, LOOP, false>(ctx, a, c, max_items, st);
 }
 
 // One iteration over the active pairs.  a.tiles must be 1 (one SSD partial per pair); a.in is s_k,
@@ -1137,7 +1158,7 @@ int strip_capacity_t(hrebsd_ctx *ctx)
     static int configured_dev = -1;
     static int occ = 0;
     if (configured_dev != ctx->device) {
-        auto k = strip::demons_strip_kernel<3, NT, true, true>;
+        auto k = strip::demons_strip_kernel<3, NT, true, true, true>;   // the same resources without TEX
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::BYTES) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, G::BYTES) != cudaSuccess)
             occ = 0;
@@ -1209,6 +1230,77 @@ int hr_graph_run(hrebsd_ctx *ctx, const hr_graph_key &key, cudaStream_t st, Emit
     hit->last = ++ctx->graph_clock;
     HR_CHECK(cudaGraphLaunch(hit->exec, st));
     ctx->launches += hit->nodes;
+    return HREBSD_OK;
+}
+
+// Texture over the reference images of a level (R images of h x w, stacked as R h rows of w) for the
+// row sweep's four-texel gathers, which read CUDA arrays only.  The context keeps one array per level
+// width and grows it when a call needs more rows; every call first copies its references in, on its
+// stream, so the array holds them when the level's launches run (calls on one context are serialised
+// like its workspace).  *tex = 0 selects plain loads: option off, R h above the device's gather
+// height, a stream that is being captured (no allocation or synchronisation inside a capture), or an
+// array that could not be allocated.  Growing an array synchronises the device (the old one may be in
+// use) and drops the cached graphs (their launches name the old texture).
+int hr_ref_texture(hrebsd_ctx *ctx, const float *ref, int R, int h, int w, cudaStream_t st, unsigned long long *tex)
+{
+    *tex = 0;
+    if (!ctx->tex_gather) return HREBSD_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return HREBSD_OK;
+    }
+    if (!ctx->tex_max_rows) {
+        int mh = 0, mw = 0;
+        HR_CHECK(cudaDeviceGetAttribute(&mh, cudaDevAttrMaxTexture2DGatherHeight, ctx->device));
+        HR_CHECK(cudaDeviceGetAttribute(&mw, cudaDevAttrMaxTexture2DGatherWidth, ctx->device));
+        ctx->tex_max_rows = mw >= 256 && mh > 0 ? mh : -1;
+    }
+    const long long rows = (long long)R * h;
+    if (ctx->tex_max_rows < 0 || rows > ctx->tex_max_rows || w > 256) return HREBSD_OK;
+    size_t mi = ctx->mtex.size();
+    for (size_t i = 0; i < ctx->mtex.size(); ++i)
+        if (ctx->mtex[i].w == w) mi = i;
+    if (mi == ctx->mtex.size() || ctx->mtex[mi].rows < rows) {
+        long long cap_rows = rows > 8LL * h ? rows : 8LL * h;   // room for 8 references from the start
+        if (mi < ctx->mtex.size()) {
+            const long long twice = 2LL * ctx->mtex[mi].rows;
+            if (twice > cap_rows) cap_rows = twice;
+            HR_CHECK(cudaDeviceSynchronize());
+            for (auto &g : ctx->graph_cache) cudaGraphExecDestroy(g.exec);
+            ctx->graph_cache.clear();
+            cudaDestroyTextureObject(ctx->mtex[mi].tex);
+            cudaFreeArray(ctx->mtex[mi].arr);
+            ctx->mtex.erase(ctx->mtex.begin() + mi);
+        }
+        if (cap_rows > ctx->tex_max_rows) cap_rows = ctx->tex_max_rows;
+        hr_mtex m{w, (int)cap_rows, nullptr, 0};
+        const cudaChannelFormatDesc fd = cudaCreateChannelDesc<float>();
+        if (cudaMallocArray(&m.arr, &fd, (size_t)w, (size_t)cap_rows, cudaArrayTextureGather) != cudaSuccess) {
+            cudaGetLastError();
+            return HREBSD_OK;
+        }
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = m.arr;
+        cudaTextureDesc td = {};
+        td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        cudaTextureObject_t to = 0;
+        const cudaError_t ce = cudaCreateTextureObject(&to, &rd, &td, nullptr);
+        if (ce != cudaSuccess) {
+            cudaFreeArray(m.arr);
+            return hr_cuda_error(ce, "cudaCreateTextureObject", __FILE__, __LINE__);
+        }
+        m.tex = to;
+        ctx->mtex.push_back(m);
+        mi = ctx->mtex.size() - 1;
+    }
+    HR_CHECK(cudaMemcpy2DToArrayAsync(ctx->mtex[mi].arr, 0, 0, ref, (size_t)w * 4, (size_t)w * 4, (size_t)rows,
+                                      cudaMemcpyDeviceToDevice, st));
+    *tex = ctx->mtex[mi].tex;
     return HREBSD_OK;
 }
 
@@ -1425,6 +1517,9 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         // (more pairs than CTAs: per-iteration launches re-balance the uneven counts every iteration)
         const bool use_loop = use_strip && cap > 1 &&
                               (var == kLoopVariant || (var == kStripVariant && B <= strip_capacity(ctx, w)));
+        // the row sweep's moving image through texture gathers (not in the allocation-free call)
+        unsigned long long mtex = 0;
+        if (use_strip && !given && (e = hr_ref_texture(ctx, rl[l], R, h, w, st, &mtex))) return e;
         CUtensorMap tmS[3], tmF;
         const bool use_tma = !use_level && !use_strip && rad > 0 && !ctx->no_tma && cap > 1 &&
                              encode_maps(rad, var, (const float2 *)s0, (const float2 *)s1, (const float2 *)u0, tl[l],
@@ -1499,6 +1594,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 a.taps = taps;
                 a.px_count = hr_prof_pixiters(ctx);
                 a.err = ctx->d_err;
+                a.mtex = use_strip ? mtex : 0;
                 if (use_strip) e2 = launch_strip(ctx, k > 0, a, B, st);
                 else if (tma_k) e2 = dispatch_iter_tma(ctx, rad, var, k > 0, k > 0 ? tmS[k & 1] : tmS[2], tmF, a, B * tiles, st);
                 else e2 = dispatch_iter(ctx, rad, a, B * tiles, st);
@@ -1547,6 +1643,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 a.taps = taps;
                 a.px_count = hr_prof_pixiters(ctx);
                 a.err = ctx->d_err;
+                a.mtex = mtex;
                 strip::LoopArgs c;
                 c.s0 = (float2 *)s0;
                 c.s1 = (float2 *)s1;
@@ -1586,7 +1683,7 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
         // graph key: everything the launches of this level depend on
         hr_graph_key key{};
         const void *kp[] = {ref_idx, tl[l], rl[l], u0, s0, s1, uout, part, hist, lists, iters, status, field,
-                            ctx->d_err};
+                            ctx->d_err, (const void *)(uintptr_t)mtex};
         static_assert(sizeof(kp) / sizeof(kp[0]) <= sizeof(key.p) / sizeof(key.p[0]), "graph key");
         for (size_t i = 0; i < sizeof(kp) / sizeof(kp[0]); ++i) key.p[i] = kp[i];
         const int ki[] = {l, L, B, h, w, cap, cap_max, rad, var, (int)use_tma, p->stop_window, (int)use_strip,
@@ -1722,6 +1819,11 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
             tune_fill_kernel<<<ctx->num_sms * 8, 256, 0, st>>>((float *)img, Bt + 1, (float2 *)s0, (float2 *)s1,
                                                                Bt, h, w);
             HR_LAUNCHED(ctx);
+            unsigned long long mtex = 0;   // the row sweep's moving image as in a registration
+            if (strip_ok(rad, w)) {
+                const int e3 = hr_ref_texture(ctx, ref, 1, h, w, st, &mtex);
+                if (e3) return e3;
+            }
             float best = 0.0f;
             int best_v = 0;
             for (int v = 0; v < kTileVariants; ++v) {
@@ -1753,6 +1855,7 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 a.in_is_s = 1;
                 a.alpha2 = p->alpha * p->alpha;
                 a.taps = taps;
+                a.mtex = sv ? mtex : 0;
                 // 2 warm-up iterations, then the best of 3 timed batches of 4 (the loop form: one
                 // warm-up launch, then the best of 3 launches of kLoopCap - 1 iterations each)
                 constexpr int kWarm = 2, kBatch = 4, kRounds = 3;

@@ -8,9 +8,10 @@
 //   x pass of G_f on the step's s rows, for the warp's own columns -> RX rows;
 //   per column, in registers: the y pass of G_f over a rolling window of the
 //     last 2r + 1 RX rows gives u (lagging the input by r rows); the bilinear
-//     gathers of the moving image at x - u are issued for all R rows before
-//     any of them is used, then the force of Eq. 1 (test-image rows staged in
-//     shared memory)                                            -> du rows;
+//     gathers of the moving image at x - u (with TEX one texture gather of the
+//     cell's four pixels from a CUDA-array copy of the references, else four
+//     loads) are issued for all R rows before any of them is used, then the
+//     force of Eq. 1 (test-image rows staged in shared memory)  -> du rows;
 //   one CTA barrier (the du rows' x pass reads r columns of the neighbouring
 //     warps);
 //   x pass of G_u on the du rows, for the warp's own columns     -> DX rows;
@@ -123,7 +124,7 @@ __device__ __forceinline__ void run_x_halo(const float2 *row, int c0, float2 *ou
     for (int o = 0; o < RUN; o += 2) out4[o / 2] = make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
 }
 
-template <int RAD, int NT, bool IN_S, bool LOOP>
+template <int RAD, int NT, bool IN_S, bool LOOP, bool TEX>
 __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, LoopArgs c)
 {
     static_assert(!LOOP || IN_S, "the loop form runs the iterations k >= 1, which read s_k");
@@ -226,7 +227,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
         const int pair = a.active[item];
         const int next_pair = !LOOP && item + (int)gridDim.x < n_active ? a.active[item + gridDim.x] : -1;
         int next_item = item + (int)gridDim.x;
-        const float *M = a.Mref + (size_t)__ldg(a.ref_idx + pair) * plane;
+        const int ref = __ldg(a.ref_idx + pair);
+        const float *M = a.Mref + (size_t)ref * plane;
+        // TEX: texture row of the cell's upper row y0 is ref h + y0, and the gather of the texels
+        // (x0, y0) .. (x0 + 1, y0 + 1) is taken at the coordinate (x0 + 1, ref h + y0 + 1)
+        const float yt = (float)(ref * h) + 1.0f;
         const float2 *u0 = a.in + (size_t)pair * plane;   // the level's initial field when !IN_S
         const float *fp = fsrc_of(pair);
       for (int kit = K_FIRST;; ++kit) {   // LOOP: the pair's iterations; otherwise the one sweep
@@ -320,14 +325,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) demons_strip_kernel(IterArgs a, 
                     const int yu = R * k + i - RAD;
                     // row coordinate as a float (exact integers); rows outside: any valid cell
                     const float yc = IN ? yk + (float)i : (float)min(max(yu, 0), h - 1);
-                    int x0, y0;
-                    warp_cell_f(tf_, ucur[i].x, mx2, x0, fxv[i]);
-                    warp_cell_f(yc, ucur[i].y, my2, y0, fyv[i]);
-                    const float *p = M + y0 * NT + x0;
-                    mA[i] = __ldg(p);
-                    mB[i] = __ldg(p + 1);
-                    mC[i] = __ldg(p + NT);
-                    mD[i] = __ldg(p + NT + 1);
+                    if constexpr (TEX) {
+                        // one gather returns (x0, y0 + 1), (x0 + 1, y0 + 1), (x0 + 1, y0), (x0, y0)
+                        float xc, ycl;
+                        warp_cell_ff(tf_, ucur[i].x, mx2, xc, fxv[i]);
+                        warp_cell_ff(yc, ucur[i].y, my2, ycl, fyv[i]);
+                        const float4 q = tex2Dgather<float4>(a.mtex, xc + 1.0f, ycl + yt, 0);
+                        mA[i] = q.w;
+                        mB[i] = q.z;
+                        mC[i] = q.x;
+                        mD[i] = q.y;
+                    } else {
+                        int x0, y0;
+                        warp_cell_f(tf_, ucur[i].x, mx2, x0, fxv[i]);
+                        warp_cell_f(yc, ucur[i].y, my2, y0, fyv[i]);
+                        const float *p = M + y0 * NT + x0;
+                        mA[i] = __ldg(p);
+                        mB[i] = __ldg(p + 1);
+                        mC[i] = __ldg(p + NT);
+                        mD[i] = __ldg(p + NT + 1);
+                    }
                 }
                 // the force of one row (scalar) ...
                 auto force1 = [&](int i, int yu) {

@@ -56,6 +56,13 @@ struct hr_graph_entry {
 struct hr_tune_entry {
     int h, w, var;
 };
+// Copy of a level's reference images in a CUDA array (rows R x h stacked, one array per level width)
+// behind a texture object, for the four-texel gathers of the row sweep (demons.cu).
+struct hr_mtex {
+    int w, rows;
+    cudaArray_t arr;
+    unsigned long long tex;
+};
 
 struct hrebsd_ctx {
     int device = 0;
@@ -67,7 +74,10 @@ struct hrebsd_ctx {
     int no_events = 0;   // set while a call must not create CUDA events
     int no_tma = 0;      // force the non-TMA demons iteration (testing, unsupported shapes)
     int graphs = 1;      // replay each registration level from a cached CUDA graph
-    int cnn_tc = 1;      // learned initialiser: forward 3x3 convolutions on tcgen05 (else mma.sync kernels)
+    int cnn_tc = 1;      // learned initialiser: 3x3 convolutions on tcgen05 (else mma.sync kernels)
+    int tex_gather = 1;  // row sweep: moving image by texture gathers from a CUDA array copy (else plain loads)
+    int tex_max_rows = 0;         // texture-gather array height limit of the device (0 = not queried)
+    std::vector<hr_mtex> mtex;    // reference arrays per level width
     cudaStream_t cap_stream = nullptr;   // private stream the graphs are captured on
     std::vector<hr_graph_entry> graph_cache;
     unsigned long long graph_clock = 0;

@@ -131,6 +131,33 @@ def test_level_in_one_launch_matches_row_sweep_with_stop_rule(torch, lib, pairs)
         assert np.array_equal(f5[:4], f5[4:8]) and np.array_equal(it5[:4], it5[-4:])
 
 
+def test_texture_gathers_match_plain_loads(torch, lib, pairs):
+    """The row sweep's moving image by texture gathers from the context's CUDA-array copy of the
+    references (the default) equals plain loads, per-iteration launches (shape 5) and the loop form
+    (shape 6), stop rule on.  Ten references, the pairs pointing at the last two: texture rows beyond
+    the array's first allocation (8 references), so the array grows between calls (device synchronised,
+    cached graphs dropped) and the row offset of a reference is exercised."""
+    params = lib.demons_params(4, [40] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
+    refs, tests, ridx = pairs
+    many = (np.concatenate([refs] * 5), tests, (ridx + 8).astype(np.int32))
+    for v in (5, 6):
+        res = {}
+        for tex in (0, 1):
+            ctx = lib.hrebsd_create(0)
+            lib.hrebsd_set_option(ctx, lib.OPT_TEX_GATHER, tex)
+            for l in range(4):
+                lib.hrebsd_set_tile_variant(ctx, 256 >> l, 256 >> l, v)
+            res[tex] = (_register(torch, lib, ctx, pairs, params), _register(torch, lib, ctx, many, params),
+                        _register(torch, lib, ctx, pairs, params))
+            lib.hrebsd_destroy(ctx)
+        for run in range(3):
+            for a, b in zip(res[0][run], res[1][run]):
+                assert np.array_equal(a, b), (v, run)
+        for a, b in zip(res[1][0], res[1][1]):
+            assert np.array_equal(a, b), v
+        assert res[1][0][1].max() > 5   # the stop rule ran
+
+
 def test_graph_replay_matches_direct_launches(torch, lib, pairs):
     """Stop rule on: the graph path (captured, then replayed from the cache) equals direct launches."""
     params = lib.demons_params(4, [60] * 4, 1.0, 1.0, 1.0, 1e-4, 5)
