@@ -926,24 +926,117 @@ __global__ void __launch_bounds__(256) demons_finalize_kernel(const float2 *u0, 
     }
 }
 
+// The same final field for levels NT = 64, 128 or 256 pixels wide at the radius 3, as a sweep down
+// the rows: one CTA of NT threads per pair (thread t owns column t).  Steps of 7 input rows are
+// loaded into a double-buffered shared-memory block with replicated halo columns (one barrier per
+// step); each thread's x pass of its column goes into a 7-row register window (row y in slot y mod 7,
+// the first row fills every slot, rows past the bottom repeat the last row), and the y pass of the
+// window gives output row y - 3.  Same taps in the same order as the tile kernel: the same values.
+template <int NT, bool PLANAR>
+__global__ void __launch_bounds__(NT) demons_finalize_sweep_kernel(const float2 *u0, const float2 *s0,
+                                                                   const float2 *s1, const int32_t *iters,
+                                                                   int levels, int level, float *uout, int B, int h,
+                                                                   Taps taps)
+{
+    constexpr int RAD = 3, R = 2 * RAD + 1, HO = 4, RST = NT + 2 * HO;
+    __shared__ __align__(16) float2 rows[2][R][RST];
+    const int t = threadIdx.x;
+    float2 tf[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) tf[k] = make_float2(taps.f[k], taps.f[k]);
+    const size_t plane = (size_t)h * NT;
+    const int nsteps = (h + RAD + R - 1) / R;   // input rows 0 .. h + 2 (past the bottom: row h - 1)
+    int buf = 0;
+    for (int pair = blockIdx.x; pair < B; pair += gridDim.x) {
+        const int n = iters[(size_t)pair * levels + level];
+        const float2 *src = (n == 0 ? u0 : ((n & 1) ? s1 : s0)) + (size_t)pair * plane;
+        auto put = [&](int y, float2 v) {
+            if (PLANAR) {
+                uout[(size_t)pair * 2 * plane + (size_t)y * NT + t] = v.x;
+                uout[(size_t)pair * 2 * plane + plane + (size_t)y * NT + t] = v.y;
+            } else {
+                reinterpret_cast<float2 *>(uout)[(size_t)pair * plane + (size_t)y * NT + t] = v;
+            }
+        };
+        if (n == 0) {   // no update was applied: u_0 itself
+            for (int y = 0; y < h; ++y) put(y, src[(size_t)y * NT + t]);
+            continue;
+        }
+        float2 win[R];
+        for (int k = 0; k < nsteps; ++k) {
+            float2 (*rb)[RST] = rows[buf];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const float2 v = src[(size_t)min(R * k + i, h - 1) * NT + t];
+                rb[i][HO + t] = v;
+                if (t == 0)
+#pragma unroll
+                    for (int j = 1; j <= RAD; ++j) rb[i][HO - j] = v;
+                if (t == NT - 1)
+#pragma unroll
+                    for (int j = 1; j <= RAD; ++j) rb[i][HO + NT - 1 + j] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                const int y = R * k + i;
+                float2 xa = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int j = 0; j < R; ++j) xa = ffma2(tf[j], rb[i][HO + t - RAD + j], xa);
+                win[i] = xa;   // row y in slot y mod R = i
+                if (y == 0) {
+#pragma unroll
+                    for (int j = 1; j < R; ++j) win[j] = xa;
+                }
+                const int yo = y - RAD;
+                if (yo >= 0 && yo < h) {
+                    // rows yo - 3 + j = y - 6 + j sit in slots (i + 1 + j) mod R
+                    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) acc = ffma2(tf[j], win[(i + 1 + j) % R], acc);
+                    put(yo, acc);
+                }
+            }
+            buf ^= 1;
+        }
+    }
+}
+
 // Prolongation (Section 1): fine(x_f) = 2 * bilinear(coarse, (x_f + 0.5)/2 - 0.5), interleaved fields.
 // The fine level is H x W, 2h x 2w or one more row/column where the size did not halve (the extra row or
-// column samples past the coarse edge: the clamped edge value).  One CTA per fine row (blockIdx.x =
-// pair x H + row), threads along the row.
-// Grid-stride over the B H W fine pixels (row-major, so consecutive threads write consecutive pixels).
+// column samples past the coarse edge: the clamped edge value).  Each CTA walks an equal run of
+// consecutive fine rows of all pairs (row = pair x H + i; the division per row, not per pixel), threads
+// along the row, so consecutive threads write consecutive pixels.
 __global__ void __launch_bounds__(256) prolong_kernel(const float2 *__restrict__ uc, float2 *__restrict__ uf, int B,
-                                                      int h, int w, int H, int W)
+                                                      int h, int w, int H, int W, size_t rows_per_cta)
 {
-    const size_t total = (size_t)B * H * W;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = idx / (unsigned)W;   // fine row over all pairs
-        const int j = (int)(idx - r * (unsigned)W);
+    const size_t total = (size_t)B * H;
+    const size_t r0 = (size_t)blockIdx.x * rows_per_cta;
+    const size_t r1 = r0 + rows_per_cta < total ? r0 + rows_per_cta : total;
+    for (size_t r = r0; r < r1; ++r) {
         const int b = (int)(r / (unsigned)H), i = (int)(r - (size_t)b * H);
         const float y = ((float)i + 0.5f) * 0.5f - 0.5f;
-        const float x = ((float)j + 0.5f) * 0.5f - 0.5f;
-        const float2 v = bilinear2_clamped(uc + (size_t)b * h * w, h, w, x, y);
-        uf[idx] = make_float2(2.0f * v.x, 2.0f * v.y);
+        const float2 *ucb = uc + (size_t)b * h * w;
+        float2 *row = uf + r * W;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            const float x = ((float)j + 0.5f) * 0.5f - 0.5f;
+            const float2 v = bilinear2_clamped(ucb, h, w, x, y);
+            row[j] = make_float2(2.0f * v.x, 2.0f * v.y);
+        }
     }
+}
+
+// Prolongation of B coarse fields (h x w) to the finer level's stored size H x W.
+int launch_prolong(hrebsd_ctx *ctx, const float2 *uc, float2 *uf, int B, int h, int w, int H, int W, cudaStream_t st)
+{
+    const int threads = W >= 256 ? 256 : (W + 31) / 32 * 32;
+    const size_t rows = (size_t)B * H, cap = (size_t)ctx->num_sms * (2048 / threads);
+    const size_t grid = rows < cap ? rows : cap, per = (rows + grid - 1) / grid;
+    hr_prof_begin(ctx, st);
+    prolong_kernel<<<(unsigned)grid, threads, 0, st>>>(uc, uf, B, h, w, H, W, per);
+    hr_prof_end(ctx, PROF_DEMONS_AUX, st);
+    HR_LAUNCHED(ctx);
+    return HREBSD_OK;
 }
 
 // Planar [B][2][h][w] -> interleaved [B][h][w] float2 (the optional initial field).
@@ -1377,6 +1470,22 @@ int dispatch_finalize(hrebsd_ctx *ctx, int rad, bool planar, const float2 *u0, c
                       const int32_t *iters, int levels, int level, float *uout, int B, int h, int w, int tiles_x,
                       int tiles, const Taps &taps, cudaStream_t st)
 {
+    if (rad == 3 && (w == 64 || w == 128 || w == 256)) {   // the row sweep
+        const int grid = B < ctx->num_sms * 8 ? B : ctx->num_sms * 8;
+        hr_prof_begin(ctx, st);
+#define HR_FSW(NT)                                                                                                 \
+        if (planar) demons_finalize_sweep_kernel<NT, true><<<grid, NT, 0, st>>>(u0, s0, s1, iters, levels, level, \
+                                                                                uout, B, h, taps);                 \
+        else demons_finalize_sweep_kernel<NT, false><<<grid, NT, 0, st>>>(u0, s0, s1, iters, levels, level, uout, B, \
+                                                                          h, taps)
+        if (w == 64) HR_FSW(64);
+        else if (w == 128) HR_FSW(128);
+        else HR_FSW(256);
+#undef HR_FSW
+        hr_prof_end(ctx, PROF_DEMONS_AUX, st);
+        HR_LAUNCHED(ctx);
+        return HREBSD_OK;
+    }
     long long items = (long long)B * tiles;
     int grid = (int)(items < ctx->num_sms * 8LL ? items : ctx->num_sms * 8LL);
     const size_t smem = (size_t)((TX + 2 * rad) * (TY + 2 * rad) + (TY + 2 * rad) * TX) * sizeof(float2);
@@ -1554,15 +1663,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
                 a.alpha2 = p->alpha * p->alpha;
                 a.taps = taps;
                 if ((e2 = launch_level(ctx, a, st))) return e2;
-                if (l > 0) {
-                    const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
-                    const size_t px = (size_t)B * Hf * Wf, blocks = (px + 255) / 256, cap = (size_t)ctx->num_sms * 16;
-                    hr_prof_begin(ctx, st);
-                    prolong_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>(
-                        (const float2 *)uout, (float2 *)u0, B, h, w, Hf, Wf);
-                    hr_prof_end(ctx, PROF_DEMONS_AUX, st);
-                    HR_LAUNCHED(ctx);
-                }
+                if (l > 0)   // to the finer level's stored size
+                    return launch_prolong(ctx, (const float2 *)uout, (float2 *)u0, B, h, w, H >> (l - 1), W >> (l - 1), st);
                 return HREBSD_OK;
             }
             hr_prof_begin(ctx, st);
@@ -1665,15 +1767,8 @@ int register_chunk(hrebsd_ctx *ctx, const float *ref, const float *test, const i
             if ((e2 = dispatch_finalize(ctx, rad, l == 0, (const float2 *)u0, (const float2 *)s0, (const float2 *)s1,
                                         iters, L, l, dst, B, h, w, tiles_x, tiles, taps, st)))
                 return e2;
-            if (l > 0) {
-                const int Hf = H >> (l - 1), Wf = W >> (l - 1);   // the finer level's stored size
-                const size_t px = (size_t)B * Hf * Wf, blocks = (px + 255) / 256, cap = (size_t)ctx->num_sms * 16;
-                hr_prof_begin(ctx, st);
-                prolong_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, st>>>((const float2 *)uout,
-                                                                                       (float2 *)u0, B, h, w, Hf, Wf);
-                hr_prof_end(ctx, PROF_DEMONS_AUX, st);
-                HR_LAUNCHED(ctx);
-            }
+            if (l > 0)   // to the finer level's stored size
+                return launch_prolong(ctx, (const float2 *)uout, (float2 *)u0, B, h, w, H >> (l - 1), W >> (l - 1), st);
             return HREBSD_OK;
         };
         if (given || !hr_graph_usable(ctx, st)) {

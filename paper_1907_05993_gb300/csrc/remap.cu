@@ -4,10 +4,10 @@
 // projection of R^T r', r' = (x' - xpc, y' - ypc, Z*): the reference point
 // that Eq. 2 maps onto x' under the pure rotation R.  The value is a Keys
 // (1981) cubic convolution (a = -0.5) over 4x4 reference pixels with
-// replicated borders.  One thread per output pixel of a row; a persistent
-// grid walks the rows of all pairs; the references (a few grains) are
-// gathered through the read-only path and stay in L2, so HBM traffic is the
-// 4 B written per pixel.
+// replicated borders.  One thread per output pixel of a row; each CTA of a
+// persistent grid walks an equal run of consecutive rows of all pairs; the
+// references (a few grains) are gathered through the read-only path and stay
+// in L2, so HBM traffic is the 4 B written per pixel.
 #include "internal.cuh"
 
 namespace {
@@ -23,51 +23,72 @@ __device__ __forceinline__ void keys_weights(float t, float *wt)
     wt[3] = ((a * s3 - 5.0f * a) * s3 + 8.0f * a) * s3 - 4.0f * a;
 }
 
-// A CTA walks output rows (row = pair x H + i, all index arithmetic 32-bit
-// and per row), threads along the row; R^T of the pair is read once per row
-// and kept in FP32 registers.
+// A CTA walks a contiguous run of output rows (row = pair x H + i, all index
+// arithmetic 32-bit), threads along the row; R^T of a pair is converted to
+// FP32 registers once, when the run enters the pair.  Pixels whose 4 x 4
+// footprint lies inside the reference read it without clamping; the others
+// clamp every tap (the same values, since the clamp only acts outside).
 __global__ void __launch_bounds__(256) remap_kernel(const float *__restrict__ ref, const int32_t *__restrict__ ref_idx,
                                                     const double *__restrict__ Rf, int B, int H, int W, float xpc,
-                                                    float ypc, float zs, float *__restrict__ out)
+                                                    float ypc, float zs, unsigned rows_per_cta, float *__restrict__ out)
 {
-  for (unsigned row = blockIdx.x; row < (unsigned)B * (unsigned)H; row += gridDim.x) {
-    const int b = (int)(row / (unsigned)H), i = (int)(row - (unsigned)b * H);
-    float r[9];
-    const double *R = Rf + (size_t)b * 9;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) r[k] = (float)__ldg(R + k);
+    const unsigned total = (unsigned)B * (unsigned)H;
+    const unsigned r0 = blockIdx.x * rows_per_cta;
+    const unsigned r1 = min(total, r0 + rows_per_cta);
     const size_t plane = (size_t)H * W;
-    const float *M = ref + (size_t)__ldg(ref_idx + b) * plane;
-    float *orow = out + (size_t)b * plane + (size_t)i * W;
-    const float dy = (float)i + 0.5f - ypc;
-    for (int j = threadIdx.x; j < W; j += blockDim.x) {
-        const float dx = (float)j + 0.5f - xpc;
-        // v = R^T r'
-        const float v0 = fmaf(r[0], dx, fmaf(r[3], dy, r[6] * zs));
-        const float v1 = fmaf(r[1], dx, fmaf(r[4], dy, r[7] * zs));
-        const float v2 = fmaf(r[2], dx, fmaf(r[5], dy, r[8] * zs));
-        const float iv = zs / v2;
-        const float x = fmaf(v0, iv, xpc - 0.5f), y = fmaf(v1, iv, ypc - 0.5f);
-        const float fx0 = floorf(x), fy0 = floorf(y);
-        const int x0 = (int)fx0, y0 = (int)fy0;
-        float wx[4], wy[4];
-        keys_weights(x - fx0, wx);
-        keys_weights(y - fy0, wy);
-        int cx[4];
+    int bcur = -1;
+    float r[9];
+    const float *M = ref;
+    for (unsigned row = r0; row < r1; ++row) {
+        const int b = (int)(row / (unsigned)H), i = (int)(row - (unsigned)b * H);
+        if (b != bcur) {   // uniform across the CTA
+            const double *R = Rf + (size_t)b * 9;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) cx[k] = min(max(x0 - 1 + k, 0), W - 1);
-        float acc = 0.0f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float *row = M + min(max(y0 - 1 + m, 0), H - 1) * W;
-            float rr = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) rr = fmaf(wx[k], __ldg(row + cx[k]), rr);
-            acc = fmaf(wy[m], rr, acc);
+            for (int k = 0; k < 9; ++k) r[k] = (float)__ldg(R + k);
+            M = ref + (size_t)__ldg(ref_idx + b) * plane;
+            bcur = b;
         }
-        orow[j] = acc;
+        float *orow = out + (size_t)b * plane + (size_t)i * W;
+        const float dy = (float)i + 0.5f - ypc;
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            const float dx = (float)j + 0.5f - xpc;
+            // v = R^T r'
+            const float v0 = fmaf(r[0], dx, fmaf(r[3], dy, r[6] * zs));
+            const float v1 = fmaf(r[1], dx, fmaf(r[4], dy, r[7] * zs));
+            const float v2 = fmaf(r[2], dx, fmaf(r[5], dy, r[8] * zs));
+            const float iv = zs / v2;
+            const float x = fmaf(v0, iv, xpc - 0.5f), y = fmaf(v1, iv, ypc - 0.5f);
+            const float fx0 = floorf(x), fy0 = floorf(y);
+            const int x0 = (int)fx0, y0 = (int)fy0;
+            float wx[4], wy[4];
+            keys_weights(x - fx0, wx);
+            keys_weights(y - fy0, wy);
+            float acc = 0.0f;
+            if (x0 >= 1 && x0 <= W - 3 && y0 >= 1 && y0 <= H - 3) {
+                const float *p = M + (y0 - 1) * W + (x0 - 1);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    float rr = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rr = fmaf(wx[k], __ldg(p + m * W + k), rr);
+                    acc = fmaf(wy[m], rr, acc);
+                }
+            } else {
+                int cx[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cx[k] = min(max(x0 - 1 + k, 0), W - 1);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const float *rowp = M + min(max(y0 - 1 + m, 0), H - 1) * W;
+                    float rr = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rr = fmaf(wx[k], __ldg(rowp + cx[k]), rr);
+                    acc = fmaf(wy[m], rr, acc);
+                }
+            }
+            orow[j] = acc;
+        }
     }
-  }
 }
 
 }  // namespace
@@ -85,8 +106,11 @@ extern "C" int hrebsd_remap(hrebsd_ctx *ctx, const float *ref, const int32_t *re
     const int threads = W >= 256 ? 256 : (W + 31) / 32 * 32;
     const long long cap = (long long)ctx->num_sms * (2048 / threads);   // resident CTAs
     hr_prof_begin(ctx, hr_stream(stream));
-    remap_kernel<<<(unsigned)(rows < cap ? rows : cap), threads, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
-                                                      (float)(g->ystar * H), (float)(g->zstar * W), remapped);
+    const unsigned grid = (unsigned)(rows < cap ? rows : cap);
+    const unsigned per = (unsigned)((rows + grid - 1) / grid);   // rows of one CTA's run
+    remap_kernel<<<grid, threads, 0, hr_stream(stream)>>>(ref, ref_idx, R_finite, B, H, W, (float)(g->xstar * W),
+                                                          (float)(g->ystar * H), (float)(g->zstar * W), per,
+                                                          remapped);
     hr_prof_end(ctx, PROF_REMAP, hr_stream(stream));
     HR_LAUNCHED(ctx);
     return HREBSD_OK;
