@@ -278,7 +278,10 @@ int hrebsd_demons_register_batch_noalloc(hrebsd_ctx *ctx, const float *ref, cons
  * registrations of that level size in this context, the shape with the least
  * time x (1 + 0.01 log2(4096 / tile area)): smaller tiles carry a 1 % handicap
  * per halving of the area, because the synthetic timing showed a tie where
- * the 64x64 shape was 4 % faster on scan data.  Synchronises `stream`; uses context
+ * the 64x64 shape was 4 % faster on scan data; shapes 0-6 count 0.005 ms more
+ * per iteration for the stop-control launch that follows each of their
+ * iterations (shape 7 applies the stop rule in its CTAs), which the timing
+ * leaves out.  Synchronises `stream`; uses context
  * workspace.  ms_out (host, nullable): [levels][HREBSD_TILE_VARIANTS]
  * milliseconds per iteration, NaN where a shape is unavailable.  Returns
  * HREBSD_EINVAL for invalid parameters (as hrebsd_demons_register_batch). */

@@ -2053,7 +2053,13 @@ extern "C" int hrebsd_autotune(hrebsd_ctx *ctx, int B, int H, int W, const hrebs
                 // synthetic patterns (small, smooth displacements; every pair active) timed the
                 // 64x32 and 64x64 shapes as a tie at 256x256 where the 64x64 one was 4 % faster
                 // on the batched scan; a clearly faster small tile still wins.
-                const float score = ms * (1.0f + 0.01f * fmaxf(0.0f, log2f(4096.0f / (float)(kVarTX[v] * kVarTY[v]))));
+                // Every shape but the level in shared memory (7) leaves the stop rule to a control
+                // launch after each iteration, which this timing does not see: about 5 us per
+                // iteration in the batched scan's launch list, added to their time.
+                constexpr float kCtrlMs = 0.005f;
+                const float extra = vv ? 0.0f : kCtrlMs;
+                const float score = (ms + extra) *
+                                    (1.0f + 0.01f * fmaxf(0.0f, log2f(4096.0f / (float)(kVarTX[v] * kVarTY[v]))));
                 if (best_v == 0 && best == 0.0f) {
                     best = score;
                     best_v = v;

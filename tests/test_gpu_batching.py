@@ -95,7 +95,8 @@ def test_autotune_records_the_fastest_shape(torch, lib):
     assert np.isfinite(ms[:3, 5:7]).all() and np.isnan(ms[3, 5:7]).all(), ms
     assert np.isnan(ms[:2, 7]).all() and np.isfinite(ms[2:, 7]).all(), ms
     area = np.array(lib.TILE_AREAS, dtype=np.float64)
-    score = ms * (1.0 + 0.01 * np.maximum(0.0, np.log2(4096.0 / area)))   # the documented handicap of small tiles
+    ctrl = np.where(np.arange(lib.TILE_VARIANTS) < 7, 0.005, 0.0)   # the control launch of shapes 0-6
+    score = (ms + ctrl) * (1.0 + 0.01 * np.maximum(0.0, np.log2(4096.0 / area)))   # and the small-tile handicap
     score[:, 6] = np.nan   # shape 6 is timed but never chosen
     for l in range(4):
         assert lib.hrebsd_get_tile_variant(ctx, 256 >> l, 256 >> l) == int(np.nanargmin(score[l]))
