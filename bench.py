@@ -237,7 +237,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-E2E_CHUNKS = 4   # slices of the end-to-end (host-buffer) path
+E2E_CHUNKS, E2E_GROWTH = 2, 4.0   # slices of the end-to-end (host-buffer) path: 1 : 4
 
 
 def run_ours(args, rank, world, local_rank):
@@ -351,14 +351,14 @@ def run_ours(args, rank, world, local_rank):
     # side stream while slice k is processed, results copied back into pinned host tensors.  One
     # untimed pass first (new slice buffers: autotune and per-level graph capture happen there).
     host_out = {"F": h_F, "R_finite": h_R, "status": h_st}
-    pipe.run_host(h_refs, h_tests, h_ridx, chunks=E2E_CHUNKS, out=host_out)
+    pipe.run_host(h_refs, h_tests, h_ridx, chunks=E2E_CHUNKS, out=host_out, growth=E2E_GROWTH)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(e_steps):
-        pipe.run_host(h_refs, h_tests, h_ridx, chunks=E2E_CHUNKS, out=host_out)
+        pipe.run_host(h_refs, h_tests, h_ridx, chunks=E2E_CHUNKS, out=host_out, growth=E2E_GROWTH)
     e1.record(stream)
     torch.cuda.synchronize()
     te = max_over_ranks(e0.elapsed_time(e1) / 1e3, device="cuda")
@@ -414,8 +414,8 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(wl, B),
             "e2e": {"value": world * B * e_steps / te, "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
-                    "path": f"Pipeline.run_host: pinned host inputs, {E2E_CHUNKS} slices growing 1:2:4:8, copy of "
-                            f"slice k+1 overlapping slice k, F/R/status back to pinned host"},
+                    "path": f"Pipeline.run_host: pinned host inputs, {E2E_CHUNKS} slices of sizes 1:{E2E_GROWTH:g}, copy "
+                            f"of slice k+1 overlapping slice k, F/R/status back to pinned host"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "kernel": "demons iteration (every launch of every level; shapes in "
                                                    "demons_tile_shape_per_level)", "achieved": achieved, "peak": peak,

@@ -167,14 +167,18 @@ class Pipeline:
         cuts.append(B)
         return cuts
 
-    def run_host(self, refs_host, tests_host, ref_idx_host, chunks=4, out=None, growth=2.0):
+    def run_host(self, refs_host, tests_host, ref_idx_host, chunks=2, out=None, growth=4.0):
         """Host-resident inputs: refs [R,H,W] and tests [B,H,W] float32, ref_idx [B] int32, in pinned CPU
         memory.  The batch runs through ``run`` as ``chunks`` consecutive slices (sizes growing by
         ``growth``, see slice_bounds) on the current stream; the host -> device copy of slice k + 1 runs
         on a side stream while slice k is processed, and F, R_finite (FP64 [B, 9]) and status ([B]) of
         every slice are copied into pinned host tensors, returned in a dict (valid once the current
         stream has synchronised).  Each pair's result is the one ``run`` gives on the whole batch (pairs
-        are independent); the static background, a statistic of the whole batch, needs chunks=1."""
+        are independent); the static background, a statistic of the whole batch, needs chunks=1.
+        Two slices of 1 : 4 by default: every slice is a registration of its own, whose last iterations
+        (the pairs that run to the cap) leave CTAs idle once fewer pairs remain than CTAs, so more,
+        smaller slices lose more there than they hide of the copy (10,000 pairs of 256x256 on GB300 at
+        211 GB/s host to device: 4 slices 1:2:4:8 418 ms, 2 slices 1:4 388 ms, device-resident 373 ms)."""
         t = self.torch
         if self.cfg.static_background and chunks > 1:
             raise ValueError("the static background is a whole-batch statistic: use chunks=1")
@@ -222,7 +226,7 @@ class Pipeline:
                 o[name][a:b].copy_(r[name], non_blocking=True)
         return o
 
-    def run_scan(self, refs_host, tests_host, ref_idx_host, out_dir, chunk=10_000, slices=4):
+    def run_scan(self, refs_host, tests_host, ref_idx_host, out_dir, chunk=10_000, slices=2):
         """A whole scan from pinned host inputs, resumable: chunks of ``chunk`` points go through
         ``run_host`` (``slices`` overlapped slices each) and F, R_finite and status of every chunk are
         written to ``out_dir`` (see scan.run_resumable); calling it again after an interruption
