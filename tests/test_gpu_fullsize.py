@@ -10,10 +10,12 @@ oracle's inputs never come from GPU code.  The stop rule is a threshold on the r
 (reading of the convergence criterion), which FP32 and FP64 can cross one iteration apart, so the
 oracle replays the library's per-level iteration counts (its `replay` argument); every sampled pair
 is then held to the bars: rotation <= 1e-5 rad, every F component <= 1e-6, non-tie integer XCF
-peaks bit-exact, and the field bar of tests/fp32_sensitivity.py (the deviation distribution no
+peaks bit-exact (a tie: a near tie on either side, or a peak that one of the oracle's FP32
+executions moves), and the field bar of tests/fp32_sensitivity.py (the deviation distribution no
 wider than the oracle's own under FP32-sized perturbations, up to the worst pixel).  Where the oracle's own
 result moves by more than the bar when it runs with FP32 storage (an ill-conditioned pair), the
-rotation and F bars are widened to twice that measured spread, and the test reports the pair.  Each side's own stop rule is compared separately (test_stop_rule_agreement_full_size)."""
+rotation and F bars are widened to twice that measured spread, the count of compared peaks may fall
+below 20, and the test reports the pair.  Each side's own stop rule is compared separately (test_stop_rule_agreement_full_size)."""
 import math
 import multiprocessing as mp
 
@@ -134,16 +136,22 @@ def _check_scan(pool, cfg, sample):
         rot_bar, F_bar = max(ROT_TOL, 2 * rot_s), max(F_TOL, 2 * F_s)
         if rot > ROT_TOL or dF > F_TOL:
             widened.append(p)
-        ok = ~(g["near_tie"][p].astype(bool) | e["tie"])
+        # integer peaks compared where neither side has a near tie and every FP32 execution of the oracle
+        # finds the FP64 run's peak (a peak the oracle's own FP32 rounding moves is a tie at this pair's
+        # conditioning, as the rotation and F bars widen with the executions' spread)
+        stable = np.all([np.all(m["peak"] == e["peak"], axis=-1) for m in mem], axis=0)
+        ok = ~(g["near_tie"][p].astype(bool) | e["tie"]) & stable
         peaks_equal = bool(np.array_equal(g["peak"][p][ok], e["peak"][ok]))
+        ill = rot > ROT_TOL or dF > F_TOL
         fo = FS.assert_field_parity(g["field"][p], e["field"], [m["field"] for m in mem],
                                     what=f"config {cfg} pair {p}")
         lines.append(f"pair {p:5d} iters {g['iters'][p].tolist()} rot {rot:.1e} (spread {rot_s:.1e}) "
-                     f"F {dF:.1e} (spread {F_s:.1e}) peaks {int(ok.sum())} equal={peaks_equal} "
+                     f"F {dF:.1e} (spread {F_s:.1e}) peaks {int(ok.sum())} ({int((~stable).sum())} moved by the "
+                     f"oracle's FP32 executions) equal={peaks_equal} "
                      f"field max {fo['max']:.1e} (oracle's own {fo['q1.0'][1]:.1e}) "
                      f"over 1e-3 {fo['frac_over']:.1e} (oracle's own {fo['frac_over_oracle']:.1e})")
         assert rot <= rot_bar and dF <= F_bar, lines[-1]
-        assert peaks_equal and ok.sum() >= 20, lines[-1]
+        assert peaks_equal and (ok.sum() >= 20 or ill), lines[-1]
     print(f"config {cfg}:\n" + "\n".join(lines) + f"\npairs needing the conditioning allowance: {widened}")
     # the allowance is for the odd ill-conditioned pair, not a way around the bars
     assert len(widened) <= max(1, len(sample) // 10), widened
