@@ -27,6 +27,15 @@ field is no further from the FP64 oracle than the FP64 oracle is from itself und
 perturbations, at every level of the distribution up to the worst pixel.  ``strict`` holds every
 pixel to 1e-3 px instead (the bar for runs short enough not to reach the unstable regime).
 
+``arithmetic_fields`` is the stronger model: every elementary operation of the iteration (each
+product and sum of the smoothing passes, of the bilinear warp, of d, of the force denominator, of the
+quotient and of the update) rounded to FP32 by the same seeded stochastic rounding, as an FP32
+implementation rounds each operation.  Storage rounding keeps the arithmetic in FP64 between
+stores, and at a pixel where the iteration has two nearby fixed points (the force of Eq. 1 is not
+monotone in d) it can miss the branch that FP32 arithmetic reaches: one training pair (178925 of the
+training set) has such a pixel, where 64 storage-rounding executions stay within 3.3e-3 px of the
+FP64 field while 9 of 16 arithmetic-rounding executions settle 3.5e-2 px away, on the other branch.
+
 Test infrastructure: imports the oracle; only tests use it."""
 from __future__ import annotations
 
@@ -103,6 +112,84 @@ def preprocess_ulps(got, exp):
 
 def perturbed_fields(oracle, ref, test, levels, iters, members=4, seed0=1000, **kw):
     return [perturbed_register(oracle, ref, test, levels, iters, seed=seed0 + m, **kw) for m in range(members)]
+
+
+def _smooth_ops32(img, sigma, r):
+    """The oracle's separable Gaussian (x pass, then y pass; replicated borders) with every product and
+    every partial sum rounded by r."""
+    if sigma <= 0:
+        return img
+    k = int(np.ceil(3 * sigma))
+    j = np.arange(-k, k + 1)
+    t = np.exp(-j * j / (2.0 * sigma * sigma))
+    t = t / t.sum()
+    out = img
+    for axis in (1, 0):
+        pad = [(0, 0), (0, 0)]
+        pad[axis] = (k, k)
+        p = np.pad(out, pad, mode="edge")
+        n = out.shape[axis]
+        sl = (lambda i: p[:, i:i + n]) if axis == 1 else (lambda i: p[i:i + n, :])
+        acc = r(t[0] * sl(0))
+        for i in range(1, 2 * k + 1):
+            acc = r(acc + r(t[i] * sl(i)))
+        out = acc
+    return out
+
+
+def _level_ops32(oracle, F, M, u, n, alpha, sigma_up, sigma_f, r):
+    """n updates of Eq. 1 at one level, every elementary operation rounded by r."""
+    h, w = F.shape
+    gx, gy = (r(g) for g in oracle.gradient(F))
+    Y, X = np.mgrid[0:h, 0:w].astype(np.float64)
+    a2 = alpha * alpha
+    for _ in range(n):
+        # bilinear sample of M at x - u with replicated borders, each product and sum rounded
+        x = np.clip(r(X - u[0]), 0, w - 1)
+        y = np.clip(r(Y - u[1]), 0, h - 1)
+        x0 = np.minimum(np.floor(x), w - 2).astype(int)
+        y0 = np.minimum(np.floor(y), h - 2).astype(int)
+        fx, fy = r(x - x0), r(y - y0)
+        omx, omy = r(1.0 - fx), r(1.0 - fy)
+        top = r(r(omx * M[y0, x0]) + r(fx * M[y0, x0 + 1]))
+        bot = r(r(omx * M[y0 + 1, x0]) + r(fx * M[y0 + 1, x0 + 1]))
+        mw = r(r(omy * top) + r(fy * bot))
+        d = r(mw - F)
+        den = r(r(r(gx * gx) + r(gy * gy)) + r(r(a2 * d) * d))
+        ok = den > 1e-9
+        t = np.where(ok, r(d / np.where(ok, den, 1.0)), 0.0)
+        du = (r(t * gx), r(t * gy))
+        u = np.stack([_smooth_ops32(r(u[c] + _smooth_ops32(du[c], sigma_up, r)), sigma_f, r) for c in range(2)])
+    return u
+
+
+def arithmetic_register(oracle, ref, test, levels, iters, alpha=1.0, sigma_up=1.0, sigma_f=1.0, seed=0,
+                        input_ulps=0):
+    """One FP32-arithmetic execution of the registration replaying `iters` updates per level (finest
+    first): the inputs, pyramid and prolongation as in perturbed_register, the iteration with every
+    elementary operation rounded (module docstring); seed < 0 rounds nothing (FP64 throughout)."""
+    rng = np.random.default_rng(seed if seed >= 0 else 0)
+    r = (lambda a: round32(a, rng)) if seed >= 0 else (lambda a: np.asarray(a, np.float64))
+    def noisy(img):
+        img = r(img)
+        if seed >= 0 and input_ulps:
+            sp = np.spacing(np.abs(img).astype(np.float32)).astype(np.float64)
+            img = img + rng.uniform(-input_ulps, input_ulps, img.shape) * sp
+        return img
+    Fp, Mp = [noisy(test)], [noisy(ref)]
+    for _ in range(1, levels):
+        Fp.append(r(oracle.reduce2(Fp[-1])))
+        Mp.append(r(oracle.reduce2(Mp[-1])))
+    u = np.zeros((2,) + Fp[-1].shape)
+    for l in range(levels - 1, -1, -1):
+        u = _level_ops32(oracle, Fp[l], Mp[l], u, int(iters[l]), alpha, sigma_up, sigma_f, r)
+        if l > 0:
+            u = r(oracle.prolong(u, *Fp[l - 1].shape))
+    return u
+
+
+def arithmetic_fields(oracle, ref, test, levels, iters, members=4, seed0=5000, **kw):
+    return [arithmetic_register(oracle, ref, test, levels, iters, seed=seed0 + m, **kw) for m in range(members)]
 
 
 def sensitivity(exp, members):

@@ -151,6 +151,27 @@ def test_perturbed_register_helper(oracle):
     assert abs(np.mean(b - a)) < 1e-3 * np.mean(np.spacing(np.abs(a).astype(np.float32)))
 
 
+def test_arithmetic_register_helper(oracle):
+    """The FP32-arithmetic executions of the helper (every elementary operation of the iteration
+    rounded) restate the oracle's registration: without rounding they agree with
+    oracle.demons_register replaying the same counts to FP64 rounding (the sums are grouped as an FP32
+    code groups them), and their members stay within FP32-sized distances of it and differ from one
+    another."""
+    import fp32_sensitivity as FS
+    spec = K.ScanSpec(n_pairs=1, H=64, W=64, n_refs=1, mis_lo_deg=1.0, mis_hi_deg=2.0, seed=12)
+    M = oracle.preprocess(K.render_ref(spec, 0).astype(np.float64))
+    F = oracle.preprocess(K.render_test(spec, 0).astype(np.float64))
+    it = np.array([7, 5, 4], np.int32)
+    exp, _ = oracle.demons_register(M, F, 3, [10] * 3, 1.0, 1.0, 1.0, 0, 0.0, -1, None, it)
+    assert np.abs(FS.arithmetic_register(oracle, M, F, 3, it, seed=-1) - exp).max() < 1e-10
+    exp2, _ = oracle.demons_register(M, F, 3, [10] * 3, 2.0, 0.0, 1.6, 0, 0.0, -1, None, it)
+    got2 = FS.arithmetic_register(oracle, M, F, 3, it, 2.0, 0.0, 1.6, seed=-1)
+    assert np.abs(got2 - exp2).max() < 1e-10
+    m = FS.arithmetic_fields(oracle, M, F, 3, it, members=2)
+    s = FS.sensitivity(exp, m)
+    assert 0 < np.median(s) < 1e-5 and s.max() < 1e-2 and not np.array_equal(m[0], m[1])
+
+
 def test_pyramid_for_sizes_that_do_not_halve(oracle):
     """Reading for the paper's 1244 x 1024 patterns: a level is floor(H/2) x floor(W/2) (an odd last row
     or column takes no part in the 2 x 2 box mean) and the prolongation fills the stored finer size, its
